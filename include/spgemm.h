@@ -1,0 +1,194 @@
+/* spgemm.h: C ABI of the GB300 sparse matrix-matrix product C = A*B (CSR in, CSR out).
+ *
+ * The operation is the row-by-row (Gustavson) product of the paper's Algorithm 1
+ * (Sec. III-A, "A row-by-row formulation of SpGEMM"): row i of C is the merge, by column,
+ * of the rows of B named by the column indices of row i of A, each scaled by the
+ * matching value of A. Every column that receives a partial product is an entry of C,
+ * even when its sum is exactly zero (Algorithm 1 emits every column of COLB), and each
+ * row of C is sorted by column (Algorithm 1 sorts the partial products before merging;
+ * the sort unit of Sec. III-A keeps them in column order).
+ *
+ * The call sequence splits the product the way the method does: a plan that counts the
+ * partial products of each row (the B rows "streamed" for row i, Sec. III-A) and groups
+ * rows by work (the device-side counterpart of the CPU scheduling of RIR bundles,
+ * Sec. II and III-A), a symbolic pass that sizes every row of C, and a numeric pass that
+ * multiplies, merges and writes the sorted rows (the match/multiply, sort and merge units
+ * of Sec. III-A).
+ *
+ * Conventions for every entry point:
+ *  - Pointers documented as "device" must be CUDA device pointers on the current device;
+ *    "host" pointers are ordinary (pageable or pinned) host memory.
+ *  - A CSR matrix has row_ptr[rows+1] (int32 or int64, chosen by idx64_rowptr), col[nnz]
+ *    (int32) and val[nnz] (double for SPGEMM_F64, float for SPGEMM_F32_COMPENSATED).
+ *    Inputs must be canonical: row_ptr[0] == 0, row_ptr non-decreasing, row_ptr[rows] ==
+ *    nnz, and within each row the columns strictly increasing in [0, cols). Stored zeros
+ *    are allowed and are structural.
+ *  - Streams are cudaStream_t passed as void*; NULL means the legacy default stream.
+ *  - Functions return a status and never throw or abort. On failure the thread-local
+ *    message from spgemm_last_error() says what went wrong. A plan that returned an error
+ *    other than SPGEMM_ERR_NOT_READY or SPGEMM_ERR_TIMEOUT must only be destroyed.
+ *  - No entry point falls back to the CPU: every step of the product runs in the CUDA
+ *    kernels of this library.
+ */
+#ifndef SPGEMM_H_
+#define SPGEMM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spgemm_status {
+  SPGEMM_OK = 0,
+  SPGEMM_ERR_INVALID_ARG = 1,     /* bad pointer, size, shape or call order */
+  SPGEMM_ERR_INVALID_CSR = 2,     /* an input violates the canonical-CSR rules above */
+  SPGEMM_ERR_OOM = 3,             /* the allocator returned NULL */
+  SPGEMM_ERR_INDEX_OVERFLOW = 4,  /* nnz(C) needs an int64 row_ptr but int32 was requested */
+  SPGEMM_ERR_CUDA = 5,            /* a CUDA runtime call failed (message has the CUDA error) */
+  SPGEMM_ERR_TIMEOUT = 6,         /* a bounded wait gave up */
+  SPGEMM_ERR_REJECTED = 7,        /* the server refused the job (over the memory cap) */
+  SPGEMM_ERR_NOT_READY = 8,       /* a polled server job has not finished */
+  SPGEMM_ERR_UNSUPPORTED = 9,     /* a size or combination this build does not handle */
+  SPGEMM_ERR_INTERNAL = 10        /* a device-side consistency check failed */
+} spgemm_status;
+
+typedef enum spgemm_prec {
+  SPGEMM_F64 = 0,              /* FP64 values, FP64 products and sums */
+  SPGEMM_F32_COMPENSATED = 1   /* FP32 values; error-free product and compensated (two-sum)
+                                  accumulation per entry; rows whose entries exceed the
+                                  compensated error bound are recomputed in FP64 and
+                                  rounded once to FP32 */
+} spgemm_prec;
+
+/* Input matrix (device pointers, caller-owned; must stay valid until the numeric pass's
+ * stream work has completed). */
+typedef struct spgemm_csr_in {
+  int64_t rows, cols, nnz;
+  int32_t idx64_rowptr;      /* 0: row_ptr is int32, 1: int64 */
+  int32_t reserved_;
+  const void* row_ptr;
+  const int32_t* col;
+  const void* val;
+} spgemm_csr_in;
+
+/* Output matrix (caller-allocated arrays: row_ptr[rows+1], col[nnz], val[nnz]). */
+typedef struct spgemm_csr_out {
+  int64_t rows, cols, nnz;
+  int32_t idx64_rowptr;      /* 0: int32 row_ptr (only when nnz(C) < 2^31), 1: int64 */
+  int32_t reserved_;
+  void* row_ptr;
+  int32_t* col;
+  void* val;
+} spgemm_csr_out;
+
+/* Device workspace allocator. alloc returns device memory usable on `stream` (or NULL);
+ * free releases it in stream order. When the allocator pointer passed to an entry point is
+ * NULL the library uses cudaMallocAsync / cudaFreeAsync on the call's stream. */
+typedef struct spgemm_allocator {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} spgemm_allocator;
+
+/* Tuning and test knobs. Fill with spgemm_opts_default() and change what you need. */
+typedef struct spgemm_opts {
+  int32_t validate;           /* 1 (default): check the canonical-CSR rules of A and B */
+  int32_t tiny_max;           /* rows with <= this many products (<= 32) use one warp and no
+                                 shared table (default 32; 0 disables the class) */
+  int32_t warp_max;           /* symbolic: rows with min(P_i, n) <= this use a warp table;
+                                 numeric: rows with nnz(C_i) <= warp_max/2 (default 1024) */
+  int32_t block_max;          /* rows up to this size use a block-wide hash table; larger
+                                 rows take the windowed path (default 4096) */
+  int32_t window_hash_fill;   /* max entries of C per hash window (default 4800) */
+  int32_t force_window;       /* 1: every non-empty row takes the windowed path (tests) */
+  int64_t rowptr32_limit;     /* nnz(C) >= this requires an int64 row_ptr (default 2^31-1;
+                                 tests lower it) */
+  int32_t f32c_rerun_all;     /* 1: recompute every F32 row in FP64 (tests) */
+  int32_t f32c_rerun_none;    /* 1: never recompute (tests measure the bound alone) */
+  int32_t num_streams;        /* concurrent streams for the row classes (default 4) */
+  int32_t reserved[15];
+} spgemm_opts;
+
+/* Opaque plan: the work description of one product (row counts, row classes, row
+ * offsets of C) and its device workspace. */
+typedef struct spgemm_plan_s spgemm_plan_t;
+
+/* Counters describing a plan (host values). */
+typedef struct spgemm_plan_info {
+  int64_t rows, inner, cols;
+  int64_t products;            /* sum_i P_i = number of partial products (flops = 2x) */
+  int64_t nnz_c;               /* -1 before spgemm_symbolic */
+  int64_t max_row_products;
+  int64_t sym_class_rows[16];  /* rows per symbolic row class (class order is internal) */
+  int64_t num_class_rows[16];  /* rows per numeric row class (after spgemm_symbolic) */
+  int64_t workspace_bytes;     /* device workspace held by the plan */
+  int64_t f32c_rerun_rows;     /* rows recomputed in FP64 by the last F32 numeric pass */
+  int32_t needs_rowptr64;
+  int32_t state;               /* 0 planned, 1 symbolic done, 2 numeric done */
+} spgemm_plan_info;
+
+void spgemm_opts_default(spgemm_opts* opts);
+
+/* The plan: validate A and B (if opts->validate), count P_i for every row of A
+ * (the partial products of Algorithm 1's inner loops), and group the rows into classes by
+ * work on the device. A and B are read on `stream`; the plan keeps their pointers.
+ * Blocks `stream` once to read back the class sizes and sum_i P_i.
+ * Errors: INVALID_ARG (NULL pointers, A.cols != B.rows, negative sizes, prec mismatch),
+ * INVALID_CSR, OOM, CUDA, UNSUPPORTED (sizes beyond int32 column indices). */
+spgemm_status spgemm_plan(const spgemm_csr_in* A, const spgemm_csr_in* B, spgemm_prec prec,
+                          const spgemm_opts* opts, const spgemm_allocator* alloc,
+                          void* stream, spgemm_plan_t** out_plan);
+
+/* The symbolic pass. Computes nnz(C_i) for every row (the size of Algorithm 1's
+ * COLB set for row i), the row offsets of C, and the numeric row classes. Blocks `stream`
+ * once and returns nnz(C) in *nnz_c and, in *needs_rowptr64, 1 when nnz(C) does not fit an
+ * int32 row_ptr. Either output pointer may be NULL. Errors: INVALID_ARG (wrong state),
+ * OOM, CUDA, INTERNAL. */
+spgemm_status spgemm_symbolic(spgemm_plan_t* plan, void* stream, int64_t* nnz_c,
+                              int32_t* needs_rowptr64);
+
+/* The numeric pass. Writes C.row_ptr, C.col (sorted per row) and C.val into the
+ * caller's device arrays, asynchronously on `stream` (no host synchronisation, except for
+ * SPGEMM_F32_COMPENSATED, which reads back the number of rows to recompute in FP64).
+ * C->rows/cols/nnz must equal A.rows/B.cols/nnz(C). May be called again on the same plan
+ * (for example after the values of A or B changed but not their patterns).
+ * Errors: INVALID_ARG (wrong state or shape, NULL arrays), INDEX_OVERFLOW, CUDA, INTERNAL. */
+spgemm_status spgemm_numeric(spgemm_plan_t* plan, spgemm_csr_out* C, void* stream);
+
+spgemm_status spgemm_plan_get_info(const spgemm_plan_t* plan, spgemm_plan_info* info);
+
+/* Waits for `stream` and reports the device-side consistency checks latched by the passes
+ * run so far on this plan (a row that wrote a different number of entries than the
+ * symbolic pass counted, a full hash table): INTERNAL when any fired, else OK.
+ * spgemm_numeric itself does not wait, so call this to check a numeric pass. */
+spgemm_status spgemm_plan_check(spgemm_plan_t* plan, void* stream);
+
+/* Releases the workspace (in order on the stream given at plan time) and the plan.
+ * NULL is accepted. */
+spgemm_status spgemm_plan_destroy(spgemm_plan_t* plan);
+
+/* One product through HOST buffers: copies A and B (host pointers) to the device, runs
+ * plan, symbolic and numeric, and copies C back into the caller's host arrays C->row_ptr
+ * (rows+1), C->col and C->val, which must hold nnz_capacity entries. When nnz(C) exceeds
+ * nnz_capacity nothing is copied, *nnz_c is set and INVALID_ARG is returned, so the caller
+ * can grow its buffers and call again. Synchronous. C->idx64_rowptr selects the row_ptr
+ * type. Device staging comes from `alloc` (cudaMallocAsync when NULL). */
+spgemm_status spgemm_multiply_host(const spgemm_csr_in* A_host, const spgemm_csr_in* B_host,
+                                   spgemm_prec prec, const spgemm_opts* opts,
+                                   const spgemm_allocator* alloc, void* stream,
+                                   spgemm_csr_out* C_host, int64_t nnz_capacity,
+                                   int64_t* nnz_c);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* spgemm_last_error(void);
+
+/* Library version string. */
+const char* spgemm_version(void);
+
+#ifdef __cplusplus
+}  /* extern "C" */
+#endif
+
+#endif /* SPGEMM_H_ */

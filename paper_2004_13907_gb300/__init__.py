@@ -1,0 +1,233 @@
+"""GB300 (sm_103a) sparse matrix-matrix product C = A*B on CSR matrices.
+
+A thin Python binding of the C ABI in ``include/spgemm.h`` with the same entry-point
+names. It only marshals arguments (device pointers from torch tensors, the current CUDA
+stream); every step of the product runs in the library's CUDA kernels. PyTorch provides
+device memory and streams.
+
+The product is the row-by-row (Gustavson) formulation of the paper's Algorithm 1
+(Sec. III-A): row i of C merges, by column, the rows of B named by row i of A scaled by
+the matching entries of A, sorted by column, one entry per column that received a partial
+product.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _native
+from ._native import F32_COMPENSATED, F64, SpgemmError  # noqa: F401
+
+__all__ = [
+    "DeviceCSR", "Plan", "SpgemmError", "F64", "F32_COMPENSATED", "spgemm_opts_default",
+    "spgemm_plan", "spgemm_symbolic", "spgemm_numeric", "spgemm_plan_get_info",
+    "spgemm_plan_check", "spgemm_plan_destroy", "spgemm_multiply_host", "spgemm_last_error",
+    "spgemm_version", "multiply", "lib",
+]
+
+
+def lib() -> ctypes.CDLL:
+    return _native.load()
+
+
+def _prec(p) -> int:
+    if p in (F64, "f64", "fp64", torch.float64):
+        return F64
+    if p in (F32_COMPENSATED, "f32c", "fp32c", "f32", torch.float32):
+        return F32_COMPENSATED
+    raise ValueError(f"unknown precision {p!r}")
+
+
+def _vdtype(prec: int) -> torch.dtype:
+    return torch.float64 if prec == F64 else torch.float32
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+@dataclass
+class DeviceCSR:
+    """A CSR matrix whose arrays are torch tensors (device, or host for the host entry)."""
+
+    rows: int
+    cols: int
+    row_ptr: torch.Tensor   # int32 or int64, rows+1
+    col: torch.Tensor       # int32, nnz
+    val: torch.Tensor       # float64 or float32, nnz
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    @property
+    def idx64(self) -> int:
+        return 1 if self.row_ptr.dtype == torch.int64 else 0
+
+    @staticmethod
+    def from_host(M, device="cuda", dtype=None, idx64: bool = False) -> "DeviceCSR":
+        """From a host CSR (numpy arrays ``row_ptr``, ``col``, ``val``)."""
+        rp = torch.as_tensor(M.row_ptr).to(torch.int64 if idx64 else torch.int32)
+        col = torch.as_tensor(M.col).to(torch.int32)
+        val = torch.as_tensor(M.val)
+        if dtype is not None:
+            val = val.to(dtype)
+        return DeviceCSR(int(M.rows), int(M.cols), rp.to(device), col.to(device), val.to(device))
+
+    def to_host(self):
+        return DeviceCSR(self.rows, self.cols, self.row_ptr.cpu(), self.col.cpu(), self.val.cpu())
+
+    def as_in(self) -> _native.CsrIn:
+        return _native.CsrIn(self.rows, self.cols, self.nnz, self.idx64, 0, self.row_ptr.data_ptr(),
+                             self.col.data_ptr(), self.val.data_ptr())
+
+    def as_out(self) -> _native.CsrOut:
+        return _native.CsrOut(self.rows, self.cols, self.nnz, self.idx64, 0, self.row_ptr.data_ptr(),
+                              self.col.data_ptr(), self.val.data_ptr())
+
+
+class Plan:
+    """Handle of a native plan; keeps the input tensors alive while the plan holds their
+    pointers."""
+
+    def __init__(self, handle: int, A: DeviceCSR, B: DeviceCSR, prec: int):
+        self.handle = handle
+        self.A, self.B, self.prec = A, B, prec
+        self.nnz_c = -1
+        self.needs_rowptr64 = 0
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().spgemm_plan_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def spgemm_opts_default(**overrides) -> _native.Opts:
+    o = _native.Opts()
+    lib().spgemm_opts_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"spgemm_opts has no field {k}")
+        setattr(o, k, v)
+    return o
+
+
+def spgemm_plan(A: DeviceCSR, B: DeviceCSR, prec=F64, opts: _native.Opts | None = None,
+                stream=None) -> Plan:
+    prec = _prec(prec)
+    a, b = A.as_in(), B.as_in()
+    h = ctypes.c_void_p()
+    st = lib().spgemm_plan(ctypes.byref(a), ctypes.byref(b), prec,
+                           ctypes.byref(opts) if opts is not None else None, None,
+                           _stream_handle(stream), ctypes.byref(h))
+    _native.check(st)
+    return Plan(h.value, A, B, prec)
+
+
+def spgemm_symbolic(plan: Plan, stream=None) -> tuple:
+    nnz = ctypes.c_int64()
+    need = ctypes.c_int32()
+    _native.check(lib().spgemm_symbolic(plan.handle, _stream_handle(stream), ctypes.byref(nnz),
+                                        ctypes.byref(need)))
+    plan.nnz_c, plan.needs_rowptr64 = int(nnz.value), int(need.value)
+    return plan.nnz_c, plan.needs_rowptr64
+
+
+def spgemm_numeric(plan: Plan, C: DeviceCSR, stream=None) -> DeviceCSR:
+    c = C.as_out()
+    _native.check(lib().spgemm_numeric(plan.handle, ctypes.byref(c), _stream_handle(stream)))
+    return C
+
+
+def spgemm_plan_get_info(plan: Plan) -> dict:
+    info = _native.PlanInfo()
+    _native.check(lib().spgemm_plan_get_info(plan.handle, ctypes.byref(info)))
+    out = {}
+    for name, _ in _native.PlanInfo._fields_:
+        v = getattr(info, name)
+        out[name] = list(v) if not isinstance(v, int) else v
+    return out
+
+
+def spgemm_plan_check(plan: Plan, stream=None) -> None:
+    _native.check(lib().spgemm_plan_check(plan.handle, _stream_handle(stream)))
+
+
+def spgemm_plan_destroy(plan: Plan) -> None:
+    if plan.handle:
+        _native.check(lib().spgemm_plan_destroy(plan.handle))
+        plan.handle = None
+
+
+def spgemm_last_error() -> str:
+    return lib().spgemm_last_error().decode()
+
+
+def spgemm_version() -> str:
+    return lib().spgemm_version().decode()
+
+
+def alloc_output(plan: Plan, idx64: bool | None = None, device=None) -> DeviceCSR:
+    """Allocates C for a plan after spgemm_symbolic (row_ptr int64 when required)."""
+    if plan.nnz_c < 0:
+        raise RuntimeError("spgemm_symbolic has not run")
+    dev = device if device is not None else plan.A.col.device
+    use64 = plan.needs_rowptr64 if idx64 is None else int(idx64)
+    rp = torch.empty(plan.A.rows + 1, dtype=torch.int64 if use64 else torch.int32, device=dev)
+    col = torch.empty(plan.nnz_c, dtype=torch.int32, device=dev)
+    val = torch.empty(plan.nnz_c, dtype=_vdtype(plan.prec), device=dev)
+    return DeviceCSR(plan.A.rows, plan.B.cols, rp, col, val)
+
+
+def multiply(A: DeviceCSR, B: DeviceCSR, prec=F64, opts: _native.Opts | None = None, stream=None,
+             idx64: bool | None = None, check: bool = False) -> DeviceCSR:
+    """C = A*B on the device: plan, symbolic, allocate C, numeric (asynchronous after the
+    symbolic pass's read-back of nnz(C))."""
+    plan = spgemm_plan(A, B, prec, opts, stream)
+    spgemm_symbolic(plan, stream)
+    C = alloc_output(plan, idx64)
+    spgemm_numeric(plan, C, stream)
+    if check:
+        spgemm_plan_check(plan, stream)
+    spgemm_plan_destroy(plan)
+    return C
+
+
+def spgemm_multiply_host(A, B, prec=F64, opts: _native.Opts | None = None, stream=None,
+                         out: DeviceCSR | None = None, idx64: bool = False) -> DeviceCSR:
+    """C = A*B through host buffers (``DeviceCSR`` with CPU tensors, pinned for speed).
+    ``out`` may hold pre-allocated host arrays (capacity = its col length); they are grown
+    when nnz(C) does not fit."""
+    prec = _prec(prec)
+    a, b = A.as_in(), B.as_in()
+    for _ in range(2):
+        if out is None:
+            out = DeviceCSR(A.rows, B.cols,
+                            torch.empty(A.rows + 1, dtype=torch.int64 if idx64 else torch.int32),
+                            torch.empty(0, dtype=torch.int32), torch.empty(0, dtype=_vdtype(prec)))
+        c = out.as_out()
+        cap = out.col.numel()
+        nnz = ctypes.c_int64()
+        st = lib().spgemm_multiply_host(ctypes.byref(a), ctypes.byref(b), prec,
+                                        ctypes.byref(opts) if opts is not None else None, None,
+                                        _stream_handle(stream), ctypes.byref(c), cap, ctypes.byref(nnz))
+        if st == 1 and nnz.value > cap:
+            pin = out.row_ptr.is_pinned()
+            out = DeviceCSR(A.rows, B.cols, out.row_ptr,
+                            torch.empty(nnz.value, dtype=torch.int32, pin_memory=pin),
+                            torch.empty(nnz.value, dtype=_vdtype(prec), pin_memory=pin))
+            continue
+        _native.check(st)
+        n = int(nnz.value)
+        return DeviceCSR(A.rows, B.cols, out.row_ptr, out.col[:n], out.val[:n])
+    raise RuntimeError("spgemm_multiply_host: capacity retry failed")

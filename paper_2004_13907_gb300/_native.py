@@ -1,0 +1,105 @@
+"""ctypes declarations of the C ABI in include/spgemm.h (argument marshalling only)."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspgemm.so")
+
+c_i32, c_i64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+
+STATUS_NAMES = {
+    0: "OK", 1: "INVALID_ARG", 2: "INVALID_CSR", 3: "OOM", 4: "INDEX_OVERFLOW", 5: "CUDA",
+    6: "TIMEOUT", 7: "REJECTED", 8: "NOT_READY", 9: "UNSUPPORTED", 10: "INTERNAL",
+}
+F64, F32_COMPENSATED = 0, 1
+
+
+class SpgemmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"SPGEMM_ERR_{self.name}: {message}")
+
+
+class CsrIn(ctypes.Structure):
+    _fields_ = [("rows", c_i64), ("cols", c_i64), ("nnz", c_i64), ("idx64_rowptr", c_i32),
+                ("reserved_", c_i32), ("row_ptr", c_vp), ("col", c_vp), ("val", c_vp)]
+
+
+class CsrOut(ctypes.Structure):
+    _fields_ = [("rows", c_i64), ("cols", c_i64), ("nnz", c_i64), ("idx64_rowptr", c_i32),
+                ("reserved_", c_i32), ("row_ptr", c_vp), ("col", c_vp), ("val", c_vp)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(c_vp, ctypes.c_size_t, c_vp, c_vp)
+FREE_FN = ctypes.CFUNCTYPE(None, c_vp, c_vp, c_vp)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", c_vp)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("validate", c_i32), ("tiny_max", c_i32), ("warp_max", c_i32), ("block_max", c_i32),
+                ("window_hash_fill", c_i32), ("force_window", c_i32), ("rowptr32_limit", c_i64),
+                ("f32c_rerun_all", c_i32), ("f32c_rerun_none", c_i32), ("num_streams", c_i32),
+                ("reserved", c_i32 * 15)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("rows", c_i64), ("inner", c_i64), ("cols", c_i64), ("products", c_i64),
+                ("nnz_c", c_i64), ("max_row_products", c_i64), ("sym_class_rows", c_i64 * 16),
+                ("num_class_rows", c_i64 * 16), ("workspace_bytes", c_i64),
+                ("f32c_rerun_rows", c_i64), ("needs_rowptr64", c_i32), ("state", c_i32)]
+
+
+# name -> (restype, argtypes); every symbol include/spgemm.h declares
+SIGNATURES = {
+    "spgemm_opts_default": (None, [ctypes.POINTER(Opts)]),
+    "spgemm_plan": (c_i32, [ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_i32, ctypes.POINTER(Opts),
+                            ctypes.POINTER(Allocator), c_vp, ctypes.POINTER(c_vp)]),
+    "spgemm_symbolic": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i32)]),
+    "spgemm_numeric": (c_i32, [c_vp, ctypes.POINTER(CsrOut), c_vp]),
+    "spgemm_plan_get_info": (c_i32, [c_vp, ctypes.POINTER(PlanInfo)]),
+    "spgemm_plan_check": (c_i32, [c_vp, c_vp]),
+    "spgemm_plan_destroy": (c_i32, [c_vp]),
+    "spgemm_multiply_host": (c_i32, [ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_i32,
+                                     ctypes.POINTER(Opts), ctypes.POINTER(Allocator), c_vp,
+                                     ctypes.POINTER(CsrOut), c_i64, ctypes.POINTER(c_i64)]),
+    "spgemm_last_error": (ctypes.c_char_p, []),
+    "spgemm_version": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Loads libspgemm.so (built in-tree by ``build.py``). There is no fallback: without
+    the library no product can be computed, and this raises."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"{p} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"`"
+                              " (the CUDA library is required; there is no CPU fallback)")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def check(status: int) -> None:
+    if status != 0:
+        msg = load().spgemm_last_error()
+        raise SpgemmError(status, msg.decode() if msg else "")

@@ -1,0 +1,512 @@
+// Numeric pass, FP64: forms every partial product a_ik*b_kj of row i (the match
+// and multiply unit of Sec. III-A), merges the products of equal column (the merge unit)
+// and writes row i of C sorted by column (the sort unit; Algorithm 1 sorts PP and emits
+// one entry per column of COLB, including sums that cancel to zero).
+//
+// Row classes (chosen from nnz(C_i) after the symbolic pass):
+//  * tiny  : P_i <= 32: one warp, one product per lane; equal columns are grouped with a
+//            warp match and summed by the lowest lane of the group in product order; the
+//            output position is the number of smaller columns in the row.
+//  * warp  : one warp per row, a shared hash table (column -> FP64 sum) of 64/256/1024
+//            slots, then the occupied slots are compacted and bitonic-sorted by column.
+//  * block : one block per row, a hash table of 2048 or 8192 slots, compaction, bitonic sort.
+//  * window: one persistent block per row for rows with more entries than a block table.
+//            The columns are cut into blocks of kBlockCols; the symbolic pass counted the
+//            entries of C_i in each block. Consecutive blocks with few entries are merged
+//            into a "hash window" (a hash table of 8192 slots plus a bitmap of the window's
+//            columns); a block with many entries is a "dense window" (an FP64 array indexed
+//            by column minus the window start, plus a bitmap). Either way the bitmap, read in
+//            word order, gives the sorted column list for free. Each A entry keeps a cursor
+//            into its B row (global memory) so every product is read exactly once.
+// Sums are accumulated with shared-memory FP64 atomics, so their order (and the last bits of
+// a value) can change from run to run; the pattern is always exact.
+#include "enumerate.cuh"
+
+namespace spg {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_num_tiny(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
+                                                  int64_t count, const int64_t* __restrict__ c_off,
+                                                  int32_t* __restrict__ ccol, double* __restrict__ cval,
+                                                  uint32_t* err) {
+  __shared__ int32_t s_col[8][32];
+  __shared__ double s_val[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const double* av_ = static_cast<const double*>(A.val);
+  const double* bv_ = static_cast<const double*>(B.val);
+  for (int64_t r = gw; r < count; r += nw) {
+    const int32_t i = perm[r];
+    const int64_t a0 = A.rp[i];
+    const int32_t na = static_cast<int32_t>(A.rp[i + 1] - a0);
+    int32_t len = 0;
+    int64_t bs = 0;
+    double av = 0.0;
+    if (lane < na) {
+      const int32_t k = A.col[a0 + lane];
+      av = av_[a0 + lane];
+      bs = B.rp[k];
+      len = static_cast<int32_t>(B.rp[k + 1] - bs);
+    }
+    const int32_t incl = warp_incl_scan(len);
+    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int32_t v = __shfl_sync(0xffffffffu, incl, o + step - 1);
+      if (v <= lane) o += step;
+    }
+    const int32_t incl_o = __shfl_sync(0xffffffffu, incl, o & 31);
+    const int32_t len_o = __shfl_sync(0xffffffffu, len, o & 31);
+    const int64_t bs_o = __shfl_sync(0xffffffffu, bs, o & 31);
+    const double av_o = __shfl_sync(0xffffffffu, av, o & 31);
+    int32_t col = -2 - lane;
+    double val = 0.0;
+    if (lane < total) {
+      const int64_t j = bs_o + (lane - (incl_o - len_o));
+      col = B.col[j];
+      val = av_o * bv_[j];
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, col);
+    s_col[wid][lane] = col;
+    s_val[wid][lane] = val;
+    __syncwarp();
+    const bool lead = lane < total && (__ffs(peers) - 1) == lane;
+    const unsigned leaders = __ballot_sync(0xffffffffu, lead);
+    if (lead) {
+      double sum = 0.0;
+      for (unsigned m = peers; m; m &= m - 1) sum += s_val[wid][__ffs(m) - 1];
+      int rank = 0;
+      for (unsigned m = leaders; m; m &= m - 1) rank += s_col[wid][__ffs(m) - 1] < col;
+      if (rank < c_off[i + 1] - c_off[i]) {   // a miscount raises kErrCount, never writes out of the row
+        const int64_t out = c_off[i] + rank;
+        ccol[out] = col;
+        cval[out] = sum;
+      }
+    }
+    if (lane == 0 && c_off[i + 1] - c_off[i] != __popc(leaders)) set_error(err, kErrCount);
+    __syncwarp();
+  }
+}
+
+// Accumulate v into the slot of `key` (linear probing; keys are columns, kEmpty = free).
+template <int LOG2S>
+__device__ __forceinline__ void hash_accumulate(int32_t* keys, double* vals, int32_t key, double v,
+                                                uint32_t* err) {
+  constexpr int S = 1 << LOG2S;
+  uint32_t h = hash_slot(key, LOG2S);
+  for (int probe = 0; probe < S; ++probe) {
+    const int32_t cur = *reinterpret_cast<volatile int32_t*>(&keys[h]);
+    if (cur == key) { atomicAdd(&vals[h], v); return; }
+    if (cur == kEmpty) {
+      const int32_t old = atomicCAS(&keys[h], kEmpty, key);
+      if (old == kEmpty || old == key) { atomicAdd(&vals[h], v); return; }
+    }
+    h = (h + 1) & (S - 1);
+  }
+  set_error(err, kErrHashFull);
+}
+
+// In-warp bitonic sort of keys/vals[0, N), N a power of two.
+__device__ __forceinline__ void warp_bitonic(int32_t* keys, double* vals, int N) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < (N >> 1); t += 32) {
+        const int a = ((t / j) * 2 * j) + (t % j);
+        const int b = a + j;
+        const bool up = (a & k) == 0;
+        const int32_t ka = keys[a], kb = keys[b];
+        if ((ka > kb) == up) {
+          keys[a] = kb; keys[b] = ka;
+          const double va = vals[a]; vals[a] = vals[b]; vals[b] = va;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ void block_bitonic(int32_t* keys, double* vals, int N) {
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < (N >> 1); t += NT) {
+        const int a = ((t / j) * 2 * j) + (t % j);
+        const int b = a + j;
+        const bool up = (a & k) == 0;
+        const int32_t ka = keys[a], kb = keys[b];
+        if ((ka > kb) == up) {
+          keys[a] = kb; keys[b] = ka;
+          const double va = vals[a]; vals[a] = vals[b]; vals[b] = va;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ int pow2_ceil(int x) {
+  return x <= 1 ? 1 : 1 << (32 - __clz(x - 1));
+}
+
+template <int LOG2S>
+__global__ void __launch_bounds__(256) k_num_warp(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
+                                                  int64_t count, const int64_t* __restrict__ c_off,
+                                                  int32_t* __restrict__ ccol, double* __restrict__ cval,
+                                                  uint32_t* err) {
+  constexpr int S = 1 << LOG2S;
+  extern __shared__ double smem_f64[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double* vals = smem_f64 + wid * S;
+  int32_t* keys = reinterpret_cast<int32_t*>(smem_f64 + 8 * S) + wid * S;
+  const double* av_ = static_cast<const double*>(A.val);
+  const double* bv_ = static_cast<const double*>(B.val);
+  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = gw; r < count; r += nw) {
+    const int32_t i = perm[r];
+    const int64_t a0 = A.rp[i];
+    const int64_t na = A.rp[i + 1] - a0;
+    for (int s = lane; s < S; s += 32) { keys[s] = kEmpty; vals[s] = 0.0; }
+    __syncwarp();
+    warp_for_each_product(A, B, a0, na, [&](int64_t j, int64_t e) {
+      hash_accumulate<LOG2S>(keys, vals, B.col[j], av_[a0 + e] * bv_[j], err);
+    });
+    __syncwarp();
+    // compact in place (a write position never passes the slot being read)
+    int cnt = 0;
+    for (int base = 0; base < S; base += 32) {
+      const int32_t k = keys[base + lane];
+      const double v = vals[base + lane];
+      const bool occ = k != kEmpty;
+      const unsigned b = __ballot_sync(0xffffffffu, occ);
+      const int pos = cnt + __popc(b & ((1u << lane) - 1u));
+      __syncwarp();
+      if (occ) { keys[pos] = k; vals[pos] = v; }
+      cnt += __popc(b);
+      __syncwarp();
+    }
+    const int64_t off = c_off[i];
+    const int64_t len = c_off[i + 1] - off;
+    if (lane == 0 && len != cnt) set_error(err, kErrCount);
+    const int N = pow2_ceil(cnt);
+    for (int t = cnt + lane; t < N; t += 32) keys[t] = kNoCol;
+    __syncwarp();
+    warp_bitonic(keys, vals, N);
+    const int nw_out = cnt < len ? cnt : static_cast<int>(len);
+    for (int t = lane; t < nw_out; t += 32) {
+      ccol[off + t] = keys[t];
+      cval[off + t] = vals[t];
+    }
+    __syncwarp();
+  }
+}
+
+template <int LOG2S, int NT>
+__global__ void __launch_bounds__(NT) k_num_block(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
+                                                  int64_t count, const int64_t* __restrict__ c_off,
+                                                  int32_t* __restrict__ ccol, double* __restrict__ cval,
+                                                  uint32_t* err) {
+  constexpr int S = 1 << LOG2S;
+  extern __shared__ double smem_f64[];
+  double* vals = smem_f64;
+  int32_t* keys = reinterpret_cast<int32_t*>(smem_f64 + S);
+  __shared__ int32_t s_excl[NT];
+  __shared__ int64_t s_bs[NT];
+  __shared__ int32_t s_scan[33];
+  const double* av_ = static_cast<const double*>(A.val);
+  const double* bv_ = static_cast<const double*>(B.val);
+  for (int64_t r = blockIdx.x; r < count; r += gridDim.x) {
+    const int32_t i = perm[r];
+    const int64_t a0 = A.rp[i];
+    const int64_t na = A.rp[i + 1] - a0;
+    for (int s = threadIdx.x; s < S; s += NT) { keys[s] = kEmpty; vals[s] = 0.0; }
+    __syncthreads();
+    block_for_each_product<NT>(A, B, a0, na, s_excl, s_bs, s_scan, [&](int64_t j, int64_t e) {
+      hash_accumulate<LOG2S>(keys, vals, B.col[j], av_[a0 + e] * bv_[j], err);
+    });
+    // compact in place, one block-wide chunk at a time
+    int cnt = 0;
+    for (int base = 0; base < S; base += NT) {
+      const int32_t k = keys[base + threadIdx.x];
+      const double v = vals[base + threadIdx.x];
+      const int occ = k != kEmpty;
+      int32_t tot;
+      const int32_t pos = cnt + block_excl_scan<int32_t>(occ, s_scan, &tot);
+      if (occ) { keys[pos] = k; vals[pos] = v; }
+      cnt += tot;
+      __syncthreads();
+    }
+    const int64_t off = c_off[i];
+    const int64_t len = c_off[i + 1] - off;
+    if (threadIdx.x == 0 && len != cnt) set_error(err, kErrCount);
+    const int N = pow2_ceil(cnt);
+    for (int t = cnt + threadIdx.x; t < N; t += NT) keys[t] = kNoCol;
+    __syncthreads();
+    block_bitonic<NT>(keys, vals, N);
+    const int nb_out = cnt < len ? cnt : static_cast<int>(len);
+    for (int t = threadIdx.x; t < nb_out; t += NT) {
+      ccol[off + t] = keys[t];
+      cval[off + t] = vals[t];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- windowed rows
+// Shared layout (dynamic): [0, 128 KB): dense FP64[kBlockCols] | hash {keys int32[8192] at 0,
+// vals FP64[8192] at 32 KB}; then the window bitmap, kHashWinBlocks * kBlockWords words.
+// Hash keys are stored as column + 1 so that all-zero bytes are the clean state of both
+// layouts.
+constexpr int kWinRegionBytes = kBlockCols * 8;
+constexpr int kWinBitmapWords = kHashWinBlocks * kBlockWords;
+constexpr int kWinSmemBytes = kWinRegionBytes + kWinBitmapWords * 4;
+constexpr int kHashWinLog2 = 13;
+static_assert((1 << kHashWinLog2) == kHashWinSlots, "hash window size");
+static_assert(kHashWinSlots * 12 <= kWinRegionBytes, "hash window fits the region");
+
+enum : int { kWinDone = 0, kWinDense = 1, kWinHash = 2 };
+
+__global__ void __launch_bounds__(kWinThreads, 1) k_num_window(
+    DevCsr A, DevCsr B, const int32_t* __restrict__ perm, int64_t count, int32_t* counter,
+    const int64_t* __restrict__ c_off, const int32_t* __restrict__ win_slot,
+    const uint16_t* __restrict__ blockcnt, int64_t nblocks, int64_t nslots,
+    int32_t* __restrict__ cursor, int32_t hash_fill, int32_t* __restrict__ ccol,
+    double* __restrict__ cval, uint32_t* err) {
+  extern __shared__ __align__(16) unsigned char win_smem[];
+  double* dense = reinterpret_cast<double*>(win_smem);
+  int32_t* hkeys = reinterpret_cast<int32_t*>(win_smem);
+  double* hvals = reinterpret_cast<double*>(win_smem + kHashWinSlots * 4);
+  uint32_t* bm = reinterpret_cast<uint32_t*>(win_smem + kWinRegionBytes);
+  __shared__ int64_t s_scan[33];
+  __shared__ int32_t s_ctl[6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int kWarps = kWinThreads / 32;
+  const int64_t n = B.cols;
+  const double* av_ = static_cast<const double*>(A.val);
+  const double* bv_ = static_cast<const double*>(B.val);
+
+  for (int t = threadIdx.x; t < kWinSmemBytes / 16; t += kWinThreads)
+    reinterpret_cast<uint4*>(win_smem)[t] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+
+  for (;;) {
+    if (threadIdx.x == 0) s_ctl[0] = atomicAdd(counter, 1);
+    __syncthreads();
+    const int64_t idx = s_ctl[0];
+    if (idx >= count) break;
+    const int32_t i = perm[idx];
+    const int64_t slot = win_slot[i];
+    if (slot < 0 || slot >= nslots) {      // the row was not counted by the windowed symbolic pass
+      if (threadIdx.x == 0) set_error(err, kErrWindowPlan);
+      __syncthreads();
+      continue;
+    }
+    const uint16_t* cnts = blockcnt + slot * nblocks;
+    const int64_t a0 = A.rp[i];
+    const int64_t na = A.rp[i + 1] - a0;
+    int64_t out = c_off[i];
+    const int64_t out_end = c_off[i + 1];
+    int64_t next_b = 0;   // meaningful in thread 0 only
+    bool first = true;
+    for (;;) {
+      if (threadIdx.x == 0) {
+        int64_t b = next_b;
+        while (b < nblocks && cnts[b] == 0) ++b;
+        if (b >= nblocks) {
+          s_ctl[1] = kWinDone;
+        } else if (cnts[b] > hash_fill) {
+          s_ctl[1] = kWinDense; s_ctl[2] = static_cast<int32_t>(b); s_ctl[3] = static_cast<int32_t>(b + 1);
+          s_ctl[4] = cnts[b];
+          next_b = b + 1;
+        } else {
+          int64_t e = b;
+          int32_t sum = 0;
+          while (e < nblocks && e - b < kHashWinBlocks && sum + cnts[e] <= hash_fill) { sum += cnts[e]; ++e; }
+          s_ctl[1] = kWinHash; s_ctl[2] = static_cast<int32_t>(b); s_ctl[3] = static_cast<int32_t>(e);
+          s_ctl[4] = sum;
+          next_b = e;
+        }
+      }
+      __syncthreads();
+      const int wtype = s_ctl[1];
+      if (wtype == kWinDone) break;
+      const int64_t w0 = int64_t(s_ctl[2]) * kBlockCols;
+      const int64_t w1 = int64_t(s_ctl[3]) * kBlockCols < n ? int64_t(s_ctl[3]) * kBlockCols : n;
+      const int32_t expect = s_ctl[4];
+      // accumulate: one warp per A entry, resuming at the entry's cursor
+      for (int64_t e = wid; e < na; e += kWarps) {
+        const int32_t k = A.col[a0 + e];
+        const double av = av_[a0 + e];
+        const int64_t bstart = B.rp[k], bend = B.rp[k + 1];
+        int64_t cur = first ? bstart : bstart + cursor[a0 + e];
+        while (cur < bend) {
+          const int64_t j = cur + lane;
+          const int32_t c = j < bend ? B.col[j] : kNoCol;
+          const bool ok = c < w1;
+          if (ok && c < w0) {
+            set_error(err, kErrWindowPlan);   // an entry left behind by a skipped block
+          } else if (ok) {
+            const double v = av * bv_[j];
+            const int32_t rel = static_cast<int32_t>(c - w0);
+            if (wtype == kWinDense) {
+              atomicAdd(&dense[rel], v);
+              atomicOr(&bm[rel >> 5], 1u << (rel & 31));
+            } else {
+              const int32_t key = c + 1;
+              uint32_t h = hash_slot(key, kHashWinLog2);
+              for (int probe = 0; probe < kHashWinSlots; ++probe) {
+                const int32_t cur_key = *reinterpret_cast<volatile int32_t*>(&hkeys[h]);
+                if (cur_key == key) { atomicAdd(&hvals[h], v); break; }
+                if (cur_key == 0) {
+                  const int32_t old = atomicCAS(&hkeys[h], 0, key);
+                  if (old == 0 || old == key) { atomicAdd(&hvals[h], v); break; }
+                }
+                h = (h + 1) & (kHashWinSlots - 1);
+                if (probe == kHashWinSlots - 1) set_error(err, kErrHashFull);
+              }
+            }
+          }
+          const int got = __popc(__ballot_sync(0xffffffffu, ok));
+          cur += got;
+          if (got < 32) break;
+        }
+        if (lane == 0) cursor[a0 + e] = static_cast<int32_t>(cur - bstart);
+      }
+      __syncthreads();
+      int64_t tot = 0;
+      if (wtype == kWinDense) {
+        const int nwords = static_cast<int>((w1 - w0 + 31) >> 5);
+        const uint32_t word = threadIdx.x < nwords ? bm[threadIdx.x] : 0u;
+        const int64_t pos = block_excl_scan<int64_t>(__popc(word), s_scan, &tot);
+        if (word) {
+          int64_t o = out + pos;
+          for (uint32_t m = word; m; m &= m - 1) {
+            const int bit = __ffs(m) - 1;
+            const int rel = threadIdx.x * 32 + bit;
+            if (o < out_end) {
+              ccol[o] = static_cast<int32_t>(w0 + rel);
+              cval[o] = dense[rel];
+            }
+            dense[rel] = 0.0;
+            ++o;
+          }
+          bm[threadIdx.x] = 0u;
+        }
+      } else {
+        // mark the occupied columns in the bitmap, then walk it in column order
+        for (int s = threadIdx.x; s < kHashWinSlots; s += kWinThreads) {
+          const int32_t key = hkeys[s];
+          if (key) {
+            const int32_t rel = static_cast<int32_t>(key - 1 - w0);
+            atomicOr(&bm[rel >> 5], 1u << (rel & 31));
+          }
+        }
+        __syncthreads();
+        const int nwords = static_cast<int>((w1 - w0 + 31) >> 5);
+        constexpr int kPer = kWinBitmapWords / kWinThreads;   // 16 words per thread
+        const int wlo = threadIdx.x * kPer;
+        int c = 0;
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) c += (wlo + t < nwords) ? __popc(bm[wlo + t]) : 0;
+        const int64_t pos = block_excl_scan<int64_t>(c, s_scan, &tot);
+        int64_t o = out + pos;
+        for (int t = 0; t < kPer; ++t) {
+          if (wlo + t >= nwords) break;
+          uint32_t m = bm[wlo + t];
+          if (!m) continue;
+          bm[wlo + t] = 0u;
+          for (; m; m &= m - 1) {
+            const int rel = (wlo + t) * 32 + (__ffs(m) - 1);
+            const int32_t key = static_cast<int32_t>(w0 + rel) + 1;
+            uint32_t h = hash_slot(key, kHashWinLog2);
+            double v = 0.0;
+            for (int probe = 0; probe < kHashWinSlots; ++probe) {
+              if (hkeys[h] == key) { v = hvals[h]; break; }
+              h = (h + 1) & (kHashWinSlots - 1);
+            }
+            if (o < out_end) {
+              ccol[o] = key - 1;
+              cval[o] = v;
+            }
+            ++o;
+          }
+        }
+        __syncthreads();
+        for (int s = threadIdx.x; s < kHashWinSlots; s += kWinThreads) { hkeys[s] = 0; hvals[s] = 0.0; }
+      }
+      if (threadIdx.x == 0 && tot != expect) set_error(err, kErrCount);
+      out += tot;
+      first = false;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0 && out != out_end) set_error(err, kErrCount);
+  }
+}
+
+inline unsigned grid_rows(int64_t count, int rows_per_block, int max_blocks) {
+  int64_t g = (count + rows_per_block - 1) / rows_per_block;
+  if (g > max_blocks) g = max_blocks;
+  if (g < 1) g = 1;
+  return static_cast<unsigned>(g);
+}
+
+}  // namespace
+
+void launch_num_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                     const int64_t* c_off, int32_t* ccol, double* cval, uint32_t* err,
+                     cudaStream_t s) {
+  if (count <= 0) return;
+  k_num_tiny<<<grid_rows(count, 8, 152 * 64), 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, err);
+}
+
+void launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+                     int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
+                     uint32_t* err, cudaStream_t s) {
+  if (count <= 0) return;
+  const unsigned g = grid_rows(count, 8, 152 * 32);
+  const size_t sm = size_t(8) * (size_t(1) << log2S) * 12;
+  switch (log2S) {
+    case 6: k_num_warp<6><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, err); break;
+    case 8: k_num_warp<8><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, err); break;
+    case 10:
+      cudaFuncSetAttribute(k_num_warp<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+      k_num_warp<10><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, err);
+      break;
+    default: break;
+  }
+}
+
+void launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+                      int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
+                      uint32_t* err, cudaStream_t s) {
+  if (count <= 0) return;
+  const size_t sm = (size_t(1) << log2S) * 12;
+  if (log2S == 11) {
+    k_num_block<11, 256><<<grid_rows(count, 1, 152 * 8), 256, sm, s>>>(A, B, perm, count, c_off, ccol,
+                                                                       cval, err);
+  } else if (log2S == 13) {
+    cudaFuncSetAttribute(k_num_block<13, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    k_num_block<13, 512><<<grid_rows(count, 1, 152 * 4), 512, sm, s>>>(A, B, perm, count, c_off, ccol,
+                                                                       cval, err);
+  }
+}
+
+void launch_num_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                       int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
+                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, int32_t* cursor,
+                       int32_t hash_fill, int32_t* ccol, double* cval, int num_sms,
+                       uint32_t* err, cudaStream_t s) {
+  if (count <= 0) return;
+  cudaFuncSetAttribute(k_num_window, cudaFuncAttributeMaxDynamicSharedMemorySize, kWinSmemBytes);
+  cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+  const int64_t g = count < num_sms ? count : num_sms;
+  k_num_window<<<static_cast<unsigned>(g), kWinThreads, kWinSmemBytes, s>>>(
+      A, B, perm, count, counter, c_off, win_slot, blockcnt, nblocks, nslots, cursor, hash_fill, ccol, cval,
+      err);
+}
+
+}  // namespace spg

@@ -1,0 +1,325 @@
+// Plan-phase and scan kernels: CSR validation, the per-row product count, the
+// class histogram scan, the class scatter that groups rows by work, and the row-offset
+// scan of C after the symbolic pass.
+//
+// The count is the number of partial products Algorithm 1 forms for row i (Sec. III-A):
+// P_i = sum over the stored columns k of row i of A of nnz(row k of B), i.e. only the B
+// rows named by row i are "streamed" (Sec. III-A, selective streaming of B rows).
+// Grouping rows by P_i on the device plays the role of the CPU-side scheduling of RIR
+// bundles (Sec. II, "RIR includes scheduling"; Sec. III-A, long rows split into bundles):
+// every row class gets a kernel shaped for its size.
+#include "kernels.h"
+
+namespace spg {
+
+namespace {
+
+__global__ void k_rowptr_to64(const int32_t* __restrict__ in, int64_t* __restrict__ out, int64_t n1) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n1;
+       i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = in[i];
+}
+
+// One warp per row: row pointers in range and non-decreasing, columns strictly increasing
+// in [0, cols). Any violation sets kErrInvalidCsr.
+__global__ void k_validate(DevCsr M, uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  if (warp0 == 0 && lane == 0) {
+    if (M.rp[0] != 0 || M.rp[M.rows] != M.nnz) set_error(err, kErrInvalidCsr);
+  }
+  for (int64_t i = warp0; i < M.rows; i += nwarps) {
+    const int64_t s = M.rp[i], e = M.rp[i + 1];
+    bool bad = (s < 0) || (e < s) || (e > M.nnz);
+    if (__any_sync(0xffffffffu, bad)) {
+      if (lane == 0) set_error(err, kErrInvalidCsr);
+      continue;
+    }
+    for (int64_t j = s + lane; j < e; j += 32) {
+      const int32_t c = M.col[j];
+      bool b = (c < 0) || (c >= M.cols);
+      if (j > s) b = b || (M.col[j - 1] >= c);
+      if (b) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(err, kErrInvalidCsr);
+  }
+}
+
+// Warp-aggregated increment of a shared counter per class; returns this lane's slot.
+__device__ __forceinline__ int32_t aggregated_slot(int32_t* counters, int cls, bool valid) {
+  const unsigned lane = lane_id();
+  const unsigned peers = __match_any_sync(0xffffffffu, valid ? cls : 1000 + static_cast<int>(lane));
+  const int leader = __ffs(peers) - 1;
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  int32_t base = 0;
+  if (valid && static_cast<int>(lane) == leader) base = atomicAdd(&counters[cls], __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return base + rank;
+}
+
+// P_i for a tile of kTileRows rows (256 threads, four rows each). Short rows are summed
+// by their own thread, rows with more than 64 entries by the whole warp.
+__global__ void __launch_bounds__(256) k_count(DevCsr A, DevCsr B, ClassParams cp, int64_t* P,
+                                               int32_t* nnz_row, int32_t* tile_hist,
+                                               int64_t* tile_sum, int64_t* tile_max) {
+  __shared__ int32_t hist[kMaxClasses];
+  __shared__ unsigned long long s_sum, s_max;
+  if (threadIdx.x < kMaxClasses) hist[threadIdx.x] = 0;
+  if (threadIdx.x == 0) { s_sum = 0; s_max = 0; }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t t = blockIdx.x;
+  unsigned long long my_sum = 0, my_max = 0;
+  for (int r = 0; r < kTileRows / 256; ++r) {
+    const int64_t row = t * kTileRows + r * 256 + threadIdx.x;
+    const bool valid = row < A.rows;
+    int64_t a0 = 0, na = 0;
+    if (valid) { a0 = A.rp[row]; na = A.rp[row + 1] - a0; }
+    int64_t p = 0;
+    const bool longrow = valid && na > 64;
+    if (valid && !longrow) {
+      for (int64_t j = 0; j < na; ++j) {
+        const int32_t k = A.col[a0 + j];
+        p += B.rp[k + 1] - B.rp[k];
+      }
+    }
+    unsigned lm = __ballot_sync(0xffffffffu, longrow);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int64_t sa0 = __shfl_sync(0xffffffffu, a0, src);
+      const int64_t sna = __shfl_sync(0xffffffffu, na, src);
+      int64_t acc = 0;
+      for (int64_t j = lane; j < sna; j += 32) {
+        const int32_t k = A.col[sa0 + j];
+        acc += B.rp[k + 1] - B.rp[k];
+      }
+      acc = warp_sum(acc);
+      if (lane == src) p = acc;
+    }
+    int cls = kSymZero;
+    if (valid) {
+      const int32_t na32 = na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na);
+      cls = sym_class(p, na32, cp);
+      P[row] = p;
+      if (cls == kSymZero) nnz_row[row] = 0;
+      my_sum += static_cast<unsigned long long>(p);
+      my_max = my_max > static_cast<unsigned long long>(p) ? my_max : static_cast<unsigned long long>(p);
+    }
+    aggregated_slot(hist, cls, valid);
+  }
+  my_sum = warp_sum(my_sum);
+  my_max = warp_min(~my_max);
+  my_max = ~my_max;
+  if (lane == 0) {
+    atomicAdd(&s_sum, my_sum);
+    atomicMax(&s_max, my_max);
+  }
+  __syncthreads();
+  if (threadIdx.x < kMaxClasses) tile_hist[t * kMaxClasses + threadIdx.x] = hist[threadIdx.x];
+  if (threadIdx.x == 0) {
+    tile_sum[t] = static_cast<int64_t>(s_sum);
+    if (tile_max) tile_max[t] = static_cast<int64_t>(s_max);
+  }
+}
+
+// One block: turns the per-tile class counts into per-tile base offsets (in place),
+// writes the class offsets, and scans the per-tile sums. Warp c handles class c.
+__global__ void __launch_bounds__(544) k_class_scan(int64_t ntiles, int nclasses, int32_t* tile_hist,
+                                                    const int64_t* tile_sum, const int64_t* tile_max,
+                                                    int64_t* tile_sum_off, Summary* summary) {
+  __shared__ int64_t tot[kMaxClasses];
+  __shared__ int64_t off[kMaxClasses + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w < nclasses) {
+    int64_t s = 0;
+    for (int64_t t = lane; t < ntiles; t += 32) s += tile_hist[t * kMaxClasses + w];
+    s = warp_sum(s);
+    if (lane == 0) tot[w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t o = 0;
+    for (int c = 0; c < nclasses; ++c) { off[c] = o; summary->class_off[c] = o; o += tot[c]; }
+    for (int c = nclasses; c <= kMaxClasses; ++c) { off[c] = o; summary->class_off[c] = o; }
+  }
+  __syncthreads();
+  if (w < nclasses) {
+    int64_t run = off[w];
+    for (int64_t t0 = 0; t0 < ntiles; t0 += 32) {
+      const int64_t t = t0 + lane;
+      const int64_t v = t < ntiles ? tile_hist[t * kMaxClasses + w] : 0;
+      const int64_t incl = warp_incl_scan(v);
+      if (t < ntiles) tile_hist[t * kMaxClasses + w] = static_cast<int32_t>(run + incl - v);
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  } else if (w == kMaxClasses) {
+    int64_t run = 0, mx = 0;
+    for (int64_t t0 = 0; t0 < ntiles; t0 += 32) {
+      const int64_t t = t0 + lane;
+      const int64_t v = t < ntiles ? tile_sum[t] : 0;
+      if (tile_max && t < ntiles) mx = mx > tile_max[t] ? mx : tile_max[t];
+      const int64_t incl = warp_incl_scan(v);
+      if (tile_sum_off && t < ntiles) tile_sum_off[t] = run + incl - v;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    mx = ~warp_min(~mx);
+    if (lane == 0) {
+      summary->total = run;
+      summary->max_row = mx;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scatter_sym(DevCsr A, ClassParams cp, const int64_t* P,
+                                                     const int32_t* tile_hist, int32_t* perm) {
+  __shared__ int32_t base[kMaxClasses];
+  const int64_t t = blockIdx.x;
+  if (threadIdx.x < kMaxClasses) base[threadIdx.x] = tile_hist[t * kMaxClasses + threadIdx.x];
+  __syncthreads();
+  for (int r = 0; r < kTileRows / 256; ++r) {
+    const int64_t row = t * kTileRows + r * 256 + threadIdx.x;
+    const bool valid = row < A.rows;
+    int cls = 0;
+    if (valid) {
+      const int64_t na = A.rp[row + 1] - A.rp[row];
+      cls = sym_class(P[row], na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na), cp);
+    }
+    const int32_t pos = aggregated_slot(base, cls, valid);
+    if (valid) perm[pos] = static_cast<int32_t>(row);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_num_tiles(DevCsr A, ClassParams cp, const int64_t* P,
+                                                   const int32_t* nnz_row, int32_t* tile_hist,
+                                                   int64_t* tile_sum) {
+  __shared__ int32_t hist[kMaxClasses];
+  __shared__ unsigned long long s_sum;
+  if (threadIdx.x < kMaxClasses) hist[threadIdx.x] = 0;
+  if (threadIdx.x == 0) s_sum = 0;
+  __syncthreads();
+  const int64_t t = blockIdx.x;
+  unsigned long long my = 0;
+  for (int r = 0; r < kTileRows / 256; ++r) {
+    const int64_t row = t * kTileRows + r * 256 + threadIdx.x;
+    const bool valid = row < A.rows;
+    int cls = 0;
+    if (valid) {
+      const int64_t na = A.rp[row + 1] - A.rp[row];
+      const int32_t z = nnz_row[row];
+      cls = num_class(P[row], na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na), z, cp);
+      my += static_cast<unsigned long long>(z);
+    }
+    aggregated_slot(hist, cls, valid);
+  }
+  my = warp_sum(my);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&s_sum, my);
+  __syncthreads();
+  if (threadIdx.x < kMaxClasses) tile_hist[t * kMaxClasses + threadIdx.x] = hist[threadIdx.x];
+  if (threadIdx.x == 0) tile_sum[t] = static_cast<int64_t>(s_sum);
+}
+
+// Row offsets of C (exclusive scan of nnz(C_i), int64) and the numeric class scatter.
+__global__ void __launch_bounds__(256) k_scatter_num(DevCsr A, ClassParams cp, const int64_t* P,
+                                                     const int32_t* nnz_row, const int32_t* tile_hist,
+                                                     const int64_t* tile_sum_off, int32_t* perm,
+                                                     int64_t* c_off) {
+  __shared__ int32_t base[kMaxClasses];
+  __shared__ int64_t scratch[33];
+  const int64_t t = blockIdx.x;
+  if (threadIdx.x < kMaxClasses) base[threadIdx.x] = tile_hist[t * kMaxClasses + threadIdx.x];
+  __syncthreads();
+  int64_t carry = tile_sum_off[t];
+  for (int r = 0; r < kTileRows / 256; ++r) {
+    const int64_t row = t * kTileRows + r * 256 + threadIdx.x;
+    const bool valid = row < A.rows;
+    int cls = 0;
+    int64_t z = 0;
+    if (valid) {
+      const int64_t na = A.rp[row + 1] - A.rp[row];
+      z = nnz_row[row];
+      cls = num_class(P[row], na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na),
+                      static_cast<int32_t>(z), cp);
+    }
+    int64_t tot;
+    const int64_t ex = block_excl_scan<int64_t>(z, scratch, &tot);
+    if (valid) {
+      c_off[row] = carry + ex;
+      if (row == A.rows - 1) c_off[A.rows] = carry + ex + z;
+    }
+    carry += tot;
+    const int32_t pos = aggregated_slot(base, cls, valid);
+    if (valid) perm[pos] = static_cast<int32_t>(row);
+  }
+}
+
+__global__ void k_write_rowptr(const int64_t* __restrict__ c_off, int64_t m1, void* out, int idx64) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m1;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    if (idx64) static_cast<int64_t*>(out)[i] = c_off[i];
+    else static_cast<int32_t*>(out)[i] = static_cast<int32_t>(c_off[i]);
+  }
+}
+
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 65535LL * 16) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return static_cast<unsigned>(g);
+}
+
+}  // namespace
+
+void launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t s) {
+  k_rowptr_to64<<<grid_for(n1, 256), 256, 0, s>>>(in, out, n1);
+}
+
+void launch_validate(const DevCsr& M, uint32_t* err, cudaStream_t s) {
+  const int64_t warps = M.rows > 0 ? M.rows : 1;
+  k_validate<<<grid_for(warps * 32, 256), 256, 0, s>>>(M, err);
+}
+
+void launch_count(const DevCsr& A, const DevCsr& B, ClassParams cp, int64_t* P, int32_t* nnz_row,
+                  int32_t* tile_hist, int64_t* tile_sum, int64_t* tile_max, cudaStream_t s) {
+  const int64_t ntiles = (A.rows + kTileRows - 1) / kTileRows;
+  if (ntiles == 0) return;
+  k_count<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, B, cp, P, nnz_row, tile_hist, tile_sum,
+                                                        tile_max);
+}
+
+void launch_class_scan(int64_t ntiles, int nclasses, int32_t* tile_hist, const int64_t* tile_sum,
+                       const int64_t* tile_max, int64_t* tile_sum_off, Summary* summary,
+                       cudaStream_t s) {
+  k_class_scan<<<1, 544, 0, s>>>(ntiles, nclasses, tile_hist, tile_sum, tile_max, tile_sum_off,
+                                 summary);
+}
+
+void launch_scatter_sym(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* tile_hist,
+                        int32_t* perm, cudaStream_t s) {
+  const int64_t ntiles = (A.rows + kTileRows - 1) / kTileRows;
+  if (ntiles == 0) return;
+  k_scatter_sym<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, cp, P, tile_hist, perm);
+}
+
+void launch_num_tiles(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* nnz_row,
+                      int32_t* tile_hist, int64_t* tile_sum, cudaStream_t s) {
+  const int64_t ntiles = (A.rows + kTileRows - 1) / kTileRows;
+  if (ntiles == 0) return;
+  k_num_tiles<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, cp, P, nnz_row, tile_hist, tile_sum);
+}
+
+void launch_scatter_num(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* nnz_row,
+                        const int32_t* tile_hist, const int64_t* tile_sum_off, int32_t* perm,
+                        int64_t* c_off, cudaStream_t s) {
+  const int64_t ntiles = (A.rows + kTileRows - 1) / kTileRows;
+  if (ntiles == 0) return;
+  k_scatter_num<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, cp, P, nnz_row, tile_hist,
+                                                              tile_sum_off, perm, c_off);
+}
+
+void launch_write_rowptr(const int64_t* c_off, int64_t m1, void* out, int idx64, cudaStream_t s) {
+  k_write_rowptr<<<grid_for(m1, 256), 256, 0, s>>>(c_off, m1, out, idx64);
+}
+
+}  // namespace spg

@@ -1,0 +1,270 @@
+// Symbolic pass: nnz(C_i) = |union over the stored k of row i of A of cols(B_k)|,
+// the size of the COLB set Algorithm 1 builds for row i (Sec. III-A).
+//
+// Row classes (chosen by the plan from P_i and min(P_i, n)):
+//  * tiny  : P_i <= 32, one warp, each lane holds one column; duplicates are found with a
+//            warp match, so no shared table is needed;
+//  * warp  : one warp per row, a shared-memory hash table of 128 / 512 / 2048 keys;
+//  * block : one block per row, a shared-memory hash table of 8192 keys;
+//  * window: one persistent block per row, a shared-memory bitmap of up to 2^20 columns.
+//            Besides nnz(C_i) it records how many columns of C_i fall in each block of
+//            kBlockCols columns, which the numeric pass uses to plan its windows. When B has
+//            more than 2^20 columns the bitmap slides over the columns in windows and a
+//            per-entry cursor in global memory remembers where each B row stopped.
+// Hash tables are sized to at least twice the row's upper bound min(P_i, n), so probing
+// always ends; a probe count over the table size still reports kErrHashFull.
+#include "enumerate.cuh"
+
+namespace spg {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_sym_tiny(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
+                                                  int64_t count, int32_t* __restrict__ nnz_row) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = gw; r < count; r += nw) {
+    const int32_t i = perm[r];
+    const int64_t a0 = A.rp[i];
+    const int32_t na = static_cast<int32_t>(A.rp[i + 1] - a0);
+    int32_t col = -2 - lane;
+    int32_t total = 0;
+    int32_t len = 0;
+    int64_t bs = 0;
+    if (lane < na) {
+      const int32_t k = A.col[a0 + lane];
+      bs = B.rp[k];
+      len = static_cast<int32_t>(B.rp[k + 1] - bs);
+    }
+    const int32_t incl = warp_incl_scan(len);
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int32_t v = __shfl_sync(0xffffffffu, incl, o + step - 1);
+      if (v <= lane) o += step;
+    }
+    const int32_t incl_o = __shfl_sync(0xffffffffu, incl, o & 31);
+    const int32_t len_o = __shfl_sync(0xffffffffu, len, o & 31);
+    const int64_t bs_o = __shfl_sync(0xffffffffu, bs, o & 31);
+    if (lane < total) col = B.col[bs_o + (lane - (incl_o - len_o))];
+    const unsigned peers = __match_any_sync(0xffffffffu, col);
+    const bool lead = lane < total && (__ffs(peers) - 1) == lane;
+    const int n = __popc(__ballot_sync(0xffffffffu, lead));
+    if (lane == 0) nnz_row[i] = n;
+  }
+}
+
+// Insert `key` into an open-addressing table (linear probing). Returns 1 if it was new.
+template <int LOG2S>
+__device__ __forceinline__ int insert_key(int32_t* table, int32_t key, uint32_t* err) {
+  constexpr int S = 1 << LOG2S;
+  uint32_t h = hash_slot(key, LOG2S);
+  for (int probe = 0; probe < S; ++probe) {
+    const int32_t cur = *reinterpret_cast<volatile int32_t*>(&table[h]);
+    if (cur == key) return 0;
+    if (cur == kEmpty) {
+      const int32_t old = atomicCAS(&table[h], kEmpty, key);
+      if (old == kEmpty) return 1;
+      if (old == key) return 0;
+    }
+    h = (h + 1) & (S - 1);
+  }
+  set_error(err, kErrHashFull);
+  return 0;
+}
+
+template <int LOG2S>
+__global__ void __launch_bounds__(256) k_sym_warp(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
+                                                  int64_t count, int32_t* __restrict__ nnz_row,
+                                                  uint32_t* err) {
+  constexpr int S = 1 << LOG2S;
+  extern __shared__ int32_t smem_i32[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* table = smem_i32 + wid * S;
+  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = gw; r < count; r += nw) {
+    const int32_t i = perm[r];
+    const int64_t a0 = A.rp[i];
+    const int64_t na = A.rp[i + 1] - a0;
+    for (int s = lane; s < S; s += 32) table[s] = kEmpty;
+    __syncwarp();
+    int cnt = 0;
+    warp_for_each_product(A, B, a0, na, [&](int64_t j, int64_t) {
+      cnt += insert_key<LOG2S>(table, B.col[j], err);
+    });
+    cnt = warp_sum(cnt);
+    if (lane == 0) nnz_row[i] = cnt;
+    __syncwarp();
+  }
+}
+
+template <int LOG2S, int NT>
+__global__ void __launch_bounds__(NT) k_sym_block(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
+                                                  int64_t count, int32_t* __restrict__ nnz_row,
+                                                  uint32_t* err) {
+  constexpr int S = 1 << LOG2S;
+  extern __shared__ int32_t smem_i32[];
+  int32_t* table = smem_i32;
+  __shared__ int32_t s_excl[NT];
+  __shared__ int64_t s_bs[NT];
+  __shared__ int32_t s_scan[33];
+  __shared__ int32_t s_cnt;
+  for (int64_t r = blockIdx.x; r < count; r += gridDim.x) {
+    const int32_t i = perm[r];
+    const int64_t a0 = A.rp[i];
+    const int64_t na = A.rp[i + 1] - a0;
+    for (int s = threadIdx.x; s < S; s += NT) table[s] = kEmpty;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    int cnt = 0;
+    block_for_each_product<NT>(A, B, a0, na, s_excl, s_bs, s_scan, [&](int64_t j, int64_t) {
+      cnt += insert_key<LOG2S>(table, B.col[j], err);
+    });
+    cnt = warp_sum(cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) nnz_row[i] = s_cnt;
+    __syncthreads();
+  }
+}
+
+// Windowed symbolic pass, one row per block at a time (rows handed out by an atomic
+// counter, heaviest class first).
+__global__ void __launch_bounds__(kWinThreads, 1) k_sym_window(DevCsr A, DevCsr B,
+                                                               const int32_t* __restrict__ perm,
+                                                               int64_t count, int32_t* counter,
+                                                               int32_t* __restrict__ nnz_row,
+                                                               int32_t* __restrict__ win_slot,
+                                                               uint16_t* __restrict__ blockcnt,
+                                                               int64_t nblocks, int32_t* cursor,
+                                                               uint32_t* err) {
+  extern __shared__ uint32_t bm[];  // kSymWinBits / 32 words
+  __shared__ int32_t s_excl[kWinThreads];
+  __shared__ int64_t s_bs[kWinThreads];
+  __shared__ int32_t s_scan[33];
+  __shared__ int32_t s_idx;
+  __shared__ unsigned long long s_total;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int kWarps = kWinThreads / 32;
+  const int64_t n = B.cols;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_idx = atomicAdd(counter, 1);
+      s_total = 0;
+    }
+    __syncthreads();
+    const int64_t idx = s_idx;
+    if (idx >= count) break;
+    const int32_t i = perm[idx];
+    if (threadIdx.x == 0) win_slot[i] = static_cast<int32_t>(idx);
+    const int64_t a0 = A.rp[i];
+    const int64_t na = A.rp[i + 1] - a0;
+    uint16_t* cnts = blockcnt + idx * nblocks;
+    for (int64_t w0 = 0; w0 < n; w0 += kSymWinBits) {
+      const int64_t wend = (w0 + kSymWinBits < n) ? w0 + kSymWinBits : n;
+      const int nwords = static_cast<int>((wend - w0 + 31) >> 5);
+      for (int t = threadIdx.x; t < nwords; t += kWinThreads) bm[t] = 0u;
+      __syncthreads();
+      if (n <= kSymWinBits) {
+        // one window covers every column: no cursors, products handed out flattened
+        block_for_each_product<kWinThreads>(A, B, a0, na, s_excl, s_bs, s_scan, [&](int64_t j, int64_t) {
+          const int32_t c = B.col[j];
+          atomicOr(&bm[c >> 5], 1u << (c & 31));
+        });
+      } else {
+        for (int64_t e = wid; e < na; e += kWarps) {
+          const int32_t k = A.col[a0 + e];
+          const int64_t bstart = B.rp[k], bend = B.rp[k + 1];
+          int64_t cur = (w0 == 0) ? bstart : bstart + cursor[a0 + e];
+          while (cur < bend) {
+            const int64_t j = cur + lane;
+            const int32_t c = j < bend ? B.col[j] : kNoCol;
+            const bool ok = c < wend;
+            if (ok && c >= w0) atomicOr(&bm[(c - w0) >> 5], 1u << ((c - w0) & 31));
+            const int got = __popc(__ballot_sync(0xffffffffu, ok));
+            cur += got;
+            if (got < 32) break;
+          }
+          if (lane == 0) cursor[a0 + e] = static_cast<int32_t>(cur - bstart);
+        }
+        __syncthreads();
+      }
+      // per-block counts of this window (warp per block of kBlockWords words)
+      const int64_t b0 = w0 / kBlockCols;
+      const int64_t b1 = (wend + kBlockCols - 1) / kBlockCols;
+      for (int64_t b = b0 + wid; b < b1; b += kWarps) {
+        const int wlo = static_cast<int>(b * kBlockWords - (w0 >> 5));
+        const int whi = wlo + kBlockWords < nwords ? wlo + kBlockWords : nwords;
+        int c = 0;
+        for (int t = wlo + lane; t < whi; t += 32) c += __popc(bm[t]);
+        c = warp_sum(c);
+        if (lane == 0) {
+          cnts[b] = static_cast<uint16_t>(c);
+          if (c) atomicAdd(&s_total, static_cast<unsigned long long>(c));
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) nnz_row[i] = static_cast<int32_t>(s_total);
+    __syncthreads();
+  }
+}
+
+inline unsigned grid_rows(int64_t count, int rows_per_block, int max_blocks) {
+  int64_t g = (count + rows_per_block - 1) / rows_per_block;
+  if (g > max_blocks) g = max_blocks;
+  if (g < 1) g = 1;
+  return static_cast<unsigned>(g);
+}
+
+}  // namespace
+
+void launch_sym_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                     int32_t* nnz_row, cudaStream_t s) {
+  if (count <= 0) return;
+  k_sym_tiny<<<grid_rows(count, 8, 152 * 64), 256, 0, s>>>(A, B, perm, count, nnz_row);
+}
+
+void launch_sym_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+                     int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s) {
+  if (count <= 0) return;
+  const unsigned g = grid_rows(count, 8, 152 * 32);
+  const size_t sm = size_t(8) << log2S << 2;
+  switch (log2S) {
+    case 7: k_sym_warp<7><<<g, 256, sm, s>>>(A, B, perm, count, nnz_row, err); break;
+    case 9: k_sym_warp<9><<<g, 256, sm, s>>>(A, B, perm, count, nnz_row, err); break;
+    case 11:
+      cudaFuncSetAttribute(k_sym_warp<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+      k_sym_warp<11><<<g, 256, sm, s>>>(A, B, perm, count, nnz_row, err);
+      break;
+    default: break;
+  }
+}
+
+void launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+                      int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s) {
+  if (count <= 0) return;
+  const size_t sm = size_t(4) << log2S;
+  if (log2S == 13) {
+    k_sym_block<13, 512><<<grid_rows(count, 1, 152 * 8), 512, sm, s>>>(A, B, perm, count, nnz_row, err);
+  }
+}
+
+void launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                       int32_t* counter, int32_t* nnz_row, int32_t* win_slot, uint16_t* blockcnt,
+                       int64_t nblocks, int32_t* cursor, int num_sms, uint32_t* err,
+                       cudaStream_t s) {
+  if (count <= 0) return;
+  const size_t sm = size_t(kSymWinBits / 32) * 4;
+  cudaFuncSetAttribute(k_sym_window, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+  const int64_t g = count < num_sms ? count : num_sms;
+  k_sym_window<<<static_cast<unsigned>(g), kWinThreads, sm, s>>>(A, B, perm, count, counter, nnz_row,
+                                                                 win_slot, blockcnt, nblocks, cursor,
+                                                                 err);
+}
+
+}  // namespace spg

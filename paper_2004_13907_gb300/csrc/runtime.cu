@@ -1,0 +1,192 @@
+// Pass drivers: the launch sequence of plan (validate, count, class scan, scatter),
+// symbolic (per-class symbolic kernels, row-offset scan, numeric classes) and numeric
+// (per-class numeric kernels). Two host synchronisations per product: after the plan
+// (class sizes, sum of P_i) and after the symbolic pass (nnz(C), so the caller can
+// allocate C).
+#include <cstring>
+
+#include "runtime.h"
+
+namespace spg {
+
+namespace {
+
+template <typename T>
+T* ws_get(spgemm_plan_s* p, int64_t count, spgemm_status* st) {
+  if (*st != SPGEMM_OK) return nullptr;
+  void* ptr = p->ws.get(static_cast<size_t>(count < 1 ? 1 : count) * sizeof(T));
+  if (!ptr) *st = set_error_msg(SPGEMM_ERR_OOM, "device workspace allocation of %lld bytes failed",
+                                (long long)(count * (int64_t)sizeof(T)));
+  return static_cast<T*>(ptr);
+}
+
+spgemm_status read_summary(spgemm_plan_s* p, Summary* h, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(h, p->summary, sizeof(Summary), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e, "reading the pass summary");
+  return SPGEMM_OK;
+}
+
+spgemm_status error_bits_status(uint32_t err) {
+  if (err & kErrInvalidCsr)
+    return set_error_msg(SPGEMM_ERR_INVALID_CSR, "an input is not canonical CSR (row pointers or column indices)");
+  if (err & kErrTimeout) return set_error_msg(SPGEMM_ERR_TIMEOUT, "a device wait gave up");
+  if (err) return set_error_msg(SPGEMM_ERR_INTERNAL, "device consistency check failed (error bits 0x%x)", err);
+  return SPGEMM_OK;
+}
+
+int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+}  // namespace
+
+spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s) {
+  Summary h;
+  spgemm_status st = read_summary(p, &h, s);
+  if (st != SPGEMM_OK) return st;
+  return error_bits_status(h.err);
+}
+
+spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                       cudaStream_t s) {
+  spgemm_status st = SPGEMM_OK;
+  const int64_t m = A->rows, n = B->cols;
+  p->num_sms = device_sm_count();
+  // internal int64 row pointers
+  const int64_t* arp = static_cast<const int64_t*>(A->row_ptr);
+  const int64_t* brp = static_cast<const int64_t*>(B->row_ptr);
+  if (!A->idx64_rowptr) {
+    int64_t* t = ws_get<int64_t>(p, m + 1, &st);
+    if (st) return st;
+    launch_rowptr_to64(static_cast<const int32_t*>(A->row_ptr), t, m + 1, s);
+    arp = t;
+  }
+  if (!B->idx64_rowptr) {
+    int64_t* t = ws_get<int64_t>(p, B->rows + 1, &st);
+    if (st) return st;
+    launch_rowptr_to64(static_cast<const int32_t*>(B->row_ptr), t, B->rows + 1, s);
+    brp = t;
+  }
+  p->A = DevCsr{m, A->cols, A->nnz, arp, A->col, A->val};
+  p->B = DevCsr{B->rows, n, B->nnz, brp, B->col, B->val};
+  const spgemm_opts& o = p->opts;
+  p->cp.n = n;
+  p->cp.tiny_max = clampi(o.tiny_max, 0, 32);
+  p->cp.warp_max = clampi(o.warp_max, 0, 1024);
+  p->cp.block_max = clampi(o.block_max, p->cp.warp_max > 32 ? p->cp.warp_max : 32, 4096);
+  p->cp.force_window = o.force_window ? 1 : 0;
+  if (o.window_hash_fill < 1 || o.window_hash_fill > (kHashWinSlots * 3) / 4)
+    p->opts.window_hash_fill = 4800;
+
+  p->ntiles = (m + kTileRows - 1) / kTileRows;
+  p->summary = ws_get<Summary>(p, 1, &st);
+  p->counters = ws_get<int32_t>(p, 16, &st);
+  p->P = ws_get<int64_t>(p, m, &st);
+  p->nnz_row = ws_get<int32_t>(p, m, &st);
+  p->perm_s = ws_get<int32_t>(p, m, &st);
+  p->perm_n = ws_get<int32_t>(p, m, &st);
+  p->c_off = ws_get<int64_t>(p, m + 1, &st);
+  p->tile_hist = ws_get<int32_t>(p, p->ntiles * kMaxClasses, &st);
+  p->tile_sum = ws_get<int64_t>(p, p->ntiles, &st);
+  p->tile_max = ws_get<int64_t>(p, p->ntiles, &st);
+  p->tile_sum_off = ws_get<int64_t>(p, p->ntiles, &st);
+  if (st) return st;
+  cudaMemsetAsync(p->summary, 0, sizeof(Summary), s);
+  cudaMemsetAsync(p->c_off, 0, sizeof(int64_t), s);
+
+  Summary h;
+  if (o.validate) {
+    launch_validate(p->A, &p->summary->err, s);
+    launch_validate(p->B, &p->summary->err, s);
+    if ((st = cuda_status(cudaGetLastError(), "launching validation")) != SPGEMM_OK) return st;
+    if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
+    if (h.err) return error_bits_status(h.err);
+  }
+  if (m > 0) {
+    launch_count(p->A, p->B, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum, p->tile_max, s);
+    launch_class_scan(p->ntiles, kSymNumClasses, p->tile_hist, p->tile_sum, p->tile_max, nullptr,
+                      p->summary, s);
+    launch_scatter_sym(p->A, p->cp, p->P, p->tile_hist, p->perm_s, s);
+    if ((st = cuda_status(cudaGetLastError(), "launching the plan kernels")) != SPGEMM_OK) return st;
+    if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
+    if (h.err) return error_bits_status(h.err);
+    std::memcpy(p->sym_off, h.class_off, sizeof(p->sym_off));
+    p->total_products = h.total;
+    p->max_row_products = h.max_row;
+  }
+  const int64_t nwin = p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0];
+  if (nwin > 0) {
+    p->nblocks = (n + kBlockCols - 1) / kBlockCols;
+    const int64_t cnt_bytes = nwin * p->nblocks * 2;
+    if (cnt_bytes > (int64_t(8) << 30))
+      return set_error_msg(SPGEMM_ERR_UNSUPPORTED, "windowed rows need %lld bytes of block counts", (long long)cnt_bytes);
+    p->blockcnt = ws_get<uint16_t>(p, nwin * p->nblocks, &st);
+    p->win_slot = ws_get<int32_t>(p, m, &st);
+    p->cursor = ws_get<int32_t>(p, A->nnz, &st);
+    if (st) return st;
+  }
+  p->state = 0;
+  return SPGEMM_OK;
+}
+
+spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
+  spgemm_status st;
+  const int64_t m = p->A.rows;
+  auto seg = [&](int c) { return p->perm_s + p->sym_off[c]; };
+  auto cnt = [&](int c) { return p->sym_off[c + 1] - p->sym_off[c]; };
+  uint32_t* err = &p->summary->err;
+  if (m > 0) {
+    launch_sym_window(p->A, p->B, seg(kSymWin0), p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0],
+                      p->counters + 0, p->nnz_row, p->win_slot, p->blockcnt, p->nblocks, p->cursor,
+                      p->num_sms, err, s);
+    launch_sym_block(13, p->A, p->B, seg(kSymBlock), cnt(kSymBlock), p->nnz_row, err, s);
+    launch_sym_warp(11, p->A, p->B, seg(kSymWarp3), cnt(kSymWarp3), p->nnz_row, err, s);
+    launch_sym_warp(9, p->A, p->B, seg(kSymWarp2), cnt(kSymWarp2), p->nnz_row, err, s);
+    launch_sym_warp(7, p->A, p->B, seg(kSymWarp1), cnt(kSymWarp1), p->nnz_row, err, s);
+    launch_sym_tiny(p->A, p->B, seg(kSymTiny), cnt(kSymTiny), p->nnz_row, s);
+    launch_num_tiles(p->A, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum, s);
+    launch_class_scan(p->ntiles, kNumNumClasses, p->tile_hist, p->tile_sum, nullptr, p->tile_sum_off,
+                      p->summary, s);
+    launch_scatter_num(p->A, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum_off, p->perm_n,
+                       p->c_off, s);
+    if ((st = cuda_status(cudaGetLastError(), "launching the symbolic kernels")) != SPGEMM_OK) return st;
+    Summary h;
+    if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
+    if (h.err) return error_bits_status(h.err);
+    std::memcpy(p->num_off, h.class_off, sizeof(p->num_off));
+    p->nnz_c = h.total;
+  } else {
+    if ((st = cuda_status(cudaStreamSynchronize(s), "symbolic pass")) != SPGEMM_OK) return st;
+    p->nnz_c = 0;
+  }
+  p->state = 1;
+  return SPGEMM_OK;
+}
+
+spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
+  spgemm_status st;
+  const int64_t m = p->A.rows;
+  launch_write_rowptr(p->c_off, m + 1, C->row_ptr, C->idx64_rowptr, s);
+  if (p->prec != SPGEMM_F64)
+    return set_error_msg(SPGEMM_ERR_UNSUPPORTED, "this precision is not built yet");
+  if (m > 0) {
+    auto seg = [&](int c) { return p->perm_n + p->num_off[c]; };
+    auto cnt = [&](int c) { return p->num_off[c + 1] - p->num_off[c]; };
+    uint32_t* err = &p->summary->err;
+    double* cval = static_cast<double*>(C->val);
+    launch_num_window(p->A, p->B, seg(kNumWin0), p->num_off[kNumWin3 + 1] - p->num_off[kNumWin0],
+                      p->counters + 1, p->c_off, p->win_slot, p->blockcnt, p->nblocks,
+                      p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0], p->cursor,
+                      p->opts.window_hash_fill, C->col, cval, p->num_sms, err, s);
+    launch_num_block(13, p->A, p->B, seg(kNumBlock2), cnt(kNumBlock2), p->c_off, C->col, cval, err, s);
+    launch_num_block(11, p->A, p->B, seg(kNumBlock1), cnt(kNumBlock1), p->c_off, C->col, cval, err, s);
+    launch_num_warp(10, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, cval, err, s);
+    launch_num_warp(8, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, cval, err, s);
+    launch_num_warp(6, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, cval, err, s);
+    launch_num_tiny(p->A, p->B, seg(kNumTiny), cnt(kNumTiny), p->c_off, C->col, cval, err, s);
+  }
+  if ((st = cuda_status(cudaGetLastError(), "launching the numeric kernels")) != SPGEMM_OK) return st;
+  p->state = 2;
+  return SPGEMM_OK;
+}
+
+}  // namespace spg

@@ -1,0 +1,77 @@
+// Host runtime of the SpGEMM library (internal): the plan object and the pass drivers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/spgemm.h"
+#include "kernels.h"
+
+namespace spg {
+
+// Device workspace of one plan: every block comes from the caller's allocator, or from
+// cudaMallocAsync on the plan's stream, and is released in stream order.
+struct Workspace {
+  spgemm_allocator alloc{};
+  bool has_alloc = false;
+  void* stream = nullptr;
+  std::vector<void*> blocks;
+  int64_t total = 0;
+  void* get(size_t bytes);
+  void release_all();
+};
+
+spgemm_status set_error_msg(spgemm_status st, const char* fmt, ...);
+void clear_error_msg();
+spgemm_status cuda_status(cudaError_t e, const char* what);
+int device_sm_count();
+spgemm_status check_csr_in(const spgemm_csr_in* M, const char* name, spgemm_prec prec);
+
+}  // namespace spg
+
+struct spgemm_plan_s {
+  spg::DevCsr A{}, B{};
+  spgemm_prec prec = SPGEMM_F64;
+  spgemm_opts opts{};
+  spg::ClassParams cp{};
+  spg::Workspace ws;
+  int num_sms = 1;
+  int64_t ntiles = 0;
+  int64_t* P = nullptr;
+  int32_t* nnz_row = nullptr;
+  int32_t* perm_s = nullptr;
+  int32_t* perm_n = nullptr;
+  int64_t* c_off = nullptr;
+  int32_t* tile_hist = nullptr;
+  int64_t* tile_sum = nullptr;
+  int64_t* tile_max = nullptr;
+  int64_t* tile_sum_off = nullptr;
+  spg::Summary* summary = nullptr;   // device
+  int32_t* counters = nullptr;       // device, 16 ints
+  int32_t* win_slot = nullptr;
+  uint16_t* blockcnt = nullptr;
+  int64_t nblocks = 0;
+  int32_t* cursor = nullptr;
+  // FP32-compensated path
+  int32_t* rerun_flag = nullptr;     // per row: 1 = recompute in FP64
+  int32_t* rerun_list = nullptr;
+  int64_t sym_off[spg::kMaxClasses + 1] = {};
+  int64_t num_off[spg::kMaxClasses + 1] = {};
+  int64_t total_products = 0;
+  int64_t max_row_products = 0;
+  int64_t nnz_c = -1;
+  int64_t f32c_rerun_rows = 0;
+  int state = 0;
+};
+
+namespace spg {
+
+spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                       cudaStream_t s);
+spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s);
+spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s);
+spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s);
+
+}  // namespace spg

@@ -1,0 +1,254 @@
+"""CUDA path vs the CPU oracle, element by element (FP64).
+
+Structure (row_ptr, col) must be bit-equal; every value within 1e-12 * sum|a_ik*b_kj| of
+the oracle's. Every row class is exercised: by the natural size mix of the workloads and
+by forcing paths through the tuning knobs (tiny rows off, warp/block tables off, every row
+windowed, the int64 row_ptr path at a low limit).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import assert_parity, gpu_or_skip, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    gpu_or_skip()
+
+
+def opts(**kw):
+    import paper_2004_13907_gb300 as sp
+    return sp.spgemm_opts_default(**kw)
+
+
+def test_uniform_10k_full():
+    """C = A*A, A 10,000 x 10,000 at density 1e-3 (~10 per row), values U[-1,1]."""
+    A = synth.uniform_random(10_000, 10_000, 1e-3, seed=0)
+    rp, col, val, info0, info, _ = run_gpu(A, A)
+    assert info0["products"] == int(oracle.products_per_row(A, A).sum())
+    assert_parity(A, A, rp, col, val)
+
+
+@pytest.mark.parametrize("g", [1, 2, 7, 64, 300])
+def test_laplacian2d_small(g):
+    L = synth.laplacian2d(g)
+    rp, col, val, *_ = run_gpu(L, L)
+    assert_parity(L, L, rp, col, val)
+
+
+def test_laplacian2d_1024_full():
+    """The 2D Laplacian config at full size (1,048,576 rows), every entry compared."""
+    L = synth.laplacian2d(1024)
+    rp, col, val, info0, info, _ = run_gpu(L, L)
+    assert info0["products"] == 26_177_544
+    assert info["nnz_c"] == 13_611_012
+    ref = assert_parity(L, L, rp, col, val)
+    assert np.array_equal(val, ref.val)   # small exact integers: bit-exact in any order
+
+
+@pytest.mark.parametrize("scale", [10, 13, 15])
+def test_rmat_small_full(scale):
+    A = synth.rmat(scale, 16, seed=3)
+    rp, col, val, info0, info, _ = run_gpu(A, A)
+    assert_parity(A, A, rp, col, val)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(force_window=1),
+    dict(tiny_max=0),
+    dict(tiny_max=0, warp_max=0),
+    dict(warp_max=64, block_max=64),
+    dict(window_hash_fill=64),
+    dict(validate=0),
+])
+def test_forced_paths_rmat(kw):
+    A = synth.rmat(12, 16, seed=5)
+    B = synth.uniform_random(A.cols, 3000, 2e-3, seed=6)
+    rp, col, val, *_ = run_gpu(A, B, opts=opts(**kw))
+    assert_parity(A, B, rp, col, val)
+
+
+@pytest.mark.parametrize("kw", [dict(force_window=1), dict(tiny_max=0, warp_max=0), dict()])
+def test_forced_paths_uniform_rectangular(kw):
+    A = synth.uniform_random(700, 3000, 5e-3, seed=7)
+    B = synth.uniform_random(3000, 40_000, 2e-3, seed=8)
+    rp, col, val, *_ = run_gpu(A, B, opts=opts(**kw))
+    assert_parity(A, B, rp, col, val)
+
+
+def test_window_columns_beyond_one_bitmap():
+    """n > 2^20 columns: the symbolic bitmap slides over windows with cursors."""
+    n = (1 << 20) + 70_000
+    A = synth.uniform_random(300, 200, 0.05, seed=9)
+    B = synth.uniform_random(200, n, 3e-3, seed=10)
+    rp, col, val, *_ = run_gpu(A, B, opts=opts(force_window=1))
+    assert_parity(A, B, rp, col, val)
+    rp2, col2, val2, *_ = run_gpu(A, B)
+    assert_parity(A, B, rp2, col2, val2)
+
+
+def test_dense_small_n_window():
+    """Rows denser than a hash window: dense windows on a narrow B."""
+    A = synth.uniform_random(500, 400, 0.2, seed=11)
+    B = synth.uniform_random(400, 20_000, 0.05, seed=12)
+    rp, col, val, _, info, _ = run_gpu(A, B)
+    assert_parity(A, B, rp, col, val)
+
+
+def test_int64_rowptr_path():
+    A = synth.uniform_random(2000, 2000, 4e-3, seed=13)
+    rp, col, val, _, info, C = run_gpu(A, A, opts=opts(rowptr32_limit=1000), idx64_in=True)
+    assert info["needs_rowptr64"] == 1 and C.row_ptr.dtype == torch.int64
+    assert_parity(A, A, rp, col, val)
+
+
+def test_int32_output_refused_when_too_large():
+    import paper_2004_13907_gb300 as sp
+    A = synth.uniform_random(500, 500, 1e-2, seed=14)
+    dA = sp.DeviceCSR.from_host(A, "cuda")
+    plan = sp.spgemm_plan(dA, dA, "f64", opts(rowptr32_limit=100))
+    sp.spgemm_symbolic(plan)
+    C = sp.alloc_output(plan, idx64=False)
+    with pytest.raises(sp.SpgemmError) as ei:
+        sp.spgemm_numeric(plan, C)
+    assert ei.value.name == "INDEX_OVERFLOW"
+
+
+def test_identity_exact():
+    A = synth.uniform_random(3000, 2500, 3e-3, seed=15)
+    I = synth.identity(2500)
+    rp, col, val, *_ = run_gpu(A, I)
+    assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col) and np.array_equal(val, A.val)
+    I3 = synth.identity(3000)
+    rp, col, val, *_ = run_gpu(I3, A)
+    assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col) and np.array_equal(val, A.val)
+
+
+def test_cancellation_and_stored_zeros():
+    A = synth.from_dense(np.array([[1.0, 1.0], [0.0, 2.0]]), pattern=np.array([[True, True], [True, True]]))
+    B = synth.from_dense(np.array([[1.0, 3.0], [-1.0, 0.0]]), pattern=np.array([[True, False], [True, True]]))
+    rp, col, val, *_ = run_gpu(A, B)
+    assert list(rp) == [0, 2, 4]
+    assert list(col) == [0, 1, 0, 1]
+    assert list(val) == [0.0, 0.0, -2.0, 0.0]
+
+
+@pytest.mark.parametrize("m,k,n", [(0, 0, 0), (0, 5, 7), (6, 0, 4), (5, 4, 0), (1, 1, 1), (3, 4, 2)])
+def test_degenerate_shapes(m, k, n):
+    A = synth.random_small(m, k, 0.6, seed=16)
+    B = synth.random_small(k, n, 0.6, seed=17)
+    rp, col, val, *_ = run_gpu(A, B)
+    assert_parity(A, B, rp, col, val)
+
+
+def test_empty_rows_mixed_with_heavy_rows():
+    D = np.zeros((64, 50_000))
+    rng = np.random.default_rng(0)
+    for i in (3, 40):
+        D[i, rng.choice(50_000, 9000, replace=False)] = rng.uniform(-1, 1, 9000)
+    A = synth.from_dense(np.eye(64)[:, :64])
+    B = synth.from_dense(D)
+    rp, col, val, *_ = run_gpu(A, B)
+    assert_parity(A, B, rp, col, val)
+
+
+def test_invalid_csr_is_reported():
+    import paper_2004_13907_gb300 as sp
+    A = synth.uniform_random(50, 50, 0.1, seed=18)
+    col = A.col.copy()
+    r = int(np.argmax(np.diff(A.row_ptr) >= 2))
+    s = A.row_ptr[r]
+    col[s], col[s + 1] = col[s + 1], col[s]          # unsorted row
+    bad = synth.CSR(A.rows, A.cols, A.row_ptr, col, A.val)
+    dA = sp.DeviceCSR.from_host(bad, "cuda")
+    with pytest.raises(sp.SpgemmError) as ei:
+        sp.spgemm_plan(dA, dA)
+    assert ei.value.name == "INVALID_CSR"
+    col2 = A.col.copy()
+    col2[0] = 50                                     # out of range
+    dA = sp.DeviceCSR.from_host(synth.CSR(A.rows, A.cols, A.row_ptr, col2, A.val), "cuda")
+    with pytest.raises(sp.SpgemmError) as ei:
+        sp.spgemm_plan(dA, dA)
+    assert ei.value.name == "INVALID_CSR"
+
+
+def test_host_entry_matches_oracle():
+    import paper_2004_13907_gb300 as sp
+    A = synth.uniform_random(4000, 4000, 2e-3, seed=19)
+    hA = sp.DeviceCSR(A.rows, A.cols, torch.from_numpy(A.row_ptr.astype(np.int32)).pin_memory(),
+                      torch.from_numpy(A.col).pin_memory(), torch.from_numpy(A.val).pin_memory())
+    C = sp.spgemm_multiply_host(hA, hA)
+    rp = C.row_ptr.numpy().astype(np.int64)
+    assert_parity(A, A, rp, C.col.numpy(), C.val.numpy())
+    # reuse of the grown buffers
+    C2 = sp.spgemm_multiply_host(hA, hA, out=C)
+    assert np.array_equal(C2.col.numpy(), C.col.numpy())
+
+
+def test_repeat_numeric_on_plan_and_changed_values():
+    """The plan can be re-used for a new numeric pass when the values change."""
+    import paper_2004_13907_gb300 as sp
+    A = synth.uniform_random(3000, 3000, 3e-3, seed=20)
+    dA = sp.DeviceCSR.from_host(A, "cuda")
+    plan = sp.spgemm_plan(dA, dA)
+    sp.spgemm_symbolic(plan)
+    C = sp.alloc_output(plan)
+    sp.spgemm_numeric(plan, C)
+    dA.val.mul_(2.0)
+    sp.spgemm_numeric(plan, C)
+    sp.spgemm_plan_check(plan)
+    A2 = synth.CSR(A.rows, A.cols, A.row_ptr, A.col, A.val * 2.0)
+    H = C.to_host()
+    assert_parity(A2, A2, H.row_ptr.numpy().astype(np.int64), H.col.numpy(), H.val.numpy())
+
+
+@pytest.mark.slow
+def test_rmat_2e20_sampled_rows():
+    """The R-MAT 2^20 / degree-16 config at full size, in the bench's launch
+    configuration; rows sampled across every work class compared with the oracle, plus
+    invariants over all rows (sorted columns, nnz(C) = sum of the symbolic counts)."""
+    A = synth.rmat(20, 16, seed=0)
+    import paper_2004_13907_gb300 as sp
+    dA = sp.DeviceCSR.from_host(A, "cuda")
+    plan = sp.spgemm_plan(dA, dA)
+    sp.spgemm_symbolic(plan)
+    C = sp.alloc_output(plan)
+    sp.spgemm_numeric(plan, C)
+    sp.spgemm_plan_check(plan)
+    torch.cuda.synchronize()
+    P = oracle.products_per_row(A, A)
+    assert sp.spgemm_plan_get_info(plan)["products"] == int(P.sum())
+    rp = C.row_ptr.cpu().numpy().astype(np.int64)
+    # invariants over every row: strictly increasing columns within rows
+    d = torch.diff(C.col.to(torch.int64))
+    starts = C.row_ptr[1:-1].to(torch.int64)
+    ok = d > 0
+    ok[(starts - 1)[(starts > 0) & (starts <= d.numel())]] = True  # row boundaries
+    assert bool(ok.all())
+    rng = np.random.default_rng(7)
+    order = np.argsort(P)
+    picks = list(order[-6:]) + list(rng.choice(A.rows, 40, replace=False))
+    for lo, hi in [(1, 32), (33, 1024), (1025, 4096), (4097, 1 << 17), (1 << 17, 1 << 30)]:
+        ids = np.nonzero((P >= lo) & (P <= hi))[0]
+        if len(ids):
+            picks += list(rng.choice(ids, min(8, len(ids)), replace=False))
+    rows = np.unique(np.array(picks, dtype=np.int64))
+    # fetch only the sampled rows from the device
+    col_rows, val_rows, rp_s = [], [], [0]
+    for i in rows:
+        s, e = int(rp[i]), int(rp[i + 1])
+        col_rows.append(C.col[s:e].cpu().numpy())
+        val_rows.append(C.val[s:e].cpu().numpy())
+        rp_s.append(rp_s[-1] + e - s)
+    ref = oracle.spgemm(A, A, rows=rows)
+    for t, i in enumerate(rows):
+        r = slice(ref.row_ptr[t], ref.row_ptr[t + 1])
+        assert np.array_equal(col_rows[t], ref.col[r]), f"row {i}"
+        assert np.all(np.abs(val_rows[t] - ref.val[r]) <= 1e-12 * ref.mag[r]), f"row {i} values"
+    sp.spgemm_plan_destroy(plan)
