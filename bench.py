@@ -1,0 +1,442 @@
+#!/usr/bin/env python3
+"""SpGEMM throughput on GB300: C = A*A on synthetic matrices shaped like the paper's
+workloads (the paper evaluates C = A^2, Sec. V).
+
+One step = the whole product for every matrix of the workload: plan (validation, product
+count, row classes), symbolic pass, allocation of C, numeric pass. The metric is GFLOP/s
+= 2 * (number of partial products) / time. Default workload: the 2D 5-point Laplacian on a
+1024 x 1024 grid and the R-MAT graph with 2^20 vertices and average degree 16, both FP64.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the CPU oracle instead (rank 0
+only), on a bounded row sample of the same workload each step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import csv
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "SpGEMM GFLOP/s (2 x intermediate products / s)"
+UNIT = "GFLOP/s"
+
+WORKLOADS = {
+    # name -> list of (matrix name, generator)
+    "lap2d1024+rmat20": [("lap2d_1024", lambda: synth.laplacian2d(1024)),
+                         ("rmat_2e20_deg16", lambda: synth.rmat(20, 16, seed=0))],
+    "lap2d1024": [("lap2d_1024", lambda: synth.laplacian2d(1024))],
+    "rmat20": [("rmat_2e20_deg16", lambda: synth.rmat(20, 16, seed=0))],
+    "uniform10k": [("uniform_10k_d1e-3", lambda: synth.uniform_random(10_000, 10_000, 1e-3, seed=0))],
+    "rmat16": [("rmat_2e16_deg16", lambda: synth.rmat(16, 16, seed=0))],
+}
+WORKLOAD_DESC = {
+    "lap2d1024+rmat20": "C=A*A for A = 2D 5-point Laplacian 1024^2 (FP64 4/-1) and A = R-MAT 2^20 "
+                        "vertices, 16*2^20 edge samples, (a,b,c,d)=(.57,.19,.19,.05), FP64 U[0,1], seed 0",
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for r in csv.reader(f):
+                if len(r) >= 9:
+                    rows.append([x.strip() for x in r])
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _window_bytes(info: dict) -> tuple:
+    """Algorithmic bytes of the windowed numeric kernel's launch: per row 8 (its A row
+    pointers), per A entry 12 (column, value) + 8 (start and end of the named B row), per
+    partial product 12 (the gathered B column and value), per entry of C 12 (column, value)."""
+    rows = sum(info["num_class_rows"][0:4])
+    annz = sum(info["num_class_annz"][0:4])
+    prods = sum(info["num_class_products"][0:4])
+    cnnz = sum(info["num_class_cnnz"][0:4])
+    return 8 * rows + 20 * annz + 12 * prods + 12 * cnnz, prods
+
+
+def _numeric_bytes(info: dict, m: int) -> int:
+    """Algorithmic bytes of a whole numeric pass (all classes): A (row pointers, columns,
+    values), the gathered B rows (row bounds, columns, values) and C (row pointers, columns,
+    values)."""
+    annz = sum(info["num_class_annz"])
+    return 4 * (m + 1) + 12 * annz + 8 * annz + 12 * info["products"] + 8 * (m + 1) + 12 * info["nnz_c"]
+
+
+def run_ours(args):
+    import torch
+    import paper_2004_13907_gb300 as sp
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    mats = [(name, gen()) for name, gen in WORKLOADS[args.workload]]
+    dev = [(name, M, sp.DeviceCSR.from_host(M, "cuda")) for name, M in mats]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    opts = sp.spgemm_opts_default(record_timings=1)
+    stream = torch.cuda.current_stream()
+
+    def step(collect=None):
+        for name, M, dM in dev:
+            plan = sp.spgemm_plan(dM, dM, "f64", opts)
+            sp.spgemm_symbolic(plan)
+            C = sp.alloc_output(plan)
+            sp.spgemm_numeric(plan, C)
+            if collect is not None:
+                collect.append((name, M, plan, C))
+            else:
+                del C
+                sp.spgemm_plan_destroy(plan)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, per = [], {}
+    launches = 0
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        col = []
+        e0.record(stream)
+        step(col)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for name, M, plan, C in col:
+            sp.spgemm_plan_check(plan)
+            info = sp.spgemm_plan_get_info(plan)
+            tim = sp.spgemm_plan_get_timings(plan)
+            launches += info["kernel_launches"]
+            d = per.setdefault(name, {"info": info, "stages": {}, "rows": M.rows})
+            for k, (ms, nl) in tim.items():
+                d["stages"].setdefault(k, []).append(ms)
+            sp.spgemm_plan_destroy(plan)
+        del col
+        C = plan = None    # drop the last product before the next step allocates its own
+    wall = time.perf_counter() - t_wall0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+
+    products_step = sum(per[n]["info"]["products"] for n, _, _ in dev)
+    ms_local = float(np.mean(step_ms))
+    ms = ms_local
+    if dist:
+        t = torch.tensor([ms_local], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = 2.0 * products_step * ws / (ms * 1e-3) / 1e9
+
+    # dominant kernel: the stage with the largest device time across the step
+    stage_tot = {}
+    for name, d in per.items():
+        for k, v in d["stages"].items():
+            stage_tot[(name, k)] = float(np.mean(v))
+    (dom_mat, dom_stage), dom_ms = max(stage_tot.items(), key=lambda kv: kv[1])
+    peak, peak_kind = _peaks()
+    roof = None
+    if dom_stage == "num_window":
+        bytes_, _ = _window_bytes(per[dom_mat]["info"])
+        achieved = bytes_ / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"k_num_window ({dom_mat})", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": bytes_,
+                "launch_ms": round(dom_ms, 4), "traffic": None}
+    breakdown = {}
+    for name, d in per.items():
+        info = d["info"]
+        tot = sum(float(np.mean(v)) for v in d["stages"].values())
+        breakdown[name] = {
+            "rows": d["rows"], "products": info["products"], "nnz_c": info["nnz_c"],
+            "stage_ms": {k: round(float(np.mean(v)), 4) for k, v in d["stages"].items() if np.mean(v) > 0},
+            "kernel_ms_sum": round(tot, 4),
+            "numeric_ms": round(sum(float(np.mean(d["stages"][k])) for k in
+                                    ("num_rowptr", "num_window", "num_block", "num_warp", "num_tiny")), 4),
+            "numeric_alg_bytes": _numeric_bytes(info, d["rows"]),
+            "num_class_rows": {sp._native.NUM_CLASSES[c]: info["num_class_rows"][c]
+                               for c in range(len(sp._native.NUM_CLASSES)) if info["num_class_rows"][c]},
+        }
+        nb = breakdown[name]["numeric_alg_bytes"]
+        breakdown[name]["numeric_GBps"] = round(nb / (breakdown[name]["numeric_ms"] * 1e-3) / 1e9, 1)
+        breakdown[name]["numeric_frac_of_peak"] = round(breakdown[name]["numeric_GBps"] / peak, 4)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOAD_DESC.get(args.workload, args.workload),
+                   "products_per_step": products_step, "l2": "flushed: 512 MB written between timed steps",
+                   "parallelism": f"replicas x{ws} (independent products, no collective on the data path)"},
+        "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
+        "breakdown": breakdown, "wall_s_timed": round(wall, 3),
+    }
+    # free the device-resident products before the end-to-end leg
+    del dev
+    torch.cuda.empty_cache()
+    if not args.no_e2e:
+        nnz_c = {name: per[name]["info"]["nnz_c"] for name, _ in mats}
+        line["e2e"] = run_e2e(args, mats, nnz_c, products_step, sp, torch, dist)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mats, args.cpu_seconds)
+    if dist:
+        dist.destroy_process_group()
+    return line, rank
+
+
+def _pinned(n: int, dtype, torch):
+    """Page-locked host array of exactly n elements (numpy memory registered with CUDA)."""
+    a = np.empty(max(n, 1), dtype=dtype)
+    t = torch.from_numpy(a)
+    rc = torch.cuda.cudart().cudaHostRegister(t.data_ptr(), t.numel() * t.element_size(), 0)
+    return t, (int(rc) == 0)
+
+
+def run_e2e(args, mats, nnz_c, products_step, sp, torch, dist):
+    """Same metric through spgemm_multiply_host: host A -> device, product, C -> host.
+    Host arrays are page-locked; the output arrays are sized from nnz(C) of the device run."""
+    hosts = []
+    pinned_ok = True
+    for name, M in mats:
+        rp, ok1 = _pinned(M.rows + 1, np.int32, torch)
+        col, ok2 = _pinned(M.nnz, np.int32, torch)
+        val, ok3 = _pinned(M.nnz, np.float64, torch)
+        rp.copy_(torch.from_numpy(M.row_ptr.astype(np.int32)))
+        col[:M.nnz].copy_(torch.from_numpy(M.col))
+        val[:M.nnz].copy_(torch.from_numpy(M.val))
+        hA = sp.DeviceCSR(M.rows, M.cols, rp, col[:M.nnz], val[:M.nnz])
+        nnz = nnz_c[name]
+        idx64 = nnz >= 2**31
+        orp, o1 = _pinned(M.rows + 1, np.int64 if idx64 else np.int32, torch)
+        ocol, o2 = _pinned(nnz, np.int32, torch)
+        oval, o3 = _pinned(nnz, np.float64, torch)
+        pinned_ok &= all((ok1, ok2, ok3, o1, o2, o3))
+        out = sp.DeviceCSR(M.rows, M.cols, orp, ocol[:nnz], oval[:nnz])
+        h2d = 2 * ((M.rows + 1) * 4 + M.nnz * 12)            # A and B (= A) copied in
+        d2h = (M.rows + 1) * orp.element_size() + nnz * 12    # C copied out
+        hosts.append((name, hA, out, idx64, h2d, d2h))
+
+    def step():
+        for name, hA, out, idx64, _, _ in hosts:
+            sp.spgemm_multiply_host(hA, hA, out=out, idx64=idx64)
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    ws, _, _ = _dist()
+    t = float(np.mean(times))
+    if dist:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return {"value": round(2.0 * products_step * ws / t / 1e9, 3), "unit": UNIT,
+            "h2d_bytes_per_step": int(sum(h[4] for h in hosts)),
+            "d2h_bytes_per_step": int(sum(h[5] for h in hosts)),
+            "ms_per_step": round(t * 1e3, 3), "host_buffers": "pinned" if pinned_ok else "pageable (pinning failed)",
+            "api": "spgemm_multiply_host (C ABI, host buffers)"}
+
+
+def cpu_baseline(mats, seconds: float) -> dict:
+    """The CPU oracle (ordered-map Gustavson, threaded over rows) on a seeded row sample of
+    each matrix sized to about ``seconds`` of work, extrapolated to the workload."""
+    import oracle
+    total_t = 0.0
+    total_p = 0
+    samples = []
+    threads = 0
+    for name, M in mats:
+        P = oracle.products_per_row(M, M)
+        rate_probe = 3e7  # products/s guess used only to size the sample
+        budget = max(int(seconds / len(mats) * rate_probe), 1)
+        if P.sum() <= budget:
+            rows = None
+            sampled = int(P.sum())
+        else:
+            rng = np.random.default_rng(1234)
+            order = rng.permutation(M.rows)
+            cs = np.cumsum(P[order])
+            k = int(np.searchsorted(cs, budget)) + 1
+            rows = np.sort(order[:k])
+            sampled = int(P[rows].sum())
+        t0 = time.perf_counter()
+        out = oracle.spgemm(M, M, rows=rows)
+        dt = time.perf_counter() - t0
+        threads = max(threads, out.threads)
+        rate = sampled / dt
+        total_t += int(P.sum()) / rate
+        total_p += int(P.sum())
+        samples.append(f"{name}: {'all' if rows is None else len(rows)} rows, {sampled} products in {dt:.2f} s")
+    return {"value": round(2.0 * total_p / total_t / 1e9, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "; ".join(samples) + " (time extrapolated to the whole workload by products)"}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step multiplies a bounded seeded row sample
+    of every matrix of the workload."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None, rank
+    import oracle
+    mats = [(name, gen()) for name, gen in WORKLOADS[args.workload]]
+    Ps = [oracle.products_per_row(M, M) for _, M in mats]
+    budget = int(args.ref_products_per_step)
+    rng = np.random.default_rng(99)
+    rows_per = []
+    for (name, M), P in zip(mats, Ps):
+        b = budget // len(mats)
+        order = rng.permutation(M.rows)
+        cs = np.cumsum(P[order])
+        k = int(np.searchsorted(cs, b)) + 1
+        rows_per.append(np.sort(order[:min(k, M.rows)]))
+
+    def step():
+        prods = 0
+        threads = 0
+        for (name, M), P, rows in zip(mats, Ps, rows_per):
+            out = oracle.spgemm(M, M, rows=rows)
+            threads = max(threads, out.threads)
+            prods += int(P[rows].sum())
+        return prods, threads
+
+    for _ in range(args.warmup):
+        step()
+    times, prods, threads = [], 0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        p, threads = step()
+        times.append(time.perf_counter() - t0)
+        prods = p
+    t = float(np.mean(times))
+    value = 2.0 * prods / t / 1e9
+    sample = "; ".join(f"{name}: {len(r)} seeded random rows" for (name, _), r in zip(mats, rows_per))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOAD_DESC.get(args.workload, args.workload),
+                   "products_per_step": prods, "l2": "n/a (CPU)", "parallelism": "host threads"},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample + f" per step ({prods} products)"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return line, rank
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lap2d1024+rmat20", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-products-per-step", type=float, default=2e8)
+    ap.add_argument("--json-out", default=None)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        sys.stderr.write("note: fewer than 3 warm-up steps\n")
+    if args.impl == "reference":
+        line, rank = run_reference(args)
+    else:
+        line, rank = run_ours(args)
+    if rank == 0 and line is not None:
+        s = json.dumps(line)
+        print(s, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(s + "\n")
+
+
+if __name__ == "__main__":
+    main()

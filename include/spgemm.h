@@ -85,7 +85,9 @@ typedef struct spgemm_csr_out {
 
 /* Device workspace allocator. alloc returns device memory usable on `stream` (or NULL);
  * free releases it in stream order. When the allocator pointer passed to an entry point is
- * NULL the library uses cudaMallocAsync / cudaFreeAsync on the call's stream. */
+ * NULL the library allocates in stream order (cudaMallocFromPoolAsync / cudaFreeAsync) from a
+ * memory pool of its own on the current device, which keeps freed memory reserved for reuse
+ * by later calls until the process exits. */
 typedef struct spgemm_allocator {
   void* (*alloc)(size_t bytes, void* stream, void* ctx);
   void (*free)(void* ptr, void* stream, void* ctx);
@@ -108,26 +110,63 @@ typedef struct spgemm_opts {
   int32_t f32c_rerun_all;     /* 1: recompute every F32 row in FP64 (tests) */
   int32_t f32c_rerun_none;    /* 1: never recompute (tests measure the bound alone) */
   int32_t num_streams;        /* concurrent streams for the row classes (default 4) */
-  int32_t reserved[15];
+  int32_t record_timings;     /* 1: record CUDA events around every stage of the passes
+                                 (read them with spgemm_plan_get_timings); default 0 */
+  int32_t window_split_max_mb;/* device memory budget (MiB) of the column-block split table
+                                 of B used by the windowed rows (default 4096); when the table
+                                 would be larger, those rows binary-search B instead (0: always) */
+  int32_t reserved[13];
 } spgemm_opts;
 
 /* Opaque plan: the work description of one product (row counts, row classes, row
  * offsets of C) and its device workspace. */
 typedef struct spgemm_plan_s spgemm_plan_t;
 
-/* Counters describing a plan (host values). */
+/* Counters describing a plan (host values).
+ * Row classes, in the order of the class arrays:
+ *   symbolic: 0-3 windowed (P_i >= 2^22, >= 2^20, >= 2^17, rest), 4 block table,
+ *             5-7 warp tables (2048, 512, 128 keys), 8 tiny (<= 32 products), 9 empty;
+ *   numeric:  0-3 windowed (same split), 4-5 block tables (8192, 2048 slots),
+ *             6-8 warp tables (1024, 256, 64 slots), 9 tiny, 10 empty. */
 typedef struct spgemm_plan_info {
   int64_t rows, inner, cols;
   int64_t products;            /* sum_i P_i = number of partial products (flops = 2x) */
   int64_t nnz_c;               /* -1 before spgemm_symbolic */
   int64_t max_row_products;
-  int64_t sym_class_rows[16];  /* rows per symbolic row class (class order is internal) */
+  int64_t sym_class_rows[16];  /* rows per symbolic row class */
   int64_t num_class_rows[16];  /* rows per numeric row class (after spgemm_symbolic) */
+  int64_t num_class_products[16];  /* sum of P_i over each numeric class */
+  int64_t num_class_annz[16];      /* sum of nnz(A_i) over each numeric class */
+  int64_t num_class_cnnz[16];      /* sum of nnz(C_i) over each numeric class */
   int64_t workspace_bytes;     /* device workspace held by the plan */
   int64_t f32c_rerun_rows;     /* rows recomputed in FP64 by the last F32 numeric pass */
+  int64_t kernel_launches;     /* CUDA kernels this plan has launched so far */
   int32_t needs_rowptr64;
   int32_t state;               /* 0 planned, 1 symbolic done, 2 numeric done */
 } spgemm_plan_info;
+
+/* Stages timed when spgemm_opts.record_timings is set. */
+typedef enum spgemm_stage {
+  SPGEMM_STAGE_VALIDATE = 0,
+  SPGEMM_STAGE_COUNT = 1,        /* product count, class scan, class scatter */
+  SPGEMM_STAGE_SYM_WINDOW = 2,
+  SPGEMM_STAGE_SYM_BLOCK = 3,
+  SPGEMM_STAGE_SYM_WARP = 4,
+  SPGEMM_STAGE_SYM_TINY = 5,
+  SPGEMM_STAGE_SYM_SCAN = 6,     /* row offsets of C and numeric classes */
+  SPGEMM_STAGE_NUM_ROWPTR = 7,
+  SPGEMM_STAGE_NUM_WINDOW = 8,
+  SPGEMM_STAGE_NUM_BLOCK = 9,
+  SPGEMM_STAGE_NUM_WARP = 10,
+  SPGEMM_STAGE_NUM_TINY = 11,
+  SPGEMM_STAGE_NUM_RERUN = 12,   /* FP64 recomputation of flagged FP32 rows */
+  SPGEMM_NUM_STAGES = 13
+} spgemm_stage;
+
+typedef struct spgemm_timings {
+  double ms[16];          /* device time of each stage's last run (CUDA events on its stream) */
+  int32_t launches[16];   /* kernels launched by that run of the stage */
+} spgemm_timings;
 
 void spgemm_opts_default(spgemm_opts* opts);
 
@@ -164,6 +203,10 @@ spgemm_status spgemm_plan_get_info(const spgemm_plan_t* plan, spgemm_plan_info* 
  * symbolic pass counted, a full hash table): INTERNAL when any fired, else OK.
  * spgemm_numeric itself does not wait, so call this to check a numeric pass. */
 spgemm_status spgemm_plan_check(spgemm_plan_t* plan, void* stream);
+
+/* Waits for the recorded events and returns the per-stage times of the last run of each
+ * stage (zero for stages that did not run or when record_timings was not set). */
+spgemm_status spgemm_plan_get_timings(spgemm_plan_t* plan, spgemm_timings* timings);
 
 /* Releases the workspace (in order on the stream given at plan time) and the plan.
  * NULL is accepted. */

@@ -24,7 +24,7 @@ from ._native import F32_COMPENSATED, F64, SpgemmError  # noqa: F401
 __all__ = [
     "DeviceCSR", "Plan", "SpgemmError", "F64", "F32_COMPENSATED", "spgemm_opts_default",
     "spgemm_plan", "spgemm_symbolic", "spgemm_numeric", "spgemm_plan_get_info",
-    "spgemm_plan_check", "spgemm_plan_destroy", "spgemm_multiply_host", "spgemm_last_error",
+    "spgemm_plan_check", "spgemm_plan_get_timings", "spgemm_plan_destroy", "spgemm_multiply_host", "spgemm_last_error",
     "spgemm_version", "multiply", "lib",
 ]
 
@@ -157,6 +157,14 @@ def spgemm_plan_get_info(plan: Plan) -> dict:
         v = getattr(info, name)
         out[name] = list(v) if not isinstance(v, int) else v
     return out
+
+
+def spgemm_plan_get_timings(plan: Plan) -> dict:
+    """Per-stage device milliseconds and launch counts of the last run of each stage
+    (needs ``record_timings=1`` in the plan's options)."""
+    t = _native.Timings()
+    _native.check(lib().spgemm_plan_get_timings(plan.handle, ctypes.byref(t)))
+    return {name: (t.ms[i], t.launches[i]) for i, name in enumerate(_native.STAGES)}
 
 
 def spgemm_plan_check(plan: Plan, stream=None) -> None:

@@ -47,14 +47,28 @@ class Opts(ctypes.Structure):
     _fields_ = [("validate", c_i32), ("tiny_max", c_i32), ("warp_max", c_i32), ("block_max", c_i32),
                 ("window_hash_fill", c_i32), ("force_window", c_i32), ("rowptr32_limit", c_i64),
                 ("f32c_rerun_all", c_i32), ("f32c_rerun_none", c_i32), ("num_streams", c_i32),
-                ("reserved", c_i32 * 15)]
+                ("record_timings", c_i32), ("window_split_max_mb", c_i32), ("reserved", c_i32 * 13)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("rows", c_i64), ("inner", c_i64), ("cols", c_i64), ("products", c_i64),
                 ("nnz_c", c_i64), ("max_row_products", c_i64), ("sym_class_rows", c_i64 * 16),
-                ("num_class_rows", c_i64 * 16), ("workspace_bytes", c_i64),
-                ("f32c_rerun_rows", c_i64), ("needs_rowptr64", c_i32), ("state", c_i32)]
+                ("num_class_rows", c_i64 * 16), ("num_class_products", c_i64 * 16),
+                ("num_class_annz", c_i64 * 16), ("num_class_cnnz", c_i64 * 16), ("workspace_bytes", c_i64),
+                ("f32c_rerun_rows", c_i64), ("kernel_launches", c_i64), ("needs_rowptr64", c_i32),
+                ("state", c_i32)]
+
+
+STAGES = ["validate", "count", "sym_window", "sym_block", "sym_warp", "sym_tiny", "sym_scan",
+          "num_rowptr", "num_window", "num_block", "num_warp", "num_tiny", "num_rerun"]
+SYM_CLASSES = ["win0", "win1", "win2", "win3", "block8192", "warp2048", "warp512", "warp128", "tiny",
+               "empty"]
+NUM_CLASSES = ["win0", "win1", "win2", "win3", "block8192", "block2048", "warp1024", "warp256", "warp64",
+               "tiny", "empty"]
+
+
+class Timings(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 16), ("launches", c_i32 * 16)]
 
 
 # name -> (restype, argtypes); every symbol include/spgemm.h declares
@@ -67,6 +81,7 @@ SIGNATURES = {
     "spgemm_plan_get_info": (c_i32, [c_vp, ctypes.POINTER(PlanInfo)]),
     "spgemm_plan_check": (c_i32, [c_vp, c_vp]),
     "spgemm_plan_destroy": (c_i32, [c_vp]),
+    "spgemm_plan_get_timings": (c_i32, [c_vp, ctypes.POINTER(Timings)]),
     "spgemm_multiply_host": (c_i32, [ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_i32,
                                      ctypes.POINTER(Opts), ctypes.POINTER(Allocator), c_vp,
                                      ctypes.POINTER(CsrOut), c_i64, ctypes.POINTER(c_i64)]),

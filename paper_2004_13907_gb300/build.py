@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspgemm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["k_setup.cu", "k_symbolic.cu", "k_numeric.cu", "runtime.cu", "api.cu", "host_entry.cu"]
+SOURCES = ["k_setup.cu", "k_symbolic.cu", "k_numeric.cu", "k_window.cu", "runtime.cu", "api.cu",
+           "host_entry.cu"]
 
 
 def _nvcc() -> str:

@@ -52,6 +52,33 @@ int device_sm_count() {
   return cache[dev];
 }
 
+// The library's own stream-ordered memory pool on the current device, created on first use.
+// It keeps freed memory reserved (release threshold = max) so repeated products reuse it
+// instead of mapping fresh pages every call; the default pool of the process is untouched.
+cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (static_cast<int>(pools.size()) <= dev) pools.resize(dev + 1, nullptr);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t threshold = ~uint64_t(0);
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+
 void* Workspace::get(size_t bytes) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
@@ -59,7 +86,10 @@ void* Workspace::get(size_t bytes) {
   if (has_alloc) {
     p = alloc.alloc(bytes, stream, alloc.ctx);
   } else {
-    if (cudaMallocAsync(&p, bytes, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    cudaMemPool_t pool = library_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, static_cast<cudaStream_t>(stream))
+                         : cudaMallocAsync(&p, bytes, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;
     }
@@ -114,6 +144,8 @@ void spgemm_opts_default(spgemm_opts* o) {
   o->f32c_rerun_all = 0;
   o->f32c_rerun_none = 0;
   o->num_streams = 4;
+  o->record_timings = 0;
+  o->window_split_max_mb = 4096;
 }
 
 const char* spgemm_last_error(void) { return g_last_error.c_str(); }
@@ -147,6 +179,7 @@ spgemm_status spgemm_plan(const spgemm_csr_in* A, const spgemm_csr_in* B, spgemm
   if (st != SPGEMM_OK) {
     const std::string msg = g_last_error;
     cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    destroy_events(p);
     p->ws.release_all();
     delete p;
     g_last_error = msg;
@@ -195,10 +228,17 @@ spgemm_status spgemm_plan_get_info(const spgemm_plan_t* plan, spgemm_plan_info* 
   info->nnz_c = plan->state >= 1 ? plan->nnz_c : -1;
   info->max_row_products = plan->max_row_products;
   for (int c = 0; c < kSymNumClasses; ++c) info->sym_class_rows[c] = plan->sym_off[c + 1] - plan->sym_off[c];
-  if (plan->state >= 1)
-    for (int c = 0; c < kNumNumClasses; ++c) info->num_class_rows[c] = plan->num_off[c + 1] - plan->num_off[c];
+  if (plan->state >= 1) {
+    for (int c = 0; c < kNumNumClasses; ++c) {
+      info->num_class_rows[c] = plan->num_off[c + 1] - plan->num_off[c];
+      info->num_class_products[c] = static_cast<int64_t>(plan->cls_sums[c][0]);
+      info->num_class_annz[c] = static_cast<int64_t>(plan->cls_sums[c][1]);
+      info->num_class_cnnz[c] = static_cast<int64_t>(plan->cls_sums[c][2]);
+    }
+  }
   info->workspace_bytes = plan->ws.total;
   info->f32c_rerun_rows = plan->f32c_rerun_rows;
+  info->kernel_launches = plan->launches;
   info->needs_rowptr64 = plan->state >= 1 && plan->nnz_c > plan->opts.rowptr32_limit;
   info->state = plan->state;
   return SPGEMM_OK;
@@ -210,8 +250,26 @@ spgemm_status spgemm_plan_check(spgemm_plan_t* plan, void* stream) {
   return read_device_error(plan, static_cast<cudaStream_t>(stream));
 }
 
+spgemm_status spgemm_plan_get_timings(spgemm_plan_t* plan, spgemm_timings* t) {
+  clear_error_msg();
+  if (!plan || !t) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "NULL argument");
+  std::memset(t, 0, sizeof(*t));
+  if (!plan->ev_made) return SPGEMM_OK;
+  for (int i = 0; i < SPGEMM_NUM_STAGES; ++i) {
+    if (!plan->ev_rec[i]) continue;
+    cudaError_t e = cudaEventSynchronize(plan->ev[i][1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, plan->ev[i][0], plan->ev[i][1]);
+    if (e != cudaSuccess) return cuda_status(e, "reading stage timings");
+    t->ms[i] = ms;
+    t->launches[i] = plan->ev_launches[i];
+  }
+  return SPGEMM_OK;
+}
+
 spgemm_status spgemm_plan_destroy(spgemm_plan_t* plan) {
   if (!plan) return SPGEMM_OK;
+  destroy_events(plan);
   plan->ws.release_all();
   delete plan;
   return SPGEMM_OK;

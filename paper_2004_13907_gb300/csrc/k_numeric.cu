@@ -10,14 +10,7 @@
 //  * warp  : one warp per row, a shared hash table (column -> FP64 sum) of 64/256/1024
 //            slots, then the occupied slots are compacted and bitonic-sorted by column.
 //  * block : one block per row, a hash table of 2048 or 8192 slots, compaction, bitonic sort.
-//  * window: one persistent block per row for rows with more entries than a block table.
-//            The columns are cut into blocks of kBlockCols; the symbolic pass counted the
-//            entries of C_i in each block. Consecutive blocks with few entries are merged
-//            into a "hash window" (a hash table of 8192 slots plus a bitmap of the window's
-//            columns); a block with many entries is a "dense window" (an FP64 array indexed
-//            by column minus the window start, plus a bitmap). Either way the bitmap, read in
-//            word order, gives the sorted column list for free. Each A entry keeps a cursor
-//            into its B row (global memory) so every product is read exactly once.
+//  * window: rows with more entries than a block table (k_window.cu).
 // Sums are accumulated with shared-memory FP64 atomics, so their order (and the last bits of
 // a value) can change from run to run; the pattern is always exact.
 #include "enumerate.cuh"
@@ -256,197 +249,6 @@ __global__ void __launch_bounds__(NT) k_num_block(DevCsr A, DevCsr B, const int3
   }
 }
 
-// ---- windowed rows
-// Shared layout (dynamic): [0, 128 KB): dense FP64[kBlockCols] | hash {keys int32[8192] at 0,
-// vals FP64[8192] at 32 KB}; then the window bitmap, kHashWinBlocks * kBlockWords words.
-// Hash keys are stored as column + 1 so that all-zero bytes are the clean state of both
-// layouts.
-constexpr int kWinRegionBytes = kBlockCols * 8;
-constexpr int kWinBitmapWords = kHashWinBlocks * kBlockWords;
-constexpr int kWinSmemBytes = kWinRegionBytes + kWinBitmapWords * 4;
-constexpr int kHashWinLog2 = 13;
-static_assert((1 << kHashWinLog2) == kHashWinSlots, "hash window size");
-static_assert(kHashWinSlots * 12 <= kWinRegionBytes, "hash window fits the region");
-
-enum : int { kWinDone = 0, kWinDense = 1, kWinHash = 2 };
-
-__global__ void __launch_bounds__(kWinThreads, 1) k_num_window(
-    DevCsr A, DevCsr B, const int32_t* __restrict__ perm, int64_t count, int32_t* counter,
-    const int64_t* __restrict__ c_off, const int32_t* __restrict__ win_slot,
-    const uint16_t* __restrict__ blockcnt, int64_t nblocks, int64_t nslots,
-    int32_t* __restrict__ cursor, int32_t hash_fill, int32_t* __restrict__ ccol,
-    double* __restrict__ cval, uint32_t* err) {
-  extern __shared__ __align__(16) unsigned char win_smem[];
-  double* dense = reinterpret_cast<double*>(win_smem);
-  int32_t* hkeys = reinterpret_cast<int32_t*>(win_smem);
-  double* hvals = reinterpret_cast<double*>(win_smem + kHashWinSlots * 4);
-  uint32_t* bm = reinterpret_cast<uint32_t*>(win_smem + kWinRegionBytes);
-  __shared__ int64_t s_scan[33];
-  __shared__ int32_t s_ctl[6];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int kWarps = kWinThreads / 32;
-  const int64_t n = B.cols;
-  const double* av_ = static_cast<const double*>(A.val);
-  const double* bv_ = static_cast<const double*>(B.val);
-
-  for (int t = threadIdx.x; t < kWinSmemBytes / 16; t += kWinThreads)
-    reinterpret_cast<uint4*>(win_smem)[t] = make_uint4(0u, 0u, 0u, 0u);
-  __syncthreads();
-
-  for (;;) {
-    if (threadIdx.x == 0) s_ctl[0] = atomicAdd(counter, 1);
-    __syncthreads();
-    const int64_t idx = s_ctl[0];
-    if (idx >= count) break;
-    const int32_t i = perm[idx];
-    const int64_t slot = win_slot[i];
-    if (slot < 0 || slot >= nslots) {      // the row was not counted by the windowed symbolic pass
-      if (threadIdx.x == 0) set_error(err, kErrWindowPlan);
-      __syncthreads();
-      continue;
-    }
-    const uint16_t* cnts = blockcnt + slot * nblocks;
-    const int64_t a0 = A.rp[i];
-    const int64_t na = A.rp[i + 1] - a0;
-    int64_t out = c_off[i];
-    const int64_t out_end = c_off[i + 1];
-    int64_t next_b = 0;   // meaningful in thread 0 only
-    bool first = true;
-    for (;;) {
-      if (threadIdx.x == 0) {
-        int64_t b = next_b;
-        while (b < nblocks && cnts[b] == 0) ++b;
-        if (b >= nblocks) {
-          s_ctl[1] = kWinDone;
-        } else if (cnts[b] > hash_fill) {
-          s_ctl[1] = kWinDense; s_ctl[2] = static_cast<int32_t>(b); s_ctl[3] = static_cast<int32_t>(b + 1);
-          s_ctl[4] = cnts[b];
-          next_b = b + 1;
-        } else {
-          int64_t e = b;
-          int32_t sum = 0;
-          while (e < nblocks && e - b < kHashWinBlocks && sum + cnts[e] <= hash_fill) { sum += cnts[e]; ++e; }
-          s_ctl[1] = kWinHash; s_ctl[2] = static_cast<int32_t>(b); s_ctl[3] = static_cast<int32_t>(e);
-          s_ctl[4] = sum;
-          next_b = e;
-        }
-      }
-      __syncthreads();
-      const int wtype = s_ctl[1];
-      if (wtype == kWinDone) break;
-      const int64_t w0 = int64_t(s_ctl[2]) * kBlockCols;
-      const int64_t w1 = int64_t(s_ctl[3]) * kBlockCols < n ? int64_t(s_ctl[3]) * kBlockCols : n;
-      const int32_t expect = s_ctl[4];
-      // accumulate: one warp per A entry, resuming at the entry's cursor
-      for (int64_t e = wid; e < na; e += kWarps) {
-        const int32_t k = A.col[a0 + e];
-        const double av = av_[a0 + e];
-        const int64_t bstart = B.rp[k], bend = B.rp[k + 1];
-        int64_t cur = first ? bstart : bstart + cursor[a0 + e];
-        while (cur < bend) {
-          const int64_t j = cur + lane;
-          const int32_t c = j < bend ? B.col[j] : kNoCol;
-          const bool ok = c < w1;
-          if (ok && c < w0) {
-            set_error(err, kErrWindowPlan);   // an entry left behind by a skipped block
-          } else if (ok) {
-            const double v = av * bv_[j];
-            const int32_t rel = static_cast<int32_t>(c - w0);
-            if (wtype == kWinDense) {
-              atomicAdd(&dense[rel], v);
-              atomicOr(&bm[rel >> 5], 1u << (rel & 31));
-            } else {
-              const int32_t key = c + 1;
-              uint32_t h = hash_slot(key, kHashWinLog2);
-              for (int probe = 0; probe < kHashWinSlots; ++probe) {
-                const int32_t cur_key = *reinterpret_cast<volatile int32_t*>(&hkeys[h]);
-                if (cur_key == key) { atomicAdd(&hvals[h], v); break; }
-                if (cur_key == 0) {
-                  const int32_t old = atomicCAS(&hkeys[h], 0, key);
-                  if (old == 0 || old == key) { atomicAdd(&hvals[h], v); break; }
-                }
-                h = (h + 1) & (kHashWinSlots - 1);
-                if (probe == kHashWinSlots - 1) set_error(err, kErrHashFull);
-              }
-            }
-          }
-          const int got = __popc(__ballot_sync(0xffffffffu, ok));
-          cur += got;
-          if (got < 32) break;
-        }
-        if (lane == 0) cursor[a0 + e] = static_cast<int32_t>(cur - bstart);
-      }
-      __syncthreads();
-      int64_t tot = 0;
-      if (wtype == kWinDense) {
-        const int nwords = static_cast<int>((w1 - w0 + 31) >> 5);
-        const uint32_t word = threadIdx.x < nwords ? bm[threadIdx.x] : 0u;
-        const int64_t pos = block_excl_scan<int64_t>(__popc(word), s_scan, &tot);
-        if (word) {
-          int64_t o = out + pos;
-          for (uint32_t m = word; m; m &= m - 1) {
-            const int bit = __ffs(m) - 1;
-            const int rel = threadIdx.x * 32 + bit;
-            if (o < out_end) {
-              ccol[o] = static_cast<int32_t>(w0 + rel);
-              cval[o] = dense[rel];
-            }
-            dense[rel] = 0.0;
-            ++o;
-          }
-          bm[threadIdx.x] = 0u;
-        }
-      } else {
-        // mark the occupied columns in the bitmap, then walk it in column order
-        for (int s = threadIdx.x; s < kHashWinSlots; s += kWinThreads) {
-          const int32_t key = hkeys[s];
-          if (key) {
-            const int32_t rel = static_cast<int32_t>(key - 1 - w0);
-            atomicOr(&bm[rel >> 5], 1u << (rel & 31));
-          }
-        }
-        __syncthreads();
-        const int nwords = static_cast<int>((w1 - w0 + 31) >> 5);
-        constexpr int kPer = kWinBitmapWords / kWinThreads;   // 16 words per thread
-        const int wlo = threadIdx.x * kPer;
-        int c = 0;
-#pragma unroll
-        for (int t = 0; t < kPer; ++t) c += (wlo + t < nwords) ? __popc(bm[wlo + t]) : 0;
-        const int64_t pos = block_excl_scan<int64_t>(c, s_scan, &tot);
-        int64_t o = out + pos;
-        for (int t = 0; t < kPer; ++t) {
-          if (wlo + t >= nwords) break;
-          uint32_t m = bm[wlo + t];
-          if (!m) continue;
-          bm[wlo + t] = 0u;
-          for (; m; m &= m - 1) {
-            const int rel = (wlo + t) * 32 + (__ffs(m) - 1);
-            const int32_t key = static_cast<int32_t>(w0 + rel) + 1;
-            uint32_t h = hash_slot(key, kHashWinLog2);
-            double v = 0.0;
-            for (int probe = 0; probe < kHashWinSlots; ++probe) {
-              if (hkeys[h] == key) { v = hvals[h]; break; }
-              h = (h + 1) & (kHashWinSlots - 1);
-            }
-            if (o < out_end) {
-              ccol[o] = key - 1;
-              cval[o] = v;
-            }
-            ++o;
-          }
-        }
-        __syncthreads();
-        for (int s = threadIdx.x; s < kHashWinSlots; s += kWinThreads) { hkeys[s] = 0; hvals[s] = 0.0; }
-      }
-      if (threadIdx.x == 0 && tot != expect) set_error(err, kErrCount);
-      out += tot;
-      first = false;
-      __syncthreads();
-    }
-    if (threadIdx.x == 0 && out != out_end) set_error(err, kErrCount);
-  }
-}
-
 inline unsigned grid_rows(int64_t count, int rows_per_block, int max_blocks) {
   int64_t g = (count + rows_per_block - 1) / rows_per_block;
   if (g > max_blocks) g = max_blocks;
@@ -456,17 +258,18 @@ inline unsigned grid_rows(int64_t count, int rows_per_block, int max_blocks) {
 
 }  // namespace
 
-void launch_num_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+int launch_num_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                      const int64_t* c_off, int32_t* ccol, double* cval, uint32_t* err,
                      cudaStream_t s) {
-  if (count <= 0) return;
+  if (count <= 0) return 0;
   k_num_tiny<<<grid_rows(count, 8, 152 * 64), 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, err);
+  return 1;
 }
 
-void launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                      int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
                      uint32_t* err, cudaStream_t s) {
-  if (count <= 0) return;
+  if (count <= 0) return 0;
   const unsigned g = grid_rows(count, 8, 152 * 32);
   const size_t sm = size_t(8) * (size_t(1) << log2S) * 12;
   switch (log2S) {
@@ -478,12 +281,13 @@ void launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t*
       break;
     default: break;
   }
+  return 1;
 }
 
-void launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+int launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                       int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
                       uint32_t* err, cudaStream_t s) {
-  if (count <= 0) return;
+  if (count <= 0) return 0;
   const size_t sm = (size_t(1) << log2S) * 12;
   if (log2S == 11) {
     k_num_block<11, 256><<<grid_rows(count, 1, 152 * 8), 256, sm, s>>>(A, B, perm, count, c_off, ccol,
@@ -493,20 +297,7 @@ void launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t
     k_num_block<13, 512><<<grid_rows(count, 1, 152 * 4), 512, sm, s>>>(A, B, perm, count, c_off, ccol,
                                                                        cval, err);
   }
-}
-
-void launch_num_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
-                       int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
-                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, int32_t* cursor,
-                       int32_t hash_fill, int32_t* ccol, double* cval, int num_sms,
-                       uint32_t* err, cudaStream_t s) {
-  if (count <= 0) return;
-  cudaFuncSetAttribute(k_num_window, cudaFuncAttributeMaxDynamicSharedMemorySize, kWinSmemBytes);
-  cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
-  const int64_t g = count < num_sms ? count : num_sms;
-  k_num_window<<<static_cast<unsigned>(g), kWinThreads, kWinSmemBytes, s>>>(
-      A, B, perm, count, counter, c_off, win_slot, blockcnt, nblocks, nslots, cursor, hash_fill, ccol, cval,
-      err);
+  return 1;
 }
 
 }  // namespace spg

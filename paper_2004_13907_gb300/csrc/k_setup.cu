@@ -193,10 +193,12 @@ __global__ void __launch_bounds__(256) k_scatter_sym(DevCsr A, ClassParams cp, c
 
 __global__ void __launch_bounds__(256) k_num_tiles(DevCsr A, ClassParams cp, const int64_t* P,
                                                    const int32_t* nnz_row, int32_t* tile_hist,
-                                                   int64_t* tile_sum) {
+                                                   int64_t* tile_sum, unsigned long long* cls_sums) {
   __shared__ int32_t hist[kMaxClasses];
   __shared__ unsigned long long s_sum;
+  __shared__ unsigned long long s_cls[kMaxClasses][3];
   if (threadIdx.x < kMaxClasses) hist[threadIdx.x] = 0;
+  if (threadIdx.x < kMaxClasses * 3) (&s_cls[0][0])[threadIdx.x] = 0;
   if (threadIdx.x == 0) s_sum = 0;
   __syncthreads();
   const int64_t t = blockIdx.x;
@@ -210,6 +212,9 @@ __global__ void __launch_bounds__(256) k_num_tiles(DevCsr A, ClassParams cp, con
       const int32_t z = nnz_row[row];
       cls = num_class(P[row], na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na), z, cp);
       my += static_cast<unsigned long long>(z);
+      atomicAdd(&s_cls[cls][0], static_cast<unsigned long long>(P[row]));
+      atomicAdd(&s_cls[cls][1], static_cast<unsigned long long>(na));
+      atomicAdd(&s_cls[cls][2], static_cast<unsigned long long>(z));
     }
     aggregated_slot(hist, cls, valid);
   }
@@ -218,6 +223,10 @@ __global__ void __launch_bounds__(256) k_num_tiles(DevCsr A, ClassParams cp, con
   __syncthreads();
   if (threadIdx.x < kMaxClasses) tile_hist[t * kMaxClasses + threadIdx.x] = hist[threadIdx.x];
   if (threadIdx.x == 0) tile_sum[t] = static_cast<int64_t>(s_sum);
+  if (threadIdx.x < kMaxClasses * 3) {
+    const unsigned long long v = (&s_cls[0][0])[threadIdx.x];
+    if (v) atomicAdd(&cls_sums[threadIdx.x], v);
+  }
 }
 
 // Row offsets of C (exclusive scan of nnz(C_i), int64) and the numeric class scatter.
@@ -271,55 +280,64 @@ inline unsigned grid_for(int64_t n, int threads, int64_t cap = 65535LL * 16) {
 
 }  // namespace
 
-void launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t s) {
+int launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t s) {
   k_rowptr_to64<<<grid_for(n1, 256), 256, 0, s>>>(in, out, n1);
+  return 1;
 }
 
-void launch_validate(const DevCsr& M, uint32_t* err, cudaStream_t s) {
+int launch_validate(const DevCsr& M, uint32_t* err, cudaStream_t s) {
   const int64_t warps = M.rows > 0 ? M.rows : 1;
   k_validate<<<grid_for(warps * 32, 256), 256, 0, s>>>(M, err);
+  return 1;
 }
 
-void launch_count(const DevCsr& A, const DevCsr& B, ClassParams cp, int64_t* P, int32_t* nnz_row,
+int launch_count(const DevCsr& A, const DevCsr& B, ClassParams cp, int64_t* P, int32_t* nnz_row,
                   int32_t* tile_hist, int64_t* tile_sum, int64_t* tile_max, cudaStream_t s) {
   const int64_t ntiles = (A.rows + kTileRows - 1) / kTileRows;
-  if (ntiles == 0) return;
+  if (ntiles == 0) return 0;
   k_count<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, B, cp, P, nnz_row, tile_hist, tile_sum,
                                                         tile_max);
+  return 1;
 }
 
-void launch_class_scan(int64_t ntiles, int nclasses, int32_t* tile_hist, const int64_t* tile_sum,
+int launch_class_scan(int64_t ntiles, int nclasses, int32_t* tile_hist, const int64_t* tile_sum,
                        const int64_t* tile_max, int64_t* tile_sum_off, Summary* summary,
                        cudaStream_t s) {
   k_class_scan<<<1, 544, 0, s>>>(ntiles, nclasses, tile_hist, tile_sum, tile_max, tile_sum_off,
                                  summary);
+  return 1;
 }
 
-void launch_scatter_sym(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* tile_hist,
+int launch_scatter_sym(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* tile_hist,
                         int32_t* perm, cudaStream_t s) {
   const int64_t ntiles = (A.rows + kTileRows - 1) / kTileRows;
-  if (ntiles == 0) return;
+  if (ntiles == 0) return 0;
   k_scatter_sym<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, cp, P, tile_hist, perm);
+  return 1;
 }
 
-void launch_num_tiles(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* nnz_row,
-                      int32_t* tile_hist, int64_t* tile_sum, cudaStream_t s) {
+int launch_num_tiles(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* nnz_row,
+                      int32_t* tile_hist, int64_t* tile_sum, unsigned long long* cls_sums,
+                      cudaStream_t s) {
   const int64_t ntiles = (A.rows + kTileRows - 1) / kTileRows;
-  if (ntiles == 0) return;
-  k_num_tiles<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, cp, P, nnz_row, tile_hist, tile_sum);
+  if (ntiles == 0) return 0;
+  k_num_tiles<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, cp, P, nnz_row, tile_hist, tile_sum, cls_sums);
+  return 1;
 }
 
-void launch_scatter_num(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* nnz_row,
+int launch_scatter_num(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* nnz_row,
                         const int32_t* tile_hist, const int64_t* tile_sum_off, int32_t* perm,
                         int64_t* c_off, cudaStream_t s) {
   const int64_t ntiles = (A.rows + kTileRows - 1) / kTileRows;
-  if (ntiles == 0) return;
+  if (ntiles == 0) return 0;
   k_scatter_num<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, cp, P, nnz_row, tile_hist,
                                                               tile_sum_off, perm, c_off);
+  return 1;
 }
 
-void launch_write_rowptr(const int64_t* c_off, int64_t m1, void* out, int idx64, cudaStream_t s) {
+int launch_write_rowptr(const int64_t* c_off, int64_t m1, void* out, int idx64, cudaStream_t s) {
   k_write_rowptr<<<grid_for(m1, 256), 256, 0, s>>>(c_off, m1, out, idx64);
+  return 1;
 }
 
 }  // namespace spg

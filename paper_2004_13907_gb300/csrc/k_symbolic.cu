@@ -222,15 +222,16 @@ inline unsigned grid_rows(int64_t count, int rows_per_block, int max_blocks) {
 
 }  // namespace
 
-void launch_sym_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+int launch_sym_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                      int32_t* nnz_row, cudaStream_t s) {
-  if (count <= 0) return;
+  if (count <= 0) return 0;
   k_sym_tiny<<<grid_rows(count, 8, 152 * 64), 256, 0, s>>>(A, B, perm, count, nnz_row);
+  return 1;
 }
 
-void launch_sym_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+int launch_sym_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                      int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s) {
-  if (count <= 0) return;
+  if (count <= 0) return 0;
   const unsigned g = grid_rows(count, 8, 152 * 32);
   const size_t sm = size_t(8) << log2S << 2;
   switch (log2S) {
@@ -242,22 +243,24 @@ void launch_sym_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t*
       break;
     default: break;
   }
+  return 1;
 }
 
-void launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+int launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                       int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s) {
-  if (count <= 0) return;
+  if (count <= 0) return 0;
   const size_t sm = size_t(4) << log2S;
   if (log2S == 13) {
     k_sym_block<13, 512><<<grid_rows(count, 1, 152 * 8), 512, sm, s>>>(A, B, perm, count, nnz_row, err);
   }
+  return 1;
 }
 
-void launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                        int32_t* counter, int32_t* nnz_row, int32_t* win_slot, uint16_t* blockcnt,
                        int64_t nblocks, int32_t* cursor, int num_sms, uint32_t* err,
                        cudaStream_t s) {
-  if (count <= 0) return;
+  if (count <= 0) return 0;
   const size_t sm = size_t(kSymWinBits / 32) * 4;
   cudaFuncSetAttribute(k_sym_window, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
@@ -265,6 +268,7 @@ void launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, in
   k_sym_window<<<static_cast<unsigned>(g), kWinThreads, sm, s>>>(A, B, perm, count, counter, nnz_row,
                                                                  win_slot, blockcnt, nblocks, cursor,
                                                                  err);
+  return 1;
 }
 
 }  // namespace spg

@@ -23,53 +23,59 @@ struct Summary {
   int64_t class_off[kMaxClasses + 1];
   int64_t total;          // sum of P_i (plan) or of nnz(C_i) (symbolic)
   int64_t max_row;        // max P_i
+  unsigned long long cls_sums[kMaxClasses][3];  // per numeric class: sum P_i, sum nnz(A_i), sum nnz(C_i)
   uint32_t err;
   uint32_t pad;
 };
 
 // ---- setup / scan kernels (k_setup.cu)
-void launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t s);
-void launch_validate(const DevCsr& M, uint32_t* err, cudaStream_t s);
-void launch_count(const DevCsr& A, const DevCsr& B, ClassParams cp, int64_t* P, int32_t* nnz_row,
+int launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t s);
+int launch_validate(const DevCsr& M, uint32_t* err, cudaStream_t s);
+int launch_count(const DevCsr& A, const DevCsr& B, ClassParams cp, int64_t* P, int32_t* nnz_row,
                   int32_t* tile_hist, int64_t* tile_sum, int64_t* tile_max, cudaStream_t s);
-void launch_class_scan(int64_t ntiles, int nclasses, int32_t* tile_hist, const int64_t* tile_sum,
+int launch_class_scan(int64_t ntiles, int nclasses, int32_t* tile_hist, const int64_t* tile_sum,
                        const int64_t* tile_max, int64_t* tile_sum_off, Summary* summary,
                        cudaStream_t s);
-void launch_scatter_sym(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* tile_hist,
+int launch_scatter_sym(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* tile_hist,
                         int32_t* perm, cudaStream_t s);
-void launch_num_tiles(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* nnz_row,
-                      int32_t* tile_hist, int64_t* tile_sum, cudaStream_t s);
-void launch_scatter_num(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* nnz_row,
+int launch_num_tiles(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* nnz_row,
+                      int32_t* tile_hist, int64_t* tile_sum, unsigned long long* cls_sums,
+                      cudaStream_t s);
+int launch_scatter_num(const DevCsr& A, ClassParams cp, const int64_t* P, const int32_t* nnz_row,
                         const int32_t* tile_hist, const int64_t* tile_sum_off, int32_t* perm,
                         int64_t* c_off, cudaStream_t s);
-void launch_write_rowptr(const int64_t* c_off, int64_t m1, void* out, int idx64, cudaStream_t s);
+int launch_write_rowptr(const int64_t* c_off, int64_t m1, void* out, int idx64, cudaStream_t s);
 
 // ---- symbolic kernels (k_symbolic.cu). Each handles perm[start, start+count).
-void launch_sym_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+int launch_sym_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                      int32_t* nnz_row, cudaStream_t s);
-void launch_sym_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+int launch_sym_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                      int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s);
-void launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+int launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                       int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s);
-void launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                        int32_t* counter, int32_t* nnz_row, int32_t* win_slot, uint16_t* blockcnt,
                        int64_t nblocks, int32_t* cursor, int num_sms, uint32_t* err,
                        cudaStream_t s);
 
 // ---- numeric kernels, FP64 (k_numeric.cu)
-void launch_num_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+int launch_num_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                      const int64_t* c_off, int32_t* ccol, double* cval, uint32_t* err,
                      cudaStream_t s);
-void launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                      int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
                      uint32_t* err, cudaStream_t s);
-void launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
+int launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                       int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
                       uint32_t* err, cudaStream_t s);
-void launch_num_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
-                       int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
-                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, int32_t* cursor,
-                       int32_t hash_fill, int32_t* ccol, double* cval, int num_sms,
-                       uint32_t* err, cudaStream_t s);
+
+// ---- windowed numeric pass and the column-block split table of B (k_window.cu)
+int64_t split_table_bytes(int64_t brows, int64_t nblocks);
+int launch_bsplit(const DevCsr& B, int64_t nblocks, int32_t* split, cudaStream_t s);
+int launch_num_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                      int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
+                      const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
+                      int32_t hash_fill, int32_t* ccol, double* cval, int num_sms, uint32_t* err,
+                      cudaStream_t s);
 
 }  // namespace spg

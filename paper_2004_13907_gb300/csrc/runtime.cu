@@ -46,6 +46,31 @@ spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s) {
   return error_bits_status(h.err);
 }
 
+void stage_begin(spgemm_plan_s* p, int stage, cudaStream_t s) {
+  if (!p->opts.record_timings) return;
+  if (!p->ev_made) {
+    for (int i = 0; i < SPGEMM_NUM_STAGES; ++i)
+      for (int j = 0; j < 2; ++j) cudaEventCreate(&p->ev[i][j]);
+    p->ev_made = true;
+  }
+  cudaEventRecord(p->ev[stage][0], s);
+}
+
+void stage_end(spgemm_plan_s* p, int stage, int launches, cudaStream_t s) {
+  p->launches += launches;
+  if (!p->opts.record_timings || !p->ev_made) return;
+  cudaEventRecord(p->ev[stage][1], s);
+  p->ev_rec[stage] = true;
+  p->ev_launches[stage] = launches;
+}
+
+void destroy_events(spgemm_plan_s* p) {
+  if (!p->ev_made) return;
+  for (int i = 0; i < SPGEMM_NUM_STAGES; ++i)
+    for (int j = 0; j < 2; ++j) cudaEventDestroy(p->ev[i][j]);
+  p->ev_made = false;
+}
+
 spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_csr_in* B,
                        cudaStream_t s) {
   spgemm_status st = SPGEMM_OK;
@@ -54,16 +79,18 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   // internal int64 row pointers
   const int64_t* arp = static_cast<const int64_t*>(A->row_ptr);
   const int64_t* brp = static_cast<const int64_t*>(B->row_ptr);
+  int conv = 0;
+  stage_begin(p, SPGEMM_STAGE_VALIDATE, s);
   if (!A->idx64_rowptr) {
     int64_t* t = ws_get<int64_t>(p, m + 1, &st);
     if (st) return st;
-    launch_rowptr_to64(static_cast<const int32_t*>(A->row_ptr), t, m + 1, s);
+    conv += launch_rowptr_to64(static_cast<const int32_t*>(A->row_ptr), t, m + 1, s);
     arp = t;
   }
   if (!B->idx64_rowptr) {
     int64_t* t = ws_get<int64_t>(p, B->rows + 1, &st);
     if (st) return st;
-    launch_rowptr_to64(static_cast<const int32_t*>(B->row_ptr), t, B->rows + 1, s);
+    conv += launch_rowptr_to64(static_cast<const int32_t*>(B->row_ptr), t, B->rows + 1, s);
     brp = t;
   }
   p->A = DevCsr{m, A->cols, A->nnz, arp, A->col, A->val};
@@ -95,17 +122,22 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
 
   Summary h;
   if (o.validate) {
-    launch_validate(p->A, &p->summary->err, s);
-    launch_validate(p->B, &p->summary->err, s);
+    conv += launch_validate(p->A, &p->summary->err, s);
+    conv += launch_validate(p->B, &p->summary->err, s);
+    stage_end(p, SPGEMM_STAGE_VALIDATE, conv, s);
     if ((st = cuda_status(cudaGetLastError(), "launching validation")) != SPGEMM_OK) return st;
     if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
     if (h.err) return error_bits_status(h.err);
+  } else {
+    stage_end(p, SPGEMM_STAGE_VALIDATE, conv, s);
   }
   if (m > 0) {
-    launch_count(p->A, p->B, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum, p->tile_max, s);
-    launch_class_scan(p->ntiles, kSymNumClasses, p->tile_hist, p->tile_sum, p->tile_max, nullptr,
-                      p->summary, s);
-    launch_scatter_sym(p->A, p->cp, p->P, p->tile_hist, p->perm_s, s);
+    stage_begin(p, SPGEMM_STAGE_COUNT, s);
+    int nl = launch_count(p->A, p->B, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum, p->tile_max, s);
+    nl += launch_class_scan(p->ntiles, kSymNumClasses, p->tile_hist, p->tile_sum, p->tile_max, nullptr,
+                            p->summary, s);
+    nl += launch_scatter_sym(p->A, p->cp, p->P, p->tile_hist, p->perm_s, s);
+    stage_end(p, SPGEMM_STAGE_COUNT, nl, s);
     if ((st = cuda_status(cudaGetLastError(), "launching the plan kernels")) != SPGEMM_OK) return st;
     if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
     if (h.err) return error_bits_status(h.err);
@@ -135,24 +167,36 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
   auto cnt = [&](int c) { return p->sym_off[c + 1] - p->sym_off[c]; };
   uint32_t* err = &p->summary->err;
   if (m > 0) {
-    launch_sym_window(p->A, p->B, seg(kSymWin0), p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0],
-                      p->counters + 0, p->nnz_row, p->win_slot, p->blockcnt, p->nblocks, p->cursor,
-                      p->num_sms, err, s);
-    launch_sym_block(13, p->A, p->B, seg(kSymBlock), cnt(kSymBlock), p->nnz_row, err, s);
-    launch_sym_warp(11, p->A, p->B, seg(kSymWarp3), cnt(kSymWarp3), p->nnz_row, err, s);
-    launch_sym_warp(9, p->A, p->B, seg(kSymWarp2), cnt(kSymWarp2), p->nnz_row, err, s);
-    launch_sym_warp(7, p->A, p->B, seg(kSymWarp1), cnt(kSymWarp1), p->nnz_row, err, s);
-    launch_sym_tiny(p->A, p->B, seg(kSymTiny), cnt(kSymTiny), p->nnz_row, s);
-    launch_num_tiles(p->A, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum, s);
-    launch_class_scan(p->ntiles, kNumNumClasses, p->tile_hist, p->tile_sum, nullptr, p->tile_sum_off,
-                      p->summary, s);
-    launch_scatter_num(p->A, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum_off, p->perm_n,
-                       p->c_off, s);
+    int nl;
+    stage_begin(p, SPGEMM_STAGE_SYM_WINDOW, s);
+    nl = launch_sym_window(p->A, p->B, seg(kSymWin0), p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0],
+                           p->counters + 0, p->nnz_row, p->win_slot, p->blockcnt, p->nblocks, p->cursor,
+                           p->num_sms, err, s);
+    stage_end(p, SPGEMM_STAGE_SYM_WINDOW, nl, s);
+    stage_begin(p, SPGEMM_STAGE_SYM_BLOCK, s);
+    nl = launch_sym_block(13, p->A, p->B, seg(kSymBlock), cnt(kSymBlock), p->nnz_row, err, s);
+    stage_end(p, SPGEMM_STAGE_SYM_BLOCK, nl, s);
+    stage_begin(p, SPGEMM_STAGE_SYM_WARP, s);
+    nl = launch_sym_warp(11, p->A, p->B, seg(kSymWarp3), cnt(kSymWarp3), p->nnz_row, err, s);
+    nl += launch_sym_warp(9, p->A, p->B, seg(kSymWarp2), cnt(kSymWarp2), p->nnz_row, err, s);
+    nl += launch_sym_warp(7, p->A, p->B, seg(kSymWarp1), cnt(kSymWarp1), p->nnz_row, err, s);
+    stage_end(p, SPGEMM_STAGE_SYM_WARP, nl, s);
+    stage_begin(p, SPGEMM_STAGE_SYM_TINY, s);
+    nl = launch_sym_tiny(p->A, p->B, seg(kSymTiny), cnt(kSymTiny), p->nnz_row, s);
+    stage_end(p, SPGEMM_STAGE_SYM_TINY, nl, s);
+    stage_begin(p, SPGEMM_STAGE_SYM_SCAN, s);
+    nl = launch_num_tiles(p->A, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum, &p->summary->cls_sums[0][0], s);
+    nl += launch_class_scan(p->ntiles, kNumNumClasses, p->tile_hist, p->tile_sum, nullptr, p->tile_sum_off,
+                            p->summary, s);
+    nl += launch_scatter_num(p->A, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum_off, p->perm_n,
+                             p->c_off, s);
+    stage_end(p, SPGEMM_STAGE_SYM_SCAN, nl, s);
     if ((st = cuda_status(cudaGetLastError(), "launching the symbolic kernels")) != SPGEMM_OK) return st;
     Summary h;
     if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
     if (h.err) return error_bits_status(h.err);
     std::memcpy(p->num_off, h.class_off, sizeof(p->num_off));
+    std::memcpy(p->cls_sums, h.cls_sums, sizeof(p->cls_sums));
     p->nnz_c = h.total;
   } else {
     if ((st = cuda_status(cudaStreamSynchronize(s), "symbolic pass")) != SPGEMM_OK) return st;
@@ -165,24 +209,44 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
 spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
   spgemm_status st;
   const int64_t m = p->A.rows;
-  launch_write_rowptr(p->c_off, m + 1, C->row_ptr, C->idx64_rowptr, s);
   if (p->prec != SPGEMM_F64)
     return set_error_msg(SPGEMM_ERR_UNSUPPORTED, "this precision is not built yet");
+  stage_begin(p, SPGEMM_STAGE_NUM_ROWPTR, s);
+  int nl = launch_write_rowptr(p->c_off, m + 1, C->row_ptr, C->idx64_rowptr, s);
+  stage_end(p, SPGEMM_STAGE_NUM_ROWPTR, nl, s);
   if (m > 0) {
     auto seg = [&](int c) { return p->perm_n + p->num_off[c]; };
     auto cnt = [&](int c) { return p->num_off[c + 1] - p->num_off[c]; };
     uint32_t* err = &p->summary->err;
     double* cval = static_cast<double*>(C->val);
-    launch_num_window(p->A, p->B, seg(kNumWin0), p->num_off[kNumWin3 + 1] - p->num_off[kNumWin0],
-                      p->counters + 1, p->c_off, p->win_slot, p->blockcnt, p->nblocks,
-                      p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0], p->cursor,
-                      p->opts.window_hash_fill, C->col, cval, p->num_sms, err, s);
-    launch_num_block(13, p->A, p->B, seg(kNumBlock2), cnt(kNumBlock2), p->c_off, C->col, cval, err, s);
-    launch_num_block(11, p->A, p->B, seg(kNumBlock1), cnt(kNumBlock1), p->c_off, C->col, cval, err, s);
-    launch_num_warp(10, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, cval, err, s);
-    launch_num_warp(8, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, cval, err, s);
-    launch_num_warp(6, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, cval, err, s);
-    launch_num_tiny(p->A, p->B, seg(kNumTiny), cnt(kNumTiny), p->c_off, C->col, cval, err, s);
+    stage_begin(p, SPGEMM_STAGE_NUM_WINDOW, s);
+    const int64_t nwin = p->num_off[kNumWin3 + 1] - p->num_off[kNumWin0];
+    nl = 0;
+    if (nwin > 0 && !p->split_tried) {
+      // split table of B, once per plan, when it fits the budget (else the kernel searches)
+      p->split_tried = true;
+      const int64_t bytes = split_table_bytes(p->B.rows, p->nblocks);
+      if (bytes <= (int64_t(p->opts.window_split_max_mb) << 20)) {
+        p->split = static_cast<int32_t*>(p->ws.get(static_cast<size_t>(bytes)));
+        if (p->split) nl += launch_bsplit(p->B, p->nblocks, p->split, s);
+      }
+    }
+    nl += launch_num_window(p->A, p->B, seg(kNumWin0), nwin, p->counters + 1, p->c_off, p->win_slot,
+                            p->blockcnt, p->nblocks, p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0],
+                            p->split, p->opts.window_hash_fill, C->col, cval, p->num_sms, err, s);
+    stage_end(p, SPGEMM_STAGE_NUM_WINDOW, nl, s);
+    stage_begin(p, SPGEMM_STAGE_NUM_BLOCK, s);
+    nl = launch_num_block(13, p->A, p->B, seg(kNumBlock2), cnt(kNumBlock2), p->c_off, C->col, cval, err, s);
+    nl += launch_num_block(11, p->A, p->B, seg(kNumBlock1), cnt(kNumBlock1), p->c_off, C->col, cval, err, s);
+    stage_end(p, SPGEMM_STAGE_NUM_BLOCK, nl, s);
+    stage_begin(p, SPGEMM_STAGE_NUM_WARP, s);
+    nl = launch_num_warp(10, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, cval, err, s);
+    nl += launch_num_warp(8, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, cval, err, s);
+    nl += launch_num_warp(6, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, cval, err, s);
+    stage_end(p, SPGEMM_STAGE_NUM_WARP, nl, s);
+    stage_begin(p, SPGEMM_STAGE_NUM_TINY, s);
+    nl = launch_num_tiny(p->A, p->B, seg(kNumTiny), cnt(kNumTiny), p->c_off, C->col, cval, err, s);
+    stage_end(p, SPGEMM_STAGE_NUM_TINY, nl, s);
   }
   if ((st = cuda_status(cudaGetLastError(), "launching the numeric kernels")) != SPGEMM_OK) return st;
   p->state = 2;

@@ -54,6 +54,8 @@ struct spgemm_plan_s {
   uint16_t* blockcnt = nullptr;
   int64_t nblocks = 0;
   int32_t* cursor = nullptr;
+  int32_t* split = nullptr;          // column-block split table of B (windowed numeric rows)
+  bool split_tried = false;
   // FP32-compensated path
   int32_t* rerun_flag = nullptr;     // per row: 1 = recompute in FP64
   int32_t* rerun_list = nullptr;
@@ -63,6 +65,13 @@ struct spgemm_plan_s {
   int64_t max_row_products = 0;
   int64_t nnz_c = -1;
   int64_t f32c_rerun_rows = 0;
+  int64_t launches = 0;
+  unsigned long long cls_sums[spg::kMaxClasses][3] = {};
+  // stage timing (record_timings)
+  cudaEvent_t ev[16][2] = {};
+  bool ev_made = false;
+  bool ev_rec[16] = {};
+  int ev_launches[16] = {};
   int state = 0;
 };
 
@@ -73,5 +82,8 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
 spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s);
 spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s);
 spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s);
+void stage_begin(spgemm_plan_s* p, int stage, cudaStream_t s);
+void stage_end(spgemm_plan_s* p, int stage, int launches, cudaStream_t s);
+void destroy_events(spgemm_plan_s* p);
 
 }  // namespace spg
