@@ -103,7 +103,9 @@ typedef struct spgemm_opts {
                                  numeric: rows with nnz(C_i) <= warp_max/2 (default 1024) */
   int32_t block_max;          /* rows up to this size use a block-wide hash table; larger
                                  rows take the windowed path (default 4096) */
-  int32_t window_hash_fill;   /* max entries of C per hash window (default 4800) */
+  int32_t window_hash_fill;   /* windowed rows: consecutive column blocks are merged into one
+                                 window while it holds at most this many entries of C (default
+                                 and maximum 8192; a single block is always one window) */
   int32_t force_window;       /* 1: every non-empty row takes the windowed path (tests) */
   int64_t rowptr32_limit;     /* nnz(C) >= this requires an int64 row_ptr (default 2^31-1;
                                  tests lower it) */

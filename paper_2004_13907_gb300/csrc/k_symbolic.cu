@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NT) k_sym_block(DevCsr A, DevCsr B, const int3
 
 // Windowed symbolic pass, one row per block at a time (rows handed out by an atomic
 // counter, heaviest class first).
-__global__ void __launch_bounds__(kWinThreads, 1) k_sym_window(DevCsr A, DevCsr B,
+__global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevCsr B,
                                                                const int32_t* __restrict__ perm,
                                                                int64_t count, int32_t* counter,
                                                                int32_t* __restrict__ nnz_row,
@@ -142,13 +142,13 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_sym_window(DevCsr A, DevCsr 
                                                                int64_t nblocks, int32_t* cursor,
                                                                uint32_t* err) {
   extern __shared__ uint32_t bm[];  // kSymWinBits / 32 words
-  __shared__ int32_t s_excl[kWinThreads];
-  __shared__ int64_t s_bs[kWinThreads];
+  __shared__ int32_t s_excl[kSymWinThreads];
+  __shared__ int64_t s_bs[kSymWinThreads];
   __shared__ int32_t s_scan[33];
   __shared__ int32_t s_idx;
   __shared__ unsigned long long s_total;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int kWarps = kWinThreads / 32;
+  constexpr int kWarps = kSymWinThreads / 32;
   const int64_t n = B.cols;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -166,11 +166,11 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_sym_window(DevCsr A, DevCsr 
     for (int64_t w0 = 0; w0 < n; w0 += kSymWinBits) {
       const int64_t wend = (w0 + kSymWinBits < n) ? w0 + kSymWinBits : n;
       const int nwords = static_cast<int>((wend - w0 + 31) >> 5);
-      for (int t = threadIdx.x; t < nwords; t += kWinThreads) bm[t] = 0u;
+      for (int t = threadIdx.x; t < nwords; t += kSymWinThreads) bm[t] = 0u;
       __syncthreads();
       if (n <= kSymWinBits) {
         // one window covers every column: no cursors, products handed out flattened
-        block_for_each_product<kWinThreads>(A, B, a0, na, s_excl, s_bs, s_scan, [&](int64_t j, int64_t) {
+        block_for_each_product<kSymWinThreads>(A, B, a0, na, s_excl, s_bs, s_scan, [&](int64_t j, int64_t) {
           const int32_t c = B.col[j];
           atomicOr(&bm[c >> 5], 1u << (c & 31));
         });
@@ -265,7 +265,7 @@ int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int
   cudaFuncSetAttribute(k_sym_window, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   const int64_t g = count < num_sms ? count : num_sms;
-  k_sym_window<<<static_cast<unsigned>(g), kWinThreads, sm, s>>>(A, B, perm, count, counter, nnz_row,
+  k_sym_window<<<static_cast<unsigned>(g), kSymWinThreads, sm, s>>>(A, B, perm, count, counter, nnz_row,
                                                                  win_slot, blockcnt, nblocks, cursor,
                                                                  err);
   return 1;

@@ -3,16 +3,17 @@
 //
 // The columns of C are cut into blocks of kBlockCols. The symbolic pass counted, for each
 // windowed row, the entries of C_i in every block. The numeric pass takes the blocks of a
-// row in column order and groups them into windows:
-//  * a block holding more than `hash_fill` entries is a dense window: an FP64 array indexed
-//    by column minus the window start, plus a bitmap of the columns that received a
-//    partial product;
-//  * a run of consecutive blocks holding at most `hash_fill` entries together is a hash
-//    window: a hash table (column -> FP64 sum) of kHashWinSlots slots; at the end its keys
-//    are marked in a bitmap of the window's columns.
-// Reading the bitmap word by word gives the row's columns in ascending order, so no sort is
-// needed (Algorithm 1 sorts the partial products of a row and emits one entry per column of
-// COLB, Sec. III-A; here the order comes from the bitmap).
+// row in column order and groups consecutive blocks into windows of at most kRankCap entries
+// of C spanning at most kSpanBlocks blocks. Each window is done in two passes over its partial
+// products:
+//  1. mark: set one bit per column that receives a partial product (a bitmap of the window's
+//     columns); a prefix count over the bitmap then gives every column its rank, i.e. its
+//     position among the window's columns in ascending order;
+//  2. accumulate: add a_ik * b_kj into an FP64 array indexed by the rank of column j.
+// The window is written out by rank: values straight from the rank-indexed array (coalesced),
+// columns from the bitmap. The output is therefore sorted by column without any sort
+// (Algorithm 1 sorts the partial products of a row and emits one entry per column of COLB,
+// Sec. III-A; here the order comes from the bitmap).
 //
 // Inside a window, every A entry (k, a_ik) contributes the part of B row k whose columns fall
 // in the window. The split table holds, for every row k of B and every block boundary b, the
@@ -31,16 +32,24 @@ namespace spg {
 
 namespace {
 
-constexpr int kWinRegionBytes = kBlockCols * 8;                   // dense FP64 window
-constexpr int kWinBitmapWords = kHashWinBlocks * kBlockWords;     // hash window bitmap
-constexpr int kWinEntBytes = kWinThreads * (8 + 8 + 4);           // per-entry chunk state
-constexpr int kWinSmemBytes = kWinRegionBytes + kWinBitmapWords * 4 + kWinEntBytes;
-constexpr int kHashWinLog2 = 13;
-static_assert((1 << kHashWinLog2) == kHashWinSlots, "hash window size");
-static_assert(kHashWinSlots * 12 <= kWinRegionBytes, "hash window fits the region");
-static_assert(kWinSmemBytes <= 227 * 1024, "shared memory budget");
+constexpr int kRankCap = 8192;                     // entries of C per window (>= kBlockCols)
+constexpr int kSpanBlocks = 64;                    // blocks a window may span (512K columns)
+constexpr int kSpanWords = kSpanBlocks * kBlockWords;    // bitmap words, 16384
+constexpr int kGroupWords = 64;                    // words per prefix group
+constexpr int kNumThreads = 1024;                  // threads of the windowed numeric kernel
+constexpr int kWordsPerThread = kSpanWords / kNumThreads;
+constexpr int kCntCache = 1024;                    // block counts kept in shared memory
+constexpr int kSmemVals = kRankCap * 8;
+constexpr int kSmemBits = kSpanWords * 4;
+constexpr int kSmemPre = kSpanWords * 2;
+constexpr int kSmemGrp = (kSpanWords / kGroupWords) * 4;
+constexpr int kSmemEnt = kNumThreads * (8 + 8 + 8 + 4 + 4);
+constexpr int kWinSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemGrp + kSmemEnt + kCntCache * 2;
+static_assert(kRankCap >= kBlockCols, "a window must hold any single block");
+static_assert(kWordsPerThread * kNumThreads == kSpanWords, "words per thread");
+static_assert(kGroupWords % kWordsPerThread == 0, "a thread's words lie in one group");
+static_assert(kWinSmemBytes + 1024 <= 227 * 1024, "shared memory budget");
 
-enum : int { kWinDone = 0, kWinDense = 1, kWinHash = 2 };
 
 // Split table: one warp per row k of B writes split[k * (nblocks + 1) + b] for b in
 // [0, nblocks]: the offset within row k of its first entry with column >= b * kBlockCols.
@@ -48,8 +57,7 @@ __global__ void __launch_bounds__(256) k_bsplit(DevCsr B, int64_t nblocks, int32
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  constexpr int kShift = 14;
-  static_assert((1 << kShift) == kBlockCols, "block width");
+  constexpr int kShift = kBlockShift;
   for (int64_t k = gw; k < B.rows; k += nw) {
     const int64_t s = B.rp[k];
     const int32_t len = static_cast<int32_t>(B.rp[k + 1] - s);
@@ -82,59 +90,68 @@ __device__ __forceinline__ int32_t lower_bound_col(const int32_t* col, int32_t l
   return lo;
 }
 
-__device__ __forceinline__ void win_accumulate(int wtype, double* dense, int32_t* hkeys, double* hvals,
-                                               uint32_t* bm, int64_t w0, int64_t w1, int32_t c, double v,
-                                               uint32_t* err) {
-  if (c < w0 || c >= w1) {        // cannot happen with a consistent split table
-    set_error(err, kErrWindowPlan);
-    return;
-  }
-  const int32_t rel = static_cast<int32_t>(c - w0);
-  if (wtype == kWinDense) {
-    atomicAdd(&dense[rel], v);
-    atomicOr(&bm[rel >> 5], 1u << (rel & 31));
+// Per-entry segment of the current window for the A entry in chunk slot t (e < na).
+struct Seg { int64_t bs; int32_t len; };
+
+__device__ __forceinline__ Seg entry_segment(const DevCsr& A, const DevCsr& B, const int32_t* split,
+                                             int64_t nblocks, int64_t a0, int64_t e, bool resident,
+                                             const int32_t* e_k, const int64_t* e_rs, double* e_av,
+                                             int64_t b0, int64_t b1, int64_t w0, int64_t w1) {
+  int32_t k;
+  int64_t rs;
+  if (resident) {
+    k = e_k[threadIdx.x];
+    rs = e_rs[threadIdx.x];
   } else {
-    const int32_t key = c + 1;
-    uint32_t h = hash_slot(key, kHashWinLog2);
-    for (int probe = 0; probe < kHashWinSlots; ++probe) {
-      const int32_t cur = *reinterpret_cast<volatile int32_t*>(&hkeys[h]);
-      if (cur == key) { atomicAdd(&hvals[h], v); return; }
-      if (cur == 0) {
-        const int32_t old = atomicCAS(&hkeys[h], 0, key);
-        if (old == 0 || old == key) { atomicAdd(&hvals[h], v); return; }
-      }
-      h = (h + 1) & (kHashWinSlots - 1);
-    }
-    set_error(err, kErrHashFull);
+    k = A.col[a0 + e];
+    rs = B.rp[k];
+    e_av[threadIdx.x] = static_cast<const double*>(A.val)[a0 + e];
   }
+  int32_t s0, s1;
+  if (split) {
+    const int32_t* sp = split + int64_t(k) * (nblocks + 1);
+    s0 = sp[b0];
+    s1 = sp[b1];
+  } else {
+    const int32_t rl = static_cast<int32_t>(B.rp[k + 1] - rs);
+    s0 = lower_bound_col(B.col + rs, rl, w0);
+    s1 = lower_bound_col(B.col + rs, rl, w1);
+  }
+  return Seg{rs + s0, s1 - s0};
 }
 
-// Shared layout (dynamic): [0, 128 KB): dense FP64[kBlockCols] | hash {keys int32[8192] at 0,
-// vals FP64[8192] at 32 KB}; the window bitmap; the chunk's per-entry state. Hash keys are
-// stored as column + 1 so that all-zero bytes are the clean state of both layouts.
-__global__ void __launch_bounds__(kWinThreads, 1) k_num_window(
+// Shared layout (dynamic): rank-indexed FP64 values [kRankCap]; window bitmap [kSpanWords];
+// in-group word prefix (uint16) [kSpanWords]; group prefix (int32) [kSpanWords / 64]; per-entry
+// state of the current chunk of A entries (B row start, a_ik, segment start, B row number,
+// segment prefix); the row's block counts. The values and the bitmap are all zero between
+// windows. A row whose A entries fit one chunk keeps their B row numbers, B row starts and
+// values across all its windows.
+__global__ void __launch_bounds__(kNumThreads, 1) k_num_window(
     DevCsr A, DevCsr B, const int32_t* __restrict__ perm, int64_t count, int32_t* counter,
     const int64_t* __restrict__ c_off, const int32_t* __restrict__ win_slot,
     const uint16_t* __restrict__ blockcnt, int64_t nblocks, int64_t nslots,
-    const int32_t* __restrict__ split, int32_t hash_fill, int32_t* __restrict__ ccol,
+    const int32_t* __restrict__ split, int32_t merge_cap, int32_t* __restrict__ ccol,
     double* __restrict__ cval, uint32_t* err) {
   extern __shared__ __align__(16) unsigned char win_smem[];
-  double* dense = reinterpret_cast<double*>(win_smem);
-  int32_t* hkeys = reinterpret_cast<int32_t*>(win_smem);
-  double* hvals = reinterpret_cast<double*>(win_smem + kHashWinSlots * 4);
-  uint32_t* bm = reinterpret_cast<uint32_t*>(win_smem + kWinRegionBytes);
-  int64_t* e_bs = reinterpret_cast<int64_t*>(win_smem + kWinRegionBytes + kWinBitmapWords * 4);
-  double* e_av = reinterpret_cast<double*>(e_bs + kWinThreads);
-  int32_t* e_excl = reinterpret_cast<int32_t*>(e_av + kWinThreads);
-  __shared__ int64_t s_scan64[33];
+  double* vals = reinterpret_cast<double*>(win_smem);
+  uint32_t* bm = reinterpret_cast<uint32_t*>(win_smem + kSmemVals);
+  uint16_t* pre = reinterpret_cast<uint16_t*>(win_smem + kSmemVals + kSmemBits);
+  int32_t* grp = reinterpret_cast<int32_t*>(win_smem + kSmemVals + kSmemBits + kSmemPre);
+  unsigned char* ent = win_smem + kSmemVals + kSmemBits + kSmemPre + kSmemGrp;
+  int64_t* e_rs = reinterpret_cast<int64_t*>(ent);                 // B row start
+  double* e_av = reinterpret_cast<double*>(e_rs + kNumThreads);    // a_ik
+  int64_t* e_bs = reinterpret_cast<int64_t*>(e_av + kNumThreads);  // window segment start
+  int32_t* e_k = reinterpret_cast<int32_t*>(e_bs + kNumThreads);   // B row number
+  int32_t* e_excl = e_k + kNumThreads;                              // segment prefix
+  uint16_t* s_cnt = reinterpret_cast<uint16_t*>(e_excl + kNumThreads);
   __shared__ int32_t s_scan32[33];
   __shared__ int32_t s_ctl[6];
   const int64_t n = B.cols;
   const double* av_ = static_cast<const double*>(A.val);
   const double* bv_ = static_cast<const double*>(B.val);
-  constexpr int kClearBytes = kWinRegionBytes + kWinBitmapWords * 4;
+  const bool cnt_cached = nblocks <= kCntCache;
 
-  for (int t = threadIdx.x; t < kClearBytes / 16; t += kWinThreads)
+  for (int t = threadIdx.x; t < (kSmemVals + kSmemBits) / 16; t += kNumThreads)
     reinterpret_cast<uint4*>(win_smem)[t] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
 
@@ -150,148 +167,165 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_num_window(
       __syncthreads();
       continue;
     }
-    const uint16_t* cnts = blockcnt + slot * nblocks;
+    const uint16_t* gcnt = blockcnt + slot * nblocks;
     const int64_t a0 = A.rp[i];
     const int64_t na = A.rp[i + 1] - a0;
+    const bool resident = na <= kNumThreads;
+    if (cnt_cached)
+      for (int64_t b = threadIdx.x; b < nblocks; b += kNumThreads) s_cnt[b] = gcnt[b];
+    if (resident && threadIdx.x < na) {
+      const int32_t k = A.col[a0 + threadIdx.x];
+      e_k[threadIdx.x] = k;
+      e_rs[threadIdx.x] = B.rp[k];
+      e_av[threadIdx.x] = av_[a0 + threadIdx.x];
+    }
+    const uint16_t* cnts = cnt_cached ? s_cnt : gcnt;
     int64_t out = c_off[i];
     const int64_t out_end = c_off[i + 1];
     int64_t next_b = 0;   // meaningful in thread 0 only
+    __syncthreads();
     for (;;) {
       if (threadIdx.x == 0) {
         int64_t b = next_b;
         while (b < nblocks && cnts[b] == 0) ++b;
         if (b >= nblocks) {
-          s_ctl[1] = kWinDone;
-        } else if (cnts[b] > hash_fill) {
-          s_ctl[1] = kWinDense; s_ctl[2] = static_cast<int32_t>(b); s_ctl[3] = static_cast<int32_t>(b + 1);
-          s_ctl[4] = cnts[b];
-          next_b = b + 1;
+          s_ctl[1] = 0;
         } else {
           int64_t e = b;
           int32_t sum = 0;
-          while (e < nblocks && e - b < kHashWinBlocks && sum + cnts[e] <= hash_fill) { sum += cnts[e]; ++e; }
-          s_ctl[1] = kWinHash; s_ctl[2] = static_cast<int32_t>(b); s_ctl[3] = static_cast<int32_t>(e);
+          do { sum += cnts[e]; ++e; }
+          while (e < nblocks && e - b < kSpanBlocks && sum + cnts[e] <= merge_cap);
+          s_ctl[1] = 1; s_ctl[2] = static_cast<int32_t>(b); s_ctl[3] = static_cast<int32_t>(e);
           s_ctl[4] = sum;
           next_b = e;
         }
       }
       __syncthreads();
-      const int wtype = s_ctl[1];
-      if (wtype == kWinDone) break;
+      if (s_ctl[1] == 0) break;
       const int64_t b0 = s_ctl[2], b1 = s_ctl[3];
       const int64_t w0 = b0 * kBlockCols;
       const int64_t w1 = b1 * kBlockCols < n ? b1 * kBlockCols : n;
       const int32_t expect = s_ctl[4];
-      // accumulate, one chunk of A entries at a time
-      for (int64_t base = 0; base < na; base += kWinThreads) {
+      const int nwords = static_cast<int>((w1 - w0 + 31) >> 5);
+
+      // pass 1: mark the window's columns
+      int32_t p1_total = 0;   // products of the (single) chunk, reused by pass 2 when na fits one chunk
+      for (int64_t base = 0; base < na; base += kNumThreads) {
         const int64_t e = base + threadIdx.x;
-        int32_t len = 0;
-        int64_t bs = 0;
-        double av = 0.0;
-        if (e < na) {
-          const int32_t k = A.col[a0 + e];
-          const int64_t rs = B.rp[k];
-          int32_t s0, s1;
-          if (split) {
-            const int32_t* sp = split + int64_t(k) * (nblocks + 1);
-            s0 = sp[b0];
-            s1 = sp[b1];
-          } else {
-            const int32_t rl = static_cast<int32_t>(B.rp[k + 1] - rs);
-            s0 = lower_bound_col(B.col + rs, rl, w0);
-            s1 = lower_bound_col(B.col + rs, rl, w1);
-          }
-          len = s1 - s0;
-          bs = rs + s0;
-          av = av_[a0 + e];
-        }
+        Seg sg{0, 0};
+        if (e < na) sg = entry_segment(A, B, split, nblocks, a0, e, resident, e_k, e_rs, e_av, b0, b1, w0, w1);
         int32_t total;
-        const int32_t ex = block_excl_scan<int32_t>(len, s_scan32, &total);
+        const int32_t ex = block_excl_scan<int32_t>(sg.len, s_scan32, &total);
         e_excl[threadIdx.x] = ex;
-        e_bs[threadIdx.x] = bs;
-        e_av[threadIdx.x] = av;
-        const int nvalid = static_cast<int>(na - base < kWinThreads ? na - base : kWinThreads);
+        e_bs[threadIdx.x] = sg.bs;
+        p1_total = total;
+        const int nvalid = static_cast<int>(na - base < kNumThreads ? na - base : kNumThreads);
         __syncthreads();
         int owner = 0;
-        for (int32_t p = threadIdx.x; p < total; p += 2 * kWinThreads) {
+        for (int32_t p = threadIdx.x; p < total; p += kNumThreads) {
+          owner = find_owner(e_excl, nvalid, p, owner);
+          const int32_t c = B.col[e_bs[owner] + (p - e_excl[owner])];
+          const int64_t rel = c - w0;
+          if (rel >= 0 && rel < w1 - w0) atomicOr(&bm[rel >> 5], 1u << (rel & 31));
+          else set_error(err, kErrWindowPlan);
+        }
+        if (na > kNumThreads) __syncthreads();
+      }
+      __syncthreads();
+      // rank prefix: each thread owns kWordsPerThread consecutive words of one group
+      {
+        const int wlo = threadIdx.x * kWordsPerThread;
+        int c = 0;
+#pragma unroll
+        for (int t = 0; t < kWordsPerThread; ++t) c += __popc(bm[wlo + t]);
+        int32_t tot;
+        const int32_t tpre = block_excl_scan<int32_t>(c, s_scan32, &tot);
+        constexpr int kThreadsPerGroup = kGroupWords / kWordsPerThread;
+        const int lead = (threadIdx.x & 31) & ~(kThreadsPerGroup - 1);
+        const int32_t gbase = __shfl_sync(0xffffffffu, tpre, lead);
+        if ((threadIdx.x & (kThreadsPerGroup - 1)) == 0) grp[wlo / kGroupWords] = gbase;
+        int run = tpre - gbase;
+#pragma unroll
+        for (int t = 0; t < kWordsPerThread; ++t) {
+          pre[wlo + t] = static_cast<uint16_t>(run);
+          run += __popc(bm[wlo + t]);
+        }
+        if (threadIdx.x == 0) s_ctl[5] = tot;
+      }
+      __syncthreads();
+      const int32_t cnt = s_ctl[5];
+      if (threadIdx.x == 0 && cnt != expect) set_error(err, kErrCount);
+      // pass 2: accumulate by rank
+      for (int64_t base = 0; base < na; base += kNumThreads) {
+        int32_t total;
+        if (na > kNumThreads) {
+          const int64_t e = base + threadIdx.x;
+          Seg sg{0, 0};
+          if (e < na) sg = entry_segment(A, B, split, nblocks, a0, e, resident, e_k, e_rs, e_av, b0, b1, w0, w1);
+          const int32_t ex = block_excl_scan<int32_t>(sg.len, s_scan32, &total);
+          e_excl[threadIdx.x] = ex;
+          e_bs[threadIdx.x] = sg.bs;
+          __syncthreads();
+        } else {
+          total = p1_total;   // the single chunk's state from pass 1 is still in shared memory
+        }
+        const int nvalid = static_cast<int>(na - base < kNumThreads ? na - base : kNumThreads);
+        int owner = 0;
+        for (int32_t p = threadIdx.x; p < total; p += 2 * kNumThreads) {
           const int o1 = find_owner(e_excl, nvalid, p, owner);
           const int64_t j1 = e_bs[o1] + (p - e_excl[o1]);
-          const int32_t p2 = p + kWinThreads;
+          const int32_t p2 = p + kNumThreads;
           const bool two = p2 < total;
           const int o2 = two ? find_owner(e_excl, nvalid, p2, o1) : o1;
           const int64_t j2 = e_bs[o2] + (p2 - e_excl[o2]);
           const int32_t c1 = B.col[j1];
-          const double b1v = bv_[j1];
+          const double v1 = e_av[o1] * bv_[j1];
           int32_t c2 = 0;
-          double b2v = 0.0;
-          if (two) { c2 = B.col[j2]; b2v = bv_[j2]; }
-          win_accumulate(wtype, dense, hkeys, hvals, bm, w0, w1, c1, e_av[o1] * b1v, err);
-          if (two) win_accumulate(wtype, dense, hkeys, hvals, bm, w0, w1, c2, e_av[o2] * b2v, err);
+          double v2 = 0.0;
+          if (two) { c2 = B.col[j2]; v2 = e_av[o2] * bv_[j2]; }
+          {
+            const int32_t rel = static_cast<int32_t>(c1 - w0);
+            if (rel >= 0 && rel < (int32_t)(w1 - w0)) {
+              const int wd = rel >> 5;
+              const int r = grp[wd / kGroupWords] + pre[wd] + __popc(bm[wd] & ((1u << (rel & 31)) - 1u));
+              if (r < kRankCap) atomicAdd(&vals[r], v1);
+            }
+          }
+          if (two) {
+            const int32_t rel = static_cast<int32_t>(c2 - w0);
+            if (rel >= 0 && rel < (int32_t)(w1 - w0)) {
+              const int wd = rel >> 5;
+              const int r = grp[wd / kGroupWords] + pre[wd] + __popc(bm[wd] & ((1u << (rel & 31)) - 1u));
+              if (r < kRankCap) atomicAdd(&vals[r], v2);
+            }
+          }
           owner = o2;
         }
-        __syncthreads();
+        if (na > kNumThreads) __syncthreads();
       }
-      int64_t tot = 0;
-      if (wtype == kWinDense) {
-        const int nwords = static_cast<int>((w1 - w0 + 31) >> 5);
-        const uint32_t word = threadIdx.x < nwords ? bm[threadIdx.x] : 0u;
-        const int64_t pos = block_excl_scan<int64_t>(__popc(word), s_scan64, &tot);
-        if (word) {
-          int64_t o = out + pos;
-          for (uint32_t m = word; m; m &= m - 1) {
-            const int rel = threadIdx.x * 32 + (__ffs(m) - 1);
-            if (o < out_end) {
-              ccol[o] = static_cast<int32_t>(w0 + rel);
-              cval[o] = dense[rel];
-            }
-            dense[rel] = 0.0;
-            ++o;
-          }
-          bm[threadIdx.x] = 0u;
-        }
-      } else {
-        for (int s = threadIdx.x; s < kHashWinSlots; s += kWinThreads) {
-          const int32_t key = hkeys[s];
-          if (key) {
-            const int32_t rel = static_cast<int32_t>(key - 1 - w0);
-            atomicOr(&bm[rel >> 5], 1u << (rel & 31));
-          }
-        }
-        __syncthreads();
-        const int nwords = static_cast<int>((w1 - w0 + 31) >> 5);
-        constexpr int kPer = kWinBitmapWords / kWinThreads;
-        const int wlo = threadIdx.x * kPer;
-        int c = 0;
+      __syncthreads();
+      // emit: values by rank (coalesced), columns from the bitmap
+      for (int r = threadIdx.x; r < cnt && r < kRankCap; r += kNumThreads) {
+        if (out + r < out_end) cval[out + r] = vals[r];
+        vals[r] = 0.0;
+      }
+      {
+        const int wlo = threadIdx.x * kWordsPerThread;
+        if (wlo < nwords) {
+          int r = grp[wlo / kGroupWords] + pre[wlo];
 #pragma unroll
-        for (int t = 0; t < kPer; ++t) c += (wlo + t < nwords) ? __popc(bm[wlo + t]) : 0;
-        const int64_t pos = block_excl_scan<int64_t>(c, s_scan64, &tot);
-        int64_t o = out + pos;
-        for (int t = 0; t < kPer; ++t) {
-          if (wlo + t >= nwords) break;
-          uint32_t m = bm[wlo + t];
-          if (!m) continue;
-          bm[wlo + t] = 0u;
-          for (; m; m &= m - 1) {
-            const int rel = (wlo + t) * 32 + (__ffs(m) - 1);
-            const int32_t key = static_cast<int32_t>(w0 + rel) + 1;
-            uint32_t h = hash_slot(key, kHashWinLog2);
-            double v = 0.0;
-            for (int probe = 0; probe < kHashWinSlots; ++probe) {
-              if (hkeys[h] == key) { v = hvals[h]; break; }
-              h = (h + 1) & (kHashWinSlots - 1);
+          for (int t = 0; t < kWordsPerThread; ++t) {
+            uint32_t m = bm[wlo + t];
+            if (!m) continue;
+            bm[wlo + t] = 0u;
+            for (; m; m &= m - 1) {
+              if (out + r < out_end) ccol[out + r] = static_cast<int32_t>(w0 + (wlo + t) * 32 + (__ffs(m) - 1));
+              ++r;
             }
-            if (o < out_end) {
-              ccol[o] = key - 1;
-              cval[o] = v;
-            }
-            ++o;
           }
         }
-        __syncthreads();
-        for (int s = threadIdx.x; s < kHashWinSlots; s += kWinThreads) { hkeys[s] = 0; hvals[s] = 0.0; }
       }
-      if (threadIdx.x == 0 && tot != expect) set_error(err, kErrCount);
-      out += tot;
+      out += cnt;
       __syncthreads();
     }
     if (threadIdx.x == 0 && out != out_end) set_error(err, kErrCount);
@@ -319,7 +353,7 @@ int launch_num_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int
   cudaFuncSetAttribute(k_num_window, cudaFuncAttributeMaxDynamicSharedMemorySize, kWinSmemBytes);
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   const int64_t g = count < num_sms ? count : num_sms;
-  k_num_window<<<static_cast<unsigned>(g), kWinThreads, kWinSmemBytes, s>>>(
+  k_num_window<<<static_cast<unsigned>(g), kNumThreads, kWinSmemBytes, s>>>(
       A, B, perm, count, counter, c_off, win_slot, blockcnt, nblocks, nslots, split, hash_fill, ccol, cval,
       err);
   return 1;

@@ -65,6 +65,7 @@ def test_rmat_small_full(scale):
     dict(tiny_max=0, warp_max=0),
     dict(warp_max=64, block_max=64),
     dict(window_hash_fill=64),
+    dict(force_window=1, window_hash_fill=1),
     dict(force_window=1, window_split_max_mb=0),
     dict(validate=0),
 ])
