@@ -42,6 +42,7 @@ WORKLOADS = {
     "rmat20": [("rmat_2e20_deg16", lambda: synth.rmat(20, 16, seed=0))],
     "uniform10k": [("uniform_10k_d1e-3", lambda: synth.uniform_random(10_000, 10_000, 1e-3, seed=0))],
     "rmat16": [("rmat_2e16_deg16", lambda: synth.rmat(16, 16, seed=0))],
+    "rmat17": [("rmat_2e17_deg16", lambda: synth.rmat(17, 16, seed=0))],
 }
 WORKLOAD_DESC = {
     "lap2d1024+rmat20": "C=A*A for A = 2D 5-point Laplacian 1024^2 (FP64 4/-1) and A = R-MAT 2^20 "

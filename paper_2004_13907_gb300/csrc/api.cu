@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/spgemm.h"
+#include "spgemm.h"
 #include "kernels.h"
 #include "runtime.h"
 
@@ -138,7 +138,7 @@ void spgemm_opts_default(spgemm_opts* o) {
   o->tiny_max = 32;
   o->warp_max = 1024;
   o->block_max = 4096;
-  o->window_hash_fill = 8192;
+  o->window_hash_fill = 4096;
   o->force_window = 0;
   o->rowptr32_limit = 0x7fffffffLL;
   o->f32c_rerun_all = 0;

@@ -92,8 +92,8 @@ __host__ __device__ inline int num_class(int64_t P, int32_t na, int32_t nnz,
 // Windowed path geometry. The symbolic pass records, for every windowed row, how many
 // entries of C fall in each block of kBlockCols columns; the numeric pass groups blocks
 // into windows from those counts.
-constexpr int kBlockShift = 13;
-constexpr int kBlockCols = 1 << kBlockShift;   // columns per block (a dense window), 8192
+constexpr int kBlockShift = 12;
+constexpr int kBlockCols = 1 << kBlockShift;   // columns per block, 4096
 constexpr int kBlockWords = kBlockCols / 32;   // bitmap words per block
 constexpr int kSymWinBits = 1 << 20;           // symbolic bitmap window (128 KB)
 constexpr int kSymWinThreads = 1024;           // threads of the windowed symbolic kernel

@@ -32,23 +32,27 @@ namespace spg {
 
 namespace {
 
-constexpr int kRankCap = 8192;                     // entries of C per window (>= kBlockCols)
-constexpr int kSpanBlocks = 64;                    // blocks a window may span (512K columns)
+constexpr int kRankCap = 4096;                     // entries of C per window (>= kBlockCols)
+constexpr int kSpanBlocks = 64;                    // blocks a window may span (256K columns)
 constexpr int kSpanWords = kSpanBlocks * kBlockWords;    // bitmap words, 16384
 constexpr int kGroupWords = 64;                    // words per prefix group
-constexpr int kNumThreads = 1024;                  // threads of the windowed numeric kernel
+constexpr int kNumThreads = 512;                   // threads of the windowed numeric kernel
 constexpr int kWordsPerThread = kSpanWords / kNumThreads;
 constexpr int kCntCache = 1024;                    // block counts kept in shared memory
+constexpr int kMaxWin = 256;                       // windows planned per batch
+constexpr int kUnroll = 4;                         // partial products in flight per thread
 constexpr int kSmemVals = kRankCap * 8;
 constexpr int kSmemBits = kSpanWords * 4;
 constexpr int kSmemPre = kSpanWords * 2;
 constexpr int kSmemGrp = (kSpanWords / kGroupWords) * 4;
-constexpr int kSmemEnt = kNumThreads * (8 + 8 + 8 + 4 + 4);
-constexpr int kWinSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemGrp + kSmemEnt + kCntCache * 2;
+// per entry: B row start, a_ik, B row number; per non-empty segment: start, prefix, entry
+constexpr int kSmemEnt = kNumThreads * (8 + 8 + 4) + kNumThreads * (8 + 4 + 4) + 16;
+constexpr int kWinSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemGrp + kSmemEnt + kCntCache * 2 +
+                              kMaxWin * 12;
 static_assert(kRankCap >= kBlockCols, "a window must hold any single block");
 static_assert(kWordsPerThread * kNumThreads == kSpanWords, "words per thread");
 static_assert(kGroupWords % kWordsPerThread == 0, "a thread's words lie in one group");
-static_assert(kWinSmemBytes + 1024 <= 227 * 1024, "shared memory budget");
+static_assert(2 * (kWinSmemBytes + 1024 + 512) <= 228 * 1024, "two blocks per SM");
 
 
 // Split table: one warp per row k of B writes split[k * (nblocks + 1) + b] for b in
@@ -90,43 +94,45 @@ __device__ __forceinline__ int32_t lower_bound_col(const int32_t* col, int32_t l
   return lo;
 }
 
-// Per-entry segment of the current window for the A entry in chunk slot t (e < na).
-struct Seg { int64_t bs; int32_t len; };
-
-__device__ __forceinline__ Seg entry_segment(const DevCsr& A, const DevCsr& B, const int32_t* split,
-                                             int64_t nblocks, int64_t a0, int64_t e, bool resident,
-                                             const int32_t* e_k, const int64_t* e_rs, double* e_av,
-                                             int64_t b0, int64_t b1, int64_t w0, int64_t w1) {
-  int32_t k;
-  int64_t rs;
-  if (resident) {
-    k = e_k[threadIdx.x];
-    rs = e_rs[threadIdx.x];
-  } else {
-    k = A.col[a0 + e];
-    rs = B.rp[k];
-    e_av[threadIdx.x] = static_cast<const double*>(A.val)[a0 + e];
-  }
-  int32_t s0, s1;
-  if (split) {
-    const int32_t* sp = split + int64_t(k) * (nblocks + 1);
-    s0 = sp[b0];
-    s1 = sp[b1];
-  } else {
-    const int32_t rl = static_cast<int32_t>(B.rp[k + 1] - rs);
-    s0 = lower_bound_col(B.col + rs, rl, w0);
-    s1 = lower_bound_col(B.col + rs, rl, w1);
-  }
-  return Seg{rs + s0, s1 - s0};
+// Owner of each lane's partial product in a warp-contiguous range. The non-empty segments of a
+// chunk of A entries are numbered 0..nent-1 with exclusive prefix c_excl (c_excl[nent] = total).
+// For the 32 consecutive products p0..p0+31 whose first owner is `o`, lane t looks at the
+// boundary c_excl[o + 1 + t]; the boundaries inside the group form a bit mask, and lane l's owner
+// is o plus the number of boundaries at or before position l. Segments are non-empty, so at most
+// 31 boundaries fall inside a group of 32 products.
+__device__ __forceinline__ int group_owner(const int32_t* c_excl, int nent, int o, int32_t p0) {
+  const int lane = threadIdx.x & 31;
+  const int t = o + 1 + lane;
+  const int32_t rel = (t <= nent ? c_excl[t] : 0x7fffffff) - p0;
+  const unsigned bit = (rel >= 0 && rel < 32) ? (1u << rel) : 0u;
+  const unsigned q = __reduce_or_sync(0xffffffffu, bit);
+  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  return o + __popc(q & upto);
 }
 
-// Shared layout (dynamic): rank-indexed FP64 values [kRankCap]; window bitmap [kSpanWords];
-// in-group word prefix (uint16) [kSpanWords]; group prefix (int32) [kSpanWords / 64]; per-entry
-// state of the current chunk of A entries (B row start, a_ik, segment start, B row number,
-// segment prefix); the row's block counts. The values and the bitmap are all zero between
-// windows. A row whose A entries fit one chunk keeps their B row numbers, B row starts and
-// values across all its windows.
-__global__ void __launch_bounds__(kNumThreads, 1) k_num_window(
+// Largest o in [0, nent) with c_excl[o] <= p.
+__device__ __forceinline__ int search_owner(const int32_t* c_excl, int nent, int32_t p) {
+  int lo = 0, hi = nent - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (c_excl[mid] <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Shared layout (dynamic): rank-indexed FP64 values [kRankCap] (also the staging buffer of
+// the window's columns during the write-out); window bitmap [kSpanWords]; in-group word prefix
+// (uint16) [kSpanWords]; group prefix (int32) [kSpanWords / 64]; per-entry state of the current
+// chunk of A entries (B row start, a_ik, B row number); the chunk's non-empty segments in the
+// window (start in B, product prefix, entry); the row's block counts; the planned windows (first
+// block, end block, entries). The values and the bitmap are all zero between windows. A row whose
+// A entries fit one chunk keeps its entry state across all its windows.
+//
+// Each chunk's partial products are split into one contiguous range per warp; a warp walks its
+// range 32 products at a time (lane l takes product p0 + l), finding the lanes' segments with
+// group_owner, so loads of B are coalesced along each segment.
+__global__ void __launch_bounds__(kNumThreads, 2) k_num_window(
     DevCsr A, DevCsr B, const int32_t* __restrict__ perm, int64_t count, int32_t* counter,
     const int64_t* __restrict__ c_off, const int32_t* __restrict__ win_slot,
     const uint16_t* __restrict__ blockcnt, int64_t nblocks, int64_t nslots,
@@ -134,18 +140,26 @@ __global__ void __launch_bounds__(kNumThreads, 1) k_num_window(
     double* __restrict__ cval, uint32_t* err) {
   extern __shared__ __align__(16) unsigned char win_smem[];
   double* vals = reinterpret_cast<double*>(win_smem);
+  int32_t* colbuf = reinterpret_cast<int32_t*>(win_smem);
   uint32_t* bm = reinterpret_cast<uint32_t*>(win_smem + kSmemVals);
   uint16_t* pre = reinterpret_cast<uint16_t*>(win_smem + kSmemVals + kSmemBits);
   int32_t* grp = reinterpret_cast<int32_t*>(win_smem + kSmemVals + kSmemBits + kSmemPre);
   unsigned char* ent = win_smem + kSmemVals + kSmemBits + kSmemPre + kSmemGrp;
   int64_t* e_rs = reinterpret_cast<int64_t*>(ent);                 // B row start
   double* e_av = reinterpret_cast<double*>(e_rs + kNumThreads);    // a_ik
-  int64_t* e_bs = reinterpret_cast<int64_t*>(e_av + kNumThreads);  // window segment start
-  int32_t* e_k = reinterpret_cast<int32_t*>(e_bs + kNumThreads);   // B row number
-  int32_t* e_excl = e_k + kNumThreads;                              // segment prefix
-  uint16_t* s_cnt = reinterpret_cast<uint16_t*>(e_excl + kNumThreads);
+  int64_t* c_bs = reinterpret_cast<int64_t*>(e_av + kNumThreads);  // segment start in B
+  int32_t* e_k = reinterpret_cast<int32_t*>(c_bs + kNumThreads);   // B row number
+  int32_t* c_ent = e_k + kNumThreads;                               // segment's entry (chunk slot)
+  int32_t* c_excl = c_ent + kNumThreads;                            // segment product prefix [+1]
+  uint16_t* s_cnt = reinterpret_cast<uint16_t*>(c_excl + kNumThreads + 4);
+  int32_t* w_b0 = reinterpret_cast<int32_t*>(s_cnt + kCntCache);
+  int32_t* w_b1 = w_b0 + kMaxWin;
+  int32_t* w_cnt = w_b1 + kMaxWin;
+  __shared__ long long s_scan64[33];
   __shared__ int32_t s_scan32[33];
-  __shared__ int32_t s_ctl[6];
+  __shared__ int32_t s_ctl[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int kWarps = kNumThreads / 32;
   const int64_t n = B.cols;
   const double* av_ = static_cast<const double*>(A.val);
   const double* bv_ = static_cast<const double*>(B.val);
@@ -154,6 +168,55 @@ __global__ void __launch_bounds__(kNumThreads, 1) k_num_window(
   for (int t = threadIdx.x; t < (kSmemVals + kSmemBits) / 16; t += kNumThreads)
     reinterpret_cast<uint4*>(win_smem)[t] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
+
+  // Compacts the non-empty window segments of chunk [base, base + kNumThreads) of the row's A
+  // entries into c_bs / c_excl / c_ent; returns (segments, products) through s_ctl[6..7].
+  auto build_chunk = [&](int64_t a0, int64_t na, int64_t base, bool resident, int64_t b0, int64_t b1,
+                         int64_t w0, int64_t w1) {
+    const int64_t e = base + threadIdx.x;
+    int64_t bs = 0;
+    int32_t len = 0;
+    if (e < na) {
+      int32_t k;
+      int64_t rs;
+      if (resident) {
+        k = e_k[threadIdx.x];
+        rs = e_rs[threadIdx.x];
+      } else {
+        k = A.col[a0 + e];
+        rs = B.rp[k];
+        e_av[threadIdx.x] = av_[a0 + e];
+      }
+      int32_t s0, s1;
+      if (split) {
+        const int32_t* sp = split + int64_t(k) * (nblocks + 1);
+        s0 = sp[b0];
+        s1 = sp[b1];
+      } else {
+        const int32_t rl = static_cast<int32_t>(B.rp[k + 1] - rs);
+        s0 = lower_bound_col(B.col + rs, rl, w0);
+        s1 = lower_bound_col(B.col + rs, rl, w1);
+      }
+      bs = rs + s0;
+      len = s1 - s0;
+    }
+    const long long packed = (static_cast<long long>(len > 0) << 32) | static_cast<long long>(len);
+    long long tot;
+    const long long ex = block_excl_scan<long long>(packed, s_scan64, &tot);
+    if (len > 0) {
+      const int pos = static_cast<int>(ex >> 32);
+      c_bs[pos] = bs;
+      c_excl[pos] = static_cast<int32_t>(ex & 0xffffffffLL);
+      c_ent[pos] = threadIdx.x;
+    }
+    if (threadIdx.x == 0) {
+      const int nent = static_cast<int>(tot >> 32);
+      c_excl[nent] = static_cast<int32_t>(tot & 0xffffffffLL);
+      s_ctl[6] = nent;
+      s_ctl[7] = static_cast<int32_t>(tot & 0xffffffffLL);
+    }
+    __syncthreads();
+  };
 
   for (;;) {
     if (threadIdx.x == 0) s_ctl[0] = atomicAdd(counter, 1);
@@ -185,148 +248,175 @@ __global__ void __launch_bounds__(kNumThreads, 1) k_num_window(
     int64_t next_b = 0;   // meaningful in thread 0 only
     __syncthreads();
     for (;;) {
+      // plan a batch of windows: runs of consecutive blocks holding <= merge_cap entries of C
       if (threadIdx.x == 0) {
+        int nw = 0;
         int64_t b = next_b;
-        while (b < nblocks && cnts[b] == 0) ++b;
-        if (b >= nblocks) {
-          s_ctl[1] = 0;
-        } else {
+        while (nw < kMaxWin) {
+          while (b < nblocks && cnts[b] == 0) ++b;
+          if (b >= nblocks) break;
           int64_t e = b;
           int32_t sum = 0;
           do { sum += cnts[e]; ++e; }
           while (e < nblocks && e - b < kSpanBlocks && sum + cnts[e] <= merge_cap);
-          s_ctl[1] = 1; s_ctl[2] = static_cast<int32_t>(b); s_ctl[3] = static_cast<int32_t>(e);
-          s_ctl[4] = sum;
-          next_b = e;
+          w_b0[nw] = static_cast<int32_t>(b);
+          w_b1[nw] = static_cast<int32_t>(e);
+          w_cnt[nw] = sum;
+          ++nw;
+          b = e;
         }
+        next_b = b;
+        s_ctl[1] = nw;
       }
       __syncthreads();
-      if (s_ctl[1] == 0) break;
-      const int64_t b0 = s_ctl[2], b1 = s_ctl[3];
-      const int64_t w0 = b0 * kBlockCols;
-      const int64_t w1 = b1 * kBlockCols < n ? b1 * kBlockCols : n;
-      const int32_t expect = s_ctl[4];
-      const int nwords = static_cast<int>((w1 - w0 + 31) >> 5);
+      const int nwin = s_ctl[1];
+      if (nwin == 0) break;
+      for (int wi = 0; wi < nwin; ++wi) {
+        const int64_t b0 = w_b0[wi], b1 = w_b1[wi];
+        const int64_t w0 = b0 * kBlockCols;
+        const int64_t w1 = b1 * kBlockCols < n ? b1 * kBlockCols : n;
+        const int32_t span = static_cast<int32_t>(w1 - w0);
+        const int32_t expect = w_cnt[wi];
+        const int nwords = (span + 31) >> 5;
 
-      // pass 1: mark the window's columns
-      int32_t p1_total = 0;   // products of the (single) chunk, reused by pass 2 when na fits one chunk
-      for (int64_t base = 0; base < na; base += kNumThreads) {
-        const int64_t e = base + threadIdx.x;
-        Seg sg{0, 0};
-        if (e < na) sg = entry_segment(A, B, split, nblocks, a0, e, resident, e_k, e_rs, e_av, b0, b1, w0, w1);
-        int32_t total;
-        const int32_t ex = block_excl_scan<int32_t>(sg.len, s_scan32, &total);
-        e_excl[threadIdx.x] = ex;
-        e_bs[threadIdx.x] = sg.bs;
-        p1_total = total;
-        const int nvalid = static_cast<int>(na - base < kNumThreads ? na - base : kNumThreads);
-        __syncthreads();
-        int owner = 0;
-        for (int32_t p = threadIdx.x; p < total; p += kNumThreads) {
-          owner = find_owner(e_excl, nvalid, p, owner);
-          const int32_t c = B.col[e_bs[owner] + (p - e_excl[owner])];
-          const int64_t rel = c - w0;
-          if (rel >= 0 && rel < w1 - w0) atomicOr(&bm[rel >> 5], 1u << (rel & 31));
-          else set_error(err, kErrWindowPlan);
-        }
-        if (na > kNumThreads) __syncthreads();
-      }
-      __syncthreads();
-      // rank prefix: each thread owns kWordsPerThread consecutive words of one group
-      {
-        const int wlo = threadIdx.x * kWordsPerThread;
-        int c = 0;
+        // pass 1: mark the window's columns
+        for (int64_t base = 0; base < na; base += kNumThreads) {
+          build_chunk(a0, na, base, resident, b0, b1, w0, w1);
+          const int nent = s_ctl[6];
+          const int32_t total = s_ctl[7];
+          int32_t per = (total + kWarps - 1) / kWarps;
+          per = (per + 31) & ~31;
+          const int32_t lo = wid * per;
+          const int32_t hi = total < lo + per ? total : lo + per;
+          if (lo < hi) {
+            int o = search_owner(c_excl, nent, lo);
+            for (int32_t p0 = lo; p0 < hi; p0 += 32 * kUnroll) {
+              int64_t j[kUnroll];
 #pragma unroll
-        for (int t = 0; t < kWordsPerThread; ++t) c += __popc(bm[wlo + t]);
-        int32_t tot;
-        const int32_t tpre = block_excl_scan<int32_t>(c, s_scan32, &tot);
-        constexpr int kThreadsPerGroup = kGroupWords / kWordsPerThread;
-        const int lead = (threadIdx.x & 31) & ~(kThreadsPerGroup - 1);
-        const int32_t gbase = __shfl_sync(0xffffffffu, tpre, lead);
-        if ((threadIdx.x & (kThreadsPerGroup - 1)) == 0) grp[wlo / kGroupWords] = gbase;
-        int run = tpre - gbase;
+              for (int u = 0; u < kUnroll; ++u) {
+                const int32_t g0 = p0 + 32 * u;
+                j[u] = -1;
+                if (g0 < hi) {
+                  const int my = group_owner(c_excl, nent, o, g0);
+                  if (g0 + lane < hi) j[u] = c_bs[my] + (g0 + lane - c_excl[my]);
+                  o = __shfl_sync(0xffffffffu, my, 31);
+                }
+              }
+              int32_t c[kUnroll];
 #pragma unroll
-        for (int t = 0; t < kWordsPerThread; ++t) {
-          pre[wlo + t] = static_cast<uint16_t>(run);
-          run += __popc(bm[wlo + t]);
-        }
-        if (threadIdx.x == 0) s_ctl[5] = tot;
-      }
-      __syncthreads();
-      const int32_t cnt = s_ctl[5];
-      if (threadIdx.x == 0 && cnt != expect) set_error(err, kErrCount);
-      // pass 2: accumulate by rank
-      for (int64_t base = 0; base < na; base += kNumThreads) {
-        int32_t total;
-        if (na > kNumThreads) {
-          const int64_t e = base + threadIdx.x;
-          Seg sg{0, 0};
-          if (e < na) sg = entry_segment(A, B, split, nblocks, a0, e, resident, e_k, e_rs, e_av, b0, b1, w0, w1);
-          const int32_t ex = block_excl_scan<int32_t>(sg.len, s_scan32, &total);
-          e_excl[threadIdx.x] = ex;
-          e_bs[threadIdx.x] = sg.bs;
+              for (int u = 0; u < kUnroll; ++u) c[u] = j[u] >= 0 ? B.col[j[u]] : -1;
+#pragma unroll
+              for (int u = 0; u < kUnroll; ++u) {
+                if (j[u] < 0) continue;
+                const int32_t rel = static_cast<int32_t>(c[u] - w0);
+                if (rel >= 0 && rel < span) atomicOr(&bm[rel >> 5], 1u << (rel & 31));
+                else set_error(err, kErrWindowPlan);
+              }
+            }
+          }
           __syncthreads();
-        } else {
-          total = p1_total;   // the single chunk's state from pass 1 is still in shared memory
         }
-        const int nvalid = static_cast<int>(na - base < kNumThreads ? na - base : kNumThreads);
-        int owner = 0;
-        for (int32_t p = threadIdx.x; p < total; p += 2 * kNumThreads) {
-          const int o1 = find_owner(e_excl, nvalid, p, owner);
-          const int64_t j1 = e_bs[o1] + (p - e_excl[o1]);
-          const int32_t p2 = p + kNumThreads;
-          const bool two = p2 < total;
-          const int o2 = two ? find_owner(e_excl, nvalid, p2, o1) : o1;
-          const int64_t j2 = e_bs[o2] + (p2 - e_excl[o2]);
-          const int32_t c1 = B.col[j1];
-          const double v1 = e_av[o1] * bv_[j1];
-          int32_t c2 = 0;
-          double v2 = 0.0;
-          if (two) { c2 = B.col[j2]; v2 = e_av[o2] * bv_[j2]; }
-          {
-            const int32_t rel = static_cast<int32_t>(c1 - w0);
-            if (rel >= 0 && rel < (int32_t)(w1 - w0)) {
-              const int wd = rel >> 5;
-              const int r = grp[wd / kGroupWords] + pre[wd] + __popc(bm[wd] & ((1u << (rel & 31)) - 1u));
-              if (r < kRankCap) atomicAdd(&vals[r], v1);
-            }
-          }
-          if (two) {
-            const int32_t rel = static_cast<int32_t>(c2 - w0);
-            if (rel >= 0 && rel < (int32_t)(w1 - w0)) {
-              const int wd = rel >> 5;
-              const int r = grp[wd / kGroupWords] + pre[wd] + __popc(bm[wd] & ((1u << (rel & 31)) - 1u));
-              if (r < kRankCap) atomicAdd(&vals[r], v2);
-            }
-          }
-          owner = o2;
-        }
-        if (na > kNumThreads) __syncthreads();
-      }
-      __syncthreads();
-      // emit: values by rank (coalesced), columns from the bitmap
-      for (int r = threadIdx.x; r < cnt && r < kRankCap; r += kNumThreads) {
-        if (out + r < out_end) cval[out + r] = vals[r];
-        vals[r] = 0.0;
-      }
-      {
-        const int wlo = threadIdx.x * kWordsPerThread;
-        if (wlo < nwords) {
-          int r = grp[wlo / kGroupWords] + pre[wlo];
+        // rank prefix over the window's words: each thread owns kWordsPerThread consecutive
+        // words of one group
+        {
+          const int wlo = threadIdx.x * kWordsPerThread;
+          const bool mine = wlo < nwords;
+          int c = 0;
+          if (mine) {
 #pragma unroll
-          for (int t = 0; t < kWordsPerThread; ++t) {
-            uint32_t m = bm[wlo + t];
-            if (!m) continue;
-            bm[wlo + t] = 0u;
-            for (; m; m &= m - 1) {
-              if (out + r < out_end) ccol[out + r] = static_cast<int32_t>(w0 + (wlo + t) * 32 + (__ffs(m) - 1));
-              ++r;
+            for (int t = 0; t < kWordsPerThread; ++t) c += __popc(bm[wlo + t]);
+          }
+          int32_t tot;
+          const int32_t tpre = block_excl_scan<int32_t>(c, s_scan32, &tot);
+          constexpr int kThreadsPerGroup = kGroupWords / kWordsPerThread;
+          const int lead = lane & ~(kThreadsPerGroup - 1);
+          const int32_t gbase = __shfl_sync(0xffffffffu, tpre, lead);
+          if (mine) {
+            if ((threadIdx.x & (kThreadsPerGroup - 1)) == 0) grp[wlo / kGroupWords] = gbase;
+            int run = tpre - gbase;
+#pragma unroll
+            for (int t = 0; t < kWordsPerThread; ++t) {
+              pre[wlo + t] = static_cast<uint16_t>(run);
+              run += __popc(bm[wlo + t]);
             }
           }
+          if (threadIdx.x == 0) s_ctl[5] = tot;
         }
+        __syncthreads();
+        const int32_t cnt = s_ctl[5];
+        if (threadIdx.x == 0 && cnt != expect) set_error(err, kErrCount);
+        // pass 2: accumulate a_ik * b_kj by rank
+        for (int64_t base = 0; base < na; base += kNumThreads) {
+          if (na > kNumThreads) build_chunk(a0, na, base, resident, b0, b1, w0, w1);
+          const int nent = s_ctl[6];    // the single chunk of a resident row is kept from pass 1
+          const int32_t total = s_ctl[7];
+          int32_t per = (total + kWarps - 1) / kWarps;
+          per = (per + 31) & ~31;
+          const int32_t lo = wid * per;
+          const int32_t hi = total < lo + per ? total : lo + per;
+          if (lo < hi) {
+            int o = search_owner(c_excl, nent, lo);
+            for (int32_t p0 = lo; p0 < hi; p0 += 32 * kUnroll) {
+              int64_t j[kUnroll];
+              int ow[kUnroll];
+#pragma unroll
+              for (int u = 0; u < kUnroll; ++u) {
+                const int32_t g0 = p0 + 32 * u;
+                j[u] = -1;
+                ow[u] = 0;
+                if (g0 < hi) {
+                  const int my = group_owner(c_excl, nent, o, g0);
+                  ow[u] = my;
+                  if (g0 + lane < hi) j[u] = c_bs[my] + (g0 + lane - c_excl[my]);
+                  o = __shfl_sync(0xffffffffu, my, 31);
+                }
+              }
+              int32_t c[kUnroll];
+              double bv[kUnroll];
+#pragma unroll
+              for (int u = 0; u < kUnroll; ++u) {
+                c[u] = j[u] >= 0 ? B.col[j[u]] : -1;
+                bv[u] = j[u] >= 0 ? bv_[j[u]] : 0.0;
+              }
+#pragma unroll
+              for (int u = 0; u < kUnroll; ++u) {
+                if (j[u] < 0) continue;
+                const int32_t rel = static_cast<int32_t>(c[u] - w0);
+                if (rel < 0 || rel >= span) continue;
+                const int wd = rel >> 5;
+                const int r = grp[wd / kGroupWords] + pre[wd] + __popc(bm[wd] & ((1u << (rel & 31)) - 1u));
+                if (r < kRankCap) atomicAdd(&vals[r], e_av[c_ent[ow[u]]] * bv[u]);
+              }
+            }
+          }
+          __syncthreads();
+        }
+        // write-out: values by rank (coalesced); then the columns, staged by rank in the value
+        // array's memory (words interleaved across threads for balance), copied out coalesced
+        const int ncnt = cnt < kRankCap ? cnt : kRankCap;
+        for (int r = threadIdx.x; r < ncnt; r += kNumThreads) {
+          if (out + r < out_end) cval[out + r] = vals[r];
+          vals[r] = 0.0;
+        }
+        __syncthreads();
+        for (int w = threadIdx.x; w < nwords; w += kNumThreads) {
+          uint32_t m = bm[w];
+          if (!m) continue;
+          bm[w] = 0u;
+          int r = grp[w / kGroupWords] + pre[w];
+          for (; m; m &= m - 1) {
+            if (r < kRankCap) colbuf[r] = static_cast<int32_t>(w0 + w * 32 + (__ffs(m) - 1));
+            ++r;
+          }
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < ncnt; r += kNumThreads) {
+          if (out + r < out_end) ccol[out + r] = colbuf[r];
+          colbuf[r] = 0;
+        }
+        out += cnt;
+        __syncthreads();
       }
-      out += cnt;
-      __syncthreads();
     }
     if (threadIdx.x == 0 && out != out_end) set_error(err, kErrCount);
   }
@@ -352,7 +442,7 @@ int launch_num_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int
   if (count <= 0) return 0;
   cudaFuncSetAttribute(k_num_window, cudaFuncAttributeMaxDynamicSharedMemorySize, kWinSmemBytes);
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
-  const int64_t g = count < num_sms ? count : num_sms;
+  const int64_t g = count < 2 * num_sms ? count : 2 * num_sms;
   k_num_window<<<static_cast<unsigned>(g), kNumThreads, kWinSmemBytes, s>>>(
       A, B, perm, count, counter, c_off, win_slot, blockcnt, nblocks, nslots, split, hash_fill, ccol, cval,
       err);

@@ -101,7 +101,7 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   p->cp.warp_max = clampi(o.warp_max, 0, 1024);
   p->cp.block_max = clampi(o.block_max, p->cp.warp_max > 32 ? p->cp.warp_max : 32, 4096);
   p->cp.force_window = o.force_window ? 1 : 0;
-  if (o.window_hash_fill < 1 || o.window_hash_fill > 8192) p->opts.window_hash_fill = 8192;
+  if (o.window_hash_fill < 1 || o.window_hash_fill > 4096) p->opts.window_hash_fill = 4096;
 
   p->ntiles = (m + kTileRows - 1) / kTileRows;
   p->summary = ws_get<Summary>(p, 1, &st);

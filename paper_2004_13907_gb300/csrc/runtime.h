@@ -6,7 +6,7 @@
 
 #include <vector>
 
-#include "../../include/spgemm.h"
+#include "spgemm.h"
 #include "kernels.h"
 
 namespace spg {
