@@ -226,6 +226,26 @@ spgemm_status spgemm_multiply_host(const spgemm_csr_in* A_host, const spgemm_csr
                                    spgemm_csr_out* C_host, int64_t nnz_capacity,
                                    int64_t* nnz_c);
 
+/* C = A*B without allocating any device memory, for callers that cannot allocate while they
+ * call (for example code being captured into a CUDA graph, services that reserve the whole
+ * device up front, or real-time loops that must not wait on an allocator). The paper has no
+ * counterpart; it is an interface convenience of this library.
+ * A and B: device CSR (int32 or int64 row_ptr), FP64 values, canonical. C: caller-allocated
+ * device arrays, row_ptr[A.rows + 1] (C->idx64_rowptr selects its type) and col/val with room
+ * for nnz_capacity entries. *nnz_c receives nnz(C). Limits: A.rows <= 65536 and every row of C
+ * has at most 4096 entries (else SPGEMM_ERR_UNSUPPORTED); nnz(C) > nnz_capacity returns
+ * SPGEMM_ERR_INVALID_ARG with *nnz_c set and nothing written to C.
+ * Scratch: one fixed device array of about 770 KB inside the library, which every GPU that
+ * loads the library holds until the process exits. The first call on a device looks up that
+ * array's address (cudaGetSymbolAddress, with the device current), so make the first call
+ * before any stream capture. Every call uses the same array: calls whose work overlaps on the
+ * GPU (from several threads or streams) race and must be serialised by the caller. The call
+ * waits for `stream` twice (to read nnz(C) and the device error word) and returns with C
+ * written. */
+spgemm_status spgemm_multiply_noalloc(const spgemm_csr_in* A, const spgemm_csr_in* B,
+                                      spgemm_csr_out* C, int64_t nnz_capacity, int64_t* nnz_c,
+                                      void* stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* spgemm_last_error(void);
 

@@ -24,7 +24,8 @@ from ._native import F32_COMPENSATED, F64, SpgemmError  # noqa: F401
 __all__ = [
     "DeviceCSR", "Plan", "SpgemmError", "F64", "F32_COMPENSATED", "spgemm_opts_default",
     "spgemm_plan", "spgemm_symbolic", "spgemm_numeric", "spgemm_plan_get_info",
-    "spgemm_plan_check", "spgemm_plan_get_timings", "spgemm_plan_destroy", "spgemm_multiply_host", "spgemm_last_error",
+    "spgemm_plan_check", "spgemm_plan_get_timings", "spgemm_plan_destroy", "spgemm_multiply_host", "spgemm_multiply_noalloc",
+    "spgemm_last_error",
     "spgemm_version", "multiply", "lib",
 ]
 
@@ -209,6 +210,23 @@ def multiply(A: DeviceCSR, B: DeviceCSR, prec=F64, opts: _native.Opts | None = N
         spgemm_plan_check(plan, stream)
     spgemm_plan_destroy(plan)
     return C
+
+
+def spgemm_multiply_noalloc(A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, stream=None) -> int:
+    """C = A*B into the caller's device arrays without any device allocation (small
+    products: A.rows <= 65536, rows of C <= 4096 entries, FP64). ``C.col``/``C.val`` give the
+    capacity. Returns nnz(C); raises SpgemmError (INVALID_ARG with ``nnz_c`` attached) when C
+    is too small."""
+    a, b, c = A.as_in(), B.as_in(), C.as_out()
+    nnz = ctypes.c_int64()
+    st = lib().spgemm_multiply_noalloc(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), C.col.numel(),
+                                       ctypes.byref(nnz), _stream_handle(stream))
+    if st != 0:
+        msg = lib().spgemm_last_error()
+        err = SpgemmError(st, msg.decode() if msg else "")
+        err.nnz_c = int(nnz.value)
+        raise err
+    return int(nnz.value)
 
 
 def spgemm_multiply_host(A, B, prec=F64, opts: _native.Opts | None = None, stream=None,

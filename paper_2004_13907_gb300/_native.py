@@ -85,6 +85,8 @@ SIGNATURES = {
     "spgemm_multiply_host": (c_i32, [ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_i32,
                                      ctypes.POINTER(Opts), ctypes.POINTER(Allocator), c_vp,
                                      ctypes.POINTER(CsrOut), c_i64, ctypes.POINTER(c_i64)]),
+    "spgemm_multiply_noalloc": (c_i32, [ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut),
+                                        c_i64, ctypes.POINTER(c_i64), c_vp]),
     "spgemm_last_error": (ctypes.c_char_p, []),
     "spgemm_version": (ctypes.c_char_p, []),
 }
