@@ -58,6 +58,7 @@ struct ClassParams {
   int32_t warp_max;       // symbolic warp tables take min(P,n) <= warp_max
   int32_t block_max;      // block tables take <= block_max; larger rows are windowed
   int32_t force_window;
+  int32_t window_all;     // every row that is not tiny takes the windowed path (FP32-compensated)
 };
 
 __host__ __device__ inline int win_subclass(int64_t P) {
@@ -69,6 +70,7 @@ __host__ __device__ inline int sym_class(int64_t P, int32_t na, const ClassParam
   const int64_t U = P < cp.n ? P : cp.n;
   if (cp.force_window) return kSymWin0 + win_subclass(P);
   if (P <= cp.tiny_max && na <= kWarp) return kSymTiny;
+  if (cp.window_all) return kSymWin0 + win_subclass(P);
   if (U <= 64 && cp.warp_max >= 64) return kSymWarp1;
   if (U <= 256 && cp.warp_max >= 256) return kSymWarp2;
   if (U <= cp.warp_max) return kSymWarp3;
@@ -81,6 +83,7 @@ __host__ __device__ inline int num_class(int64_t P, int32_t na, int32_t nnz,
   if (nnz == 0) return kNumZero;
   if (cp.force_window) return kNumWin0 + win_subclass(P);
   if (P <= cp.tiny_max && na <= kWarp) return kNumTiny;
+  if (cp.window_all) return kNumWin0 + win_subclass(P);
   if (nnz <= 32 && cp.warp_max >= 64) return kNumWarp1;
   if (nnz <= 128 && cp.warp_max >= 256) return kNumWarp2;
   if (nnz <= 512 && cp.warp_max >= 1024) return kNumWarp3;
@@ -99,6 +102,25 @@ constexpr int kSymWinBits = 1 << 20;           // symbolic bitmap window (128 KB
 constexpr int kSymWinThreads = 1024;           // threads of the windowed symbolic kernel
 
 __device__ __forceinline__ void set_error(uint32_t* err, uint32_t code) { atomicOr(err, code); }
+
+// Error bound of the compensated FP32 accumulation. A result res = s + c of t partial products
+// accumulated with an error-free product and a compensated sum (Ogita, Rump and Oishi, "Accurate
+// sum and dot product", SIAM J. Sci. Comput. 2005, algorithm Dot2) satisfies
+//   |res - exact| <= u |exact| + gamma_t^2 * sum|p|,  u = 2^-24,  gamma_t = t u / (1 - t u).
+// The entry counts as within the FP32 bound when gamma_t^2 * sum|p| <= u |res| (its error is then
+// about 2u|exact|); `mag` is the FP32 running sum of |p|, inflated here for its own rounding.
+__device__ __forceinline__ bool f32c_within_bound(float res, float mag, int t) {
+  const float u = 5.9604644775390625e-8f;   // 2^-24
+  const float tu = static_cast<float>(t) * u;
+  if (tu >= 0.5f) return false;
+  const float g = tu / (1.0f - tu);
+  const float mag_ub = mag * (1.0f + 2.0f * g + 8.0f * u);
+  return g * g * mag_ub <= u * fabsf(res) * (1.0f - 8.0f * u);
+}
+
+// Modes of the accumulating kernels: FP64 values; FP32 values with compensated FP32
+// accumulation; FP32 values recomputed in FP64 and rounded once to FP32.
+enum : int { kModeF64 = 0, kModeF32C = 1, kModeF32R = 2 };
 
 // Knuth's multiplicative hash: the top log2S bits of key * floor(2^32 / phi).
 __device__ __forceinline__ uint32_t hash_slot(int32_t key, int log2S) {

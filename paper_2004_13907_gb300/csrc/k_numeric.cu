@@ -19,17 +19,17 @@ namespace spg {
 
 namespace {
 
+template <int Mode>
 __global__ void __launch_bounds__(256) k_num_tiny(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
                                                   int64_t count, const int64_t* __restrict__ c_off,
-                                                  int32_t* __restrict__ ccol, double* __restrict__ cval,
-                                                  uint32_t* err) {
+                                                  int32_t* __restrict__ ccol, void* __restrict__ cval_,
+                                                  int32_t* __restrict__ row_flag, uint32_t* err) {
   __shared__ int32_t s_col[8][32];
-  __shared__ double s_val[8][32];
+  __shared__ double s_val[8][32];   // FP64 product (kModeF64, kModeF32R) or the FP32 high part
+  __shared__ float s_lo[8][32];     // kModeF32C: the FP32 low part of the product
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  const double* av_ = static_cast<const double*>(A.val);
-  const double* bv_ = static_cast<const double*>(B.val);
   for (int64_t r = gw; r < count; r += nw) {
     const int32_t i = perm[r];
     const int64_t a0 = A.rp[i];
@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(256) k_num_tiny(DevCsr A, DevCsr B, const int3
     double av = 0.0;
     if (lane < na) {
       const int32_t k = A.col[a0 + lane];
-      av = av_[a0 + lane];
+      av = Mode == kModeF64 ? static_cast<const double*>(A.val)[a0 + lane]
+                            : static_cast<double>(static_cast<const float*>(A.val)[a0 + lane]);
       bs = B.rp[k];
       len = static_cast<int32_t>(B.rp[k + 1] - bs);
     }
@@ -57,27 +58,63 @@ __global__ void __launch_bounds__(256) k_num_tiny(DevCsr A, DevCsr B, const int3
     const double av_o = __shfl_sync(0xffffffffu, av, o & 31);
     int32_t col = -2 - lane;
     double val = 0.0;
+    float lo = 0.f;
     if (lane < total) {
       const int64_t j = bs_o + (lane - (incl_o - len_o));
       col = B.col[j];
-      val = av_o * bv_[j];
+      if constexpr (Mode == kModeF64) {
+        val = av_o * static_cast<const double*>(B.val)[j];
+      } else if constexpr (Mode == kModeF32R) {
+        val = av_o * static_cast<double>(static_cast<const float*>(B.val)[j]);   // exact in FP64
+      } else {
+        const float a = static_cast<float>(av_o);
+        const float b = static_cast<const float*>(B.val)[j];
+        const float ph = a * b;
+        val = ph;
+        lo = fmaf(a, b, -ph);   // a*b = ph + lo exactly
+      }
     }
     const unsigned peers = __match_any_sync(0xffffffffu, col);
     s_col[wid][lane] = col;
     s_val[wid][lane] = val;
+    s_lo[wid][lane] = lo;
     __syncwarp();
     const bool lead = lane < total && (__ffs(peers) - 1) == lane;
     const unsigned leaders = __ballot_sync(0xffffffffu, lead);
+    bool missed = false;
     if (lead) {
-      double sum = 0.0;
-      for (unsigned m = peers; m; m &= m - 1) sum += s_val[wid][__ffs(m) - 1];
       int rank = 0;
       for (unsigned m = leaders; m; m &= m - 1) rank += s_col[wid][__ffs(m) - 1] < col;
       if (rank < c_off[i + 1] - c_off[i]) {   // a miscount raises kErrCount, never writes out of the row
         const int64_t out = c_off[i] + rank;
         ccol[out] = col;
-        cval[out] = sum;
+        if constexpr (Mode == kModeF32C) {
+          // compensated sum of the group's products in product order (Dot2)
+          float sum = 0.f, comp = 0.f, mag = 0.f;
+          int t = 0;
+          for (unsigned m = peers; m; m &= m - 1) {
+            const int q = __ffs(m) - 1;
+            const float ph = static_cast<float>(s_val[wid][q]);
+            const float nsum = sum + ph;
+            const float bp = nsum - sum;
+            comp += (sum - (nsum - bp)) + (ph - bp) + s_lo[wid][q];
+            sum = nsum;
+            mag += fabsf(ph);
+            ++t;
+          }
+          const float res = sum + comp;
+          static_cast<float*>(cval_)[out] = res;
+          missed = !f32c_within_bound(res, mag, t);
+        } else {
+          double sum = 0.0;
+          for (unsigned m = peers; m; m &= m - 1) sum += s_val[wid][__ffs(m) - 1];
+          if constexpr (Mode == kModeF64) static_cast<double*>(cval_)[out] = sum;
+          else static_cast<float*>(cval_)[out] = static_cast<float>(sum);
+        }
       }
+    }
+    if constexpr (Mode == kModeF32C) {
+      if (__any_sync(0xffffffffu, missed) && lane == 0) row_flag[i] = 1;
     }
     if (lane == 0 && c_off[i + 1] - c_off[i] != __popc(leaders)) set_error(err, kErrCount);
     __syncwarp();
@@ -258,11 +295,14 @@ inline unsigned grid_rows(int64_t count, int rows_per_block, int max_blocks) {
 
 }  // namespace
 
-int launch_num_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
-                     const int64_t* c_off, int32_t* ccol, double* cval, uint32_t* err,
-                     cudaStream_t s) {
+int launch_num_tiny(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                    const int64_t* c_off, int32_t* ccol, void* cval, int32_t* row_flag, uint32_t* err,
+                    cudaStream_t s) {
   if (count <= 0) return 0;
-  k_num_tiny<<<grid_rows(count, 8, 152 * 64), 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, err);
+  const unsigned g = grid_rows(count, 8, 152 * 64);
+  if (mode == kModeF32C) k_num_tiny<kModeF32C><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, err);
+  else if (mode == kModeF32R) k_num_tiny<kModeF32R><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, err);
+  else k_num_tiny<kModeF64><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, err);
   return 1;
 }
 

@@ -263,6 +263,25 @@ __global__ void __launch_bounds__(256) k_scatter_num(DevCsr A, ClassParams cp, c
   }
 }
 
+__global__ void __launch_bounds__(256) k_collect_flagged(const int32_t* __restrict__ perm, int64_t count,
+                                                         const int32_t* __restrict__ row_flag, int all,
+                                                         int32_t* __restrict__ list, int32_t* list_count) {
+  for (int64_t r0 = blockIdx.x * int64_t(blockDim.x); r0 < count; r0 += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = r0 + threadIdx.x;
+    int32_t row = 0;
+    bool take = false;
+    if (r < count) {
+      row = perm[r];
+      take = all || row_flag[row] != 0;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    int32_t base = 0;
+    if (lane_id() == 0 && m) base = atomicAdd(list_count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) list[base + __popc(m & ((1u << lane_id()) - 1u))] = row;
+  }
+}
+
 __global__ void k_write_rowptr(const int64_t* __restrict__ c_off, int64_t m1, void* out, int idx64) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m1;
        i += int64_t(gridDim.x) * blockDim.x) {
@@ -332,6 +351,13 @@ int launch_scatter_num(const DevCsr& A, ClassParams cp, const int64_t* P, const 
   if (ntiles == 0) return 0;
   k_scatter_num<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, cp, P, nnz_row, tile_hist,
                                                               tile_sum_off, perm, c_off);
+  return 1;
+}
+
+int launch_collect_flagged(const int32_t* perm, int64_t count, const int32_t* row_flag, int all,
+                           int32_t* list, int32_t* list_count, cudaStream_t s) {
+  if (count <= 0) return 0;
+  k_collect_flagged<<<grid_for(count, 256, 152 * 16), 256, 0, s>>>(perm, count, row_flag, all, list, list_count);
   return 1;
 }
 

@@ -41,18 +41,27 @@ constexpr int kWordsPerThread = kSpanWords / kNumThreads;
 constexpr int kCntCache = 1024;                    // block counts kept in shared memory
 constexpr int kMaxWin = 256;                       // windows planned per batch
 constexpr int kUnroll = 4;                         // partial products in flight per thread
-constexpr int kSmemVals = kRankCap * 8;
 constexpr int kSmemBits = kSpanWords * 4;
 constexpr int kSmemPre = kSpanWords * 2;
 constexpr int kSmemGrp = (kSpanWords / kGroupWords) * 4;
 // per entry: B row start, a_ik, B row number; per non-empty segment: start, prefix, entry
 constexpr int kSmemEnt = kNumThreads * (8 + 8 + 4) + kNumThreads * (8 + 4 + 4) + 16;
-constexpr int kWinSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemGrp + kSmemEnt + kCntCache * 2 +
-                              kMaxWin * 12;
+// Per rank the windowed kernel keeps an FP64 sum (kModeF64, kModeF32R) or, in kModeF32C, an FP32
+// sum, its compensation, sum|p| and the term count.
+template <int Mode>
+struct WinGeom {
+  static constexpr int kValBytes = Mode == kModeF32C ? 16 : 8;
+  static constexpr int kSmemVals = kRankCap * kValBytes;
+  static constexpr int kSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemGrp + kSmemEnt + kCntCache * 2 +
+                                    kMaxWin * 12;
+  static constexpr int kBlocksPerSm = Mode == kModeF32C ? 1 : 2;
+};
+constexpr int kWinSmemBytes = WinGeom<kModeF64>::kSmemBytes;
 static_assert(kRankCap >= kBlockCols, "a window must hold any single block");
 static_assert(kWordsPerThread * kNumThreads == kSpanWords, "words per thread");
 static_assert(kGroupWords % kWordsPerThread == 0, "a thread's words lie in one group");
 static_assert(2 * (kWinSmemBytes + 1024 + 512) <= 228 * 1024, "two blocks per SM");
+static_assert(WinGeom<kModeF32C>::kSmemBytes + 1024 + 512 <= 227 * 1024, "shared memory budget");
 
 
 // Split table: one warp per row k of B writes split[k * (nblocks + 1) + b] for b in
@@ -132,14 +141,20 @@ __device__ __forceinline__ int search_owner(const int32_t* c_excl, int nent, int
 // Each chunk's partial products are split into one contiguous range per warp; a warp walks its
 // range 32 products at a time (lane l takes product p0 + l), finding the lanes' segments with
 // group_owner, so loads of B are coalesced along each segment.
-__global__ void __launch_bounds__(kNumThreads, 2) k_num_window(
+template <int Mode>
+__global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_num_window(
     DevCsr A, DevCsr B, const int32_t* __restrict__ perm, int64_t count, int32_t* counter,
     const int64_t* __restrict__ c_off, const int32_t* __restrict__ win_slot,
     const uint16_t* __restrict__ blockcnt, int64_t nblocks, int64_t nslots,
     const int32_t* __restrict__ split, int32_t merge_cap, int32_t* __restrict__ ccol,
-    double* __restrict__ cval, uint32_t* err) {
+    void* __restrict__ cval_, int32_t* __restrict__ row_flag, uint32_t* err) {
+  constexpr int kSmemVals = WinGeom<Mode>::kSmemVals;
   extern __shared__ __align__(16) unsigned char win_smem[];
-  double* vals = reinterpret_cast<double*>(win_smem);
+  double* vals = reinterpret_cast<double*>(win_smem);        // kModeF64, kModeF32R
+  float* f_s = reinterpret_cast<float*>(win_smem);            // kModeF32C: sum,
+  float* f_c = f_s + kRankCap;                                //   compensation,
+  float* f_m = f_c + kRankCap;                                //   sum |p|,
+  int32_t* f_t = reinterpret_cast<int32_t*>(f_m + kRankCap);  //   term count
   int32_t* colbuf = reinterpret_cast<int32_t*>(win_smem);
   uint32_t* bm = reinterpret_cast<uint32_t*>(win_smem + kSmemVals);
   uint16_t* pre = reinterpret_cast<uint16_t*>(win_smem + kSmemVals + kSmemBits);
@@ -161,8 +176,11 @@ __global__ void __launch_bounds__(kNumThreads, 2) k_num_window(
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int kWarps = kNumThreads / 32;
   const int64_t n = B.cols;
-  const double* av_ = static_cast<const double*>(A.val);
-  const double* bv_ = static_cast<const double*>(B.val);
+  const double* av64 = static_cast<const double*>(A.val);
+  const double* bv64 = static_cast<const double*>(B.val);
+  const float* av32 = static_cast<const float*>(A.val);
+  const float* bv32 = static_cast<const float*>(B.val);
+  auto a_at = [&](int64_t q) -> double { return Mode == kModeF64 ? av64[q] : static_cast<double>(av32[q]); };
   const bool cnt_cached = nblocks <= kCntCache;
 
   for (int t = threadIdx.x; t < (kSmemVals + kSmemBits) / 16; t += kNumThreads)
@@ -185,7 +203,7 @@ __global__ void __launch_bounds__(kNumThreads, 2) k_num_window(
       } else {
         k = A.col[a0 + e];
         rs = B.rp[k];
-        e_av[threadIdx.x] = av_[a0 + e];
+        e_av[threadIdx.x] = a_at(a0 + e);
       }
       int32_t s0, s1;
       if (split) {
@@ -240,7 +258,7 @@ __global__ void __launch_bounds__(kNumThreads, 2) k_num_window(
       const int32_t k = A.col[a0 + threadIdx.x];
       e_k[threadIdx.x] = k;
       e_rs[threadIdx.x] = B.rp[k];
-      e_av[threadIdx.x] = av_[a0 + threadIdx.x];
+      e_av[threadIdx.x] = a_at(a0 + threadIdx.x);
     }
     const uint16_t* cnts = cnt_cached ? s_cnt : gcnt;
     int64_t out = c_off[i];
@@ -376,7 +394,7 @@ __global__ void __launch_bounds__(kNumThreads, 2) k_num_window(
 #pragma unroll
               for (int u = 0; u < kUnroll; ++u) {
                 c[u] = j[u] >= 0 ? B.col[j[u]] : -1;
-                bv[u] = j[u] >= 0 ? bv_[j[u]] : 0.0;
+                bv[u] = j[u] >= 0 ? (Mode == kModeF64 ? bv64[j[u]] : static_cast<double>(bv32[j[u]])) : 0.0;
               }
 #pragma unroll
               for (int u = 0; u < kUnroll; ++u) {
@@ -385,7 +403,25 @@ __global__ void __launch_bounds__(kNumThreads, 2) k_num_window(
                 if (rel < 0 || rel >= span) continue;
                 const int wd = rel >> 5;
                 const int r = grp[wd / kGroupWords] + pre[wd] + __popc(bm[wd] & ((1u << (rel & 31)) - 1u));
-                if (r < kRankCap) atomicAdd(&vals[r], e_av[c_ent[ow[u]]] * bv[u]);
+                if (r >= kRankCap) continue;
+                if constexpr (Mode == kModeF32C) {
+                  // error-free product a*b = ph + pl (TwoProduct with fmaf); the sum's own rounding
+                  // error is rebuilt from the value atomicAdd returns (TwoSum) and, with pl, goes
+                  // to the compensation term (Ogita, Rump and Oishi's Dot2, accumulated concurrently)
+                  const float a = static_cast<float>(e_av[c_ent[ow[u]]]);
+                  const float b = static_cast<float>(bv[u]);
+                  const float ph = a * b;
+                  const float pl = fmaf(a, b, -ph);
+                  const float old = atomicAdd(&f_s[r], ph);
+                  const float nw = old + ph;
+                  const float bp = nw - old;
+                  const float q = (old - (nw - bp)) + (ph - bp);
+                  atomicAdd(&f_c[r], q + pl);
+                  atomicAdd(&f_m[r], fabsf(ph));
+                  atomicAdd(&f_t[r], 1);
+                } else {
+                  atomicAdd(&vals[r], e_av[c_ent[ow[u]]] * bv[u]);
+                }
               }
             }
           }
@@ -394,9 +430,23 @@ __global__ void __launch_bounds__(kNumThreads, 2) k_num_window(
         // write-out: values by rank (coalesced); then the columns, staged by rank in the value
         // array's memory (words interleaved across threads for balance), copied out coalesced
         const int ncnt = cnt < kRankCap ? cnt : kRankCap;
-        for (int r = threadIdx.x; r < ncnt; r += kNumThreads) {
-          if (out + r < out_end) cval[out + r] = vals[r];
-          vals[r] = 0.0;
+        if constexpr (Mode == kModeF32C) {
+          bool missed = false;
+          for (int r = threadIdx.x; r < ncnt; r += kNumThreads) {
+            const float res = f_s[r] + f_c[r];
+            if (out + r < out_end) static_cast<float*>(cval_)[out + r] = res;
+            missed |= !f32c_within_bound(res, f_m[r], f_t[r]);
+            f_s[r] = 0.f; f_c[r] = 0.f; f_m[r] = 0.f; f_t[r] = 0;
+          }
+          if (missed) row_flag[i] = 1;
+        } else {
+          for (int r = threadIdx.x; r < ncnt; r += kNumThreads) {
+            if (out + r < out_end) {
+              if constexpr (Mode == kModeF64) static_cast<double*>(cval_)[out + r] = vals[r];
+              else static_cast<float*>(cval_)[out + r] = static_cast<float>(vals[r]);
+            }
+            vals[r] = 0.0;
+          }
         }
         __syncthreads();
         for (int w = threadIdx.x; w < nwords; w += kNumThreads) {
@@ -434,18 +484,23 @@ int launch_bsplit(const DevCsr& B, int64_t nblocks, int32_t* split, cudaStream_t
   return 1;
 }
 
-int launch_num_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                       int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
-                      int32_t hash_fill, int32_t* ccol, double* cval, int num_sms, uint32_t* err,
-                      cudaStream_t s) {
+                      int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag, int num_sms,
+                      uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
-  cudaFuncSetAttribute(k_num_window, cudaFuncAttributeMaxDynamicSharedMemorySize, kWinSmemBytes);
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
-  const int64_t g = count < 2 * num_sms ? count : 2 * num_sms;
-  k_num_window<<<static_cast<unsigned>(g), kNumThreads, kWinSmemBytes, s>>>(
-      A, B, perm, count, counter, c_off, win_slot, blockcnt, nblocks, nslots, split, hash_fill, ccol, cval,
-      err);
+  auto go = [&](auto kernel, int smem, int per_sm) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int64_t g = count < int64_t(per_sm) * num_sms ? count : int64_t(per_sm) * num_sms;
+    kernel<<<static_cast<unsigned>(g), kNumThreads, smem, s>>>(A, B, perm, count, counter, c_off, win_slot,
+                                                               blockcnt, nblocks, nslots, split, merge_cap,
+                                                               ccol, cval, row_flag, err);
+  };
+  if (mode == kModeF32C) go(k_num_window<kModeF32C>, WinGeom<kModeF32C>::kSmemBytes, 1);
+  else if (mode == kModeF32R) go(k_num_window<kModeF32R>, WinGeom<kModeF32R>::kSmemBytes, 2);
+  else go(k_num_window<kModeF64>, WinGeom<kModeF64>::kSmemBytes, 2);
   return 1;
 }
 

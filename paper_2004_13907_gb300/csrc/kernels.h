@@ -59,9 +59,9 @@ int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int
                        cudaStream_t s);
 
 // ---- numeric kernels, FP64 (k_numeric.cu)
-int launch_num_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
-                     const int64_t* c_off, int32_t* ccol, double* cval, uint32_t* err,
-                     cudaStream_t s);
+int launch_num_tiny(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                    const int64_t* c_off, int32_t* ccol, void* cval, int32_t* row_flag, uint32_t* err,
+                    cudaStream_t s);
 int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                      int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
                      uint32_t* err, cudaStream_t s);
@@ -72,10 +72,14 @@ int launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t*
 // ---- windowed numeric pass and the column-block split table of B (k_window.cu)
 int64_t split_table_bytes(int64_t brows, int64_t nblocks);
 int launch_bsplit(const DevCsr& B, int64_t nblocks, int32_t* split, cudaStream_t s);
-int launch_num_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                       int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
-                      int32_t hash_fill, int32_t* ccol, double* cval, int num_sms, uint32_t* err,
-                      cudaStream_t s);
+                      int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag, int num_sms,
+                      uint32_t* err, cudaStream_t s);
+// F32-compensated rerun lists: the rows of perm[0, count) whose flag is set (all rows when
+// `all`), appended to list at list_count (a device counter)
+int launch_collect_flagged(const int32_t* perm, int64_t count, const int32_t* row_flag, int all,
+                           int32_t* list, int32_t* list_count, cudaStream_t s);
 
 }  // namespace spg

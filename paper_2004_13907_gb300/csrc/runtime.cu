@@ -101,6 +101,7 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   p->cp.warp_max = clampi(o.warp_max, 0, 1024);
   p->cp.block_max = clampi(o.block_max, p->cp.warp_max > 32 ? p->cp.warp_max : 32, 4096);
   p->cp.force_window = o.force_window ? 1 : 0;
+  p->cp.window_all = p->prec == SPGEMM_F32_COMPENSATED ? 1 : 0;
   if (o.window_hash_fill < 1 || o.window_hash_fill > 4096) p->opts.window_hash_fill = 4096;
 
   p->ntiles = (m + kTileRows - 1) / kTileRows;
@@ -206,20 +207,31 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
 }
 
 spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
-  spgemm_status st;
+  spgemm_status st = SPGEMM_OK;
   const int64_t m = p->A.rows;
-  if (p->prec != SPGEMM_F64)
-    return set_error_msg(SPGEMM_ERR_UNSUPPORTED, "this precision is not built yet");
+  const bool f32c = p->prec == SPGEMM_F32_COMPENSATED;
+  const int mode = f32c ? kModeF32C : kModeF64;
   stage_begin(p, SPGEMM_STAGE_NUM_ROWPTR, s);
   int nl = launch_write_rowptr(p->c_off, m + 1, C->row_ptr, C->idx64_rowptr, s);
   stage_end(p, SPGEMM_STAGE_NUM_ROWPTR, nl, s);
+  p->f32c_rerun_rows = 0;
   if (m > 0) {
     auto seg = [&](int c) { return p->perm_n + p->num_off[c]; };
     auto cnt = [&](int c) { return p->num_off[c + 1] - p->num_off[c]; };
     uint32_t* err = &p->summary->err;
-    double* cval = static_cast<double*>(C->val);
-    stage_begin(p, SPGEMM_STAGE_NUM_WINDOW, s);
     const int64_t nwin = p->num_off[kNumWin3 + 1] - p->num_off[kNumWin0];
+    const int64_t nslots = p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0];
+    if (f32c) {
+      for (int c = kNumBlock2; c <= kNumWarp1; ++c)
+        if (cnt(c)) return set_error_msg(SPGEMM_ERR_INTERNAL, "FP32-compensated rows outside the windowed path");
+      if (!p->rerun_flag) {
+        p->rerun_flag = ws_get<int32_t>(p, m, &st);
+        p->rerun_list = ws_get<int32_t>(p, m, &st);
+        if (st) return st;
+      }
+      cudaMemsetAsync(p->rerun_flag, 0, sizeof(int32_t) * m, s);
+    }
+    stage_begin(p, SPGEMM_STAGE_NUM_WINDOW, s);
     nl = 0;
     if (nwin > 0 && !p->split_tried) {
       // split table of B, once per plan, when it fits the budget (else the kernel searches)
@@ -230,22 +242,46 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
         if (p->split) nl += launch_bsplit(p->B, p->nblocks, p->split, s);
       }
     }
-    nl += launch_num_window(p->A, p->B, seg(kNumWin0), nwin, p->counters + 1, p->c_off, p->win_slot,
-                            p->blockcnt, p->nblocks, p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0],
-                            p->split, p->opts.window_hash_fill, C->col, cval, p->num_sms, err, s);
+    nl += launch_num_window(mode, p->A, p->B, seg(kNumWin0), nwin, p->counters + 1, p->c_off, p->win_slot,
+                            p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
+                            p->rerun_flag, p->num_sms, err, s);
     stage_end(p, SPGEMM_STAGE_NUM_WINDOW, nl, s);
-    stage_begin(p, SPGEMM_STAGE_NUM_BLOCK, s);
-    nl = launch_num_block(13, p->A, p->B, seg(kNumBlock2), cnt(kNumBlock2), p->c_off, C->col, cval, err, s);
-    nl += launch_num_block(11, p->A, p->B, seg(kNumBlock1), cnt(kNumBlock1), p->c_off, C->col, cval, err, s);
-    stage_end(p, SPGEMM_STAGE_NUM_BLOCK, nl, s);
-    stage_begin(p, SPGEMM_STAGE_NUM_WARP, s);
-    nl = launch_num_warp(10, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, cval, err, s);
-    nl += launch_num_warp(8, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, cval, err, s);
-    nl += launch_num_warp(6, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, cval, err, s);
-    stage_end(p, SPGEMM_STAGE_NUM_WARP, nl, s);
+    if (!f32c) {
+      double* cval = static_cast<double*>(C->val);
+      stage_begin(p, SPGEMM_STAGE_NUM_BLOCK, s);
+      nl = launch_num_block(13, p->A, p->B, seg(kNumBlock2), cnt(kNumBlock2), p->c_off, C->col, cval, err, s);
+      nl += launch_num_block(11, p->A, p->B, seg(kNumBlock1), cnt(kNumBlock1), p->c_off, C->col, cval, err, s);
+      stage_end(p, SPGEMM_STAGE_NUM_BLOCK, nl, s);
+      stage_begin(p, SPGEMM_STAGE_NUM_WARP, s);
+      nl = launch_num_warp(10, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, cval, err, s);
+      nl += launch_num_warp(8, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, cval, err, s);
+      nl += launch_num_warp(6, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, cval, err, s);
+      stage_end(p, SPGEMM_STAGE_NUM_WARP, nl, s);
+    }
     stage_begin(p, SPGEMM_STAGE_NUM_TINY, s);
-    nl = launch_num_tiny(p->A, p->B, seg(kNumTiny), cnt(kNumTiny), p->c_off, C->col, cval, err, s);
+    nl = launch_num_tiny(mode, p->A, p->B, seg(kNumTiny), cnt(kNumTiny), p->c_off, C->col, C->val, p->rerun_flag,
+                         err, s);
     stage_end(p, SPGEMM_STAGE_NUM_TINY, nl, s);
+    if (f32c && !p->opts.f32c_rerun_none) {
+      // rows with an entry over the compensated bound are recomputed in FP64 and rounded once
+      stage_begin(p, SPGEMM_STAGE_NUM_RERUN, s);
+      int32_t* list_w = p->rerun_list;
+      int32_t* list_t = p->rerun_list + nwin;
+      cudaMemsetAsync(p->counters + 4, 0, 2 * sizeof(int32_t), s);
+      const int all = p->opts.f32c_rerun_all ? 1 : 0;
+      nl = launch_collect_flagged(seg(kNumWin0), nwin, p->rerun_flag, all, list_w, p->counters + 4, s);
+      nl += launch_collect_flagged(seg(kNumTiny), cnt(kNumTiny), p->rerun_flag, all, list_t, p->counters + 5, s);
+      int32_t hc[2] = {0, 0};
+      cudaError_t e = cudaMemcpyAsync(hc, p->counters + 4, sizeof(hc), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_status(e, "reading the FP64 rerun counts");
+      nl += launch_num_window(kModeF32R, p->A, p->B, list_w, hc[0], p->counters + 2, p->c_off, p->win_slot,
+                              p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
+                              nullptr, p->num_sms, err, s);
+      nl += launch_num_tiny(kModeF32R, p->A, p->B, list_t, hc[1], p->c_off, C->col, C->val, nullptr, err, s);
+      stage_end(p, SPGEMM_STAGE_NUM_RERUN, nl, s);
+      p->f32c_rerun_rows = int64_t(hc[0]) + hc[1];
+    }
   }
   if ((st = cuda_status(cudaGetLastError(), "launching the numeric kernels")) != SPGEMM_OK) return st;
   p->state = 2;
