@@ -35,18 +35,21 @@ METRIC = "SpGEMM GFLOP/s (2 x intermediate products / s)"
 UNIT = "GFLOP/s"
 
 WORKLOADS = {
-    # name -> list of (matrix name, generator)
-    "lap2d1024+rmat20": [("lap2d_1024", lambda: synth.laplacian2d(1024)),
-                         ("rmat_2e20_deg16", lambda: synth.rmat(20, 16, seed=0))],
-    "lap2d1024": [("lap2d_1024", lambda: synth.laplacian2d(1024))],
-    "rmat20": [("rmat_2e20_deg16", lambda: synth.rmat(20, 16, seed=0))],
-    "uniform10k": [("uniform_10k_d1e-3", lambda: synth.uniform_random(10_000, 10_000, 1e-3, seed=0))],
-    "rmat16": [("rmat_2e16_deg16", lambda: synth.rmat(16, 16, seed=0))],
-    "rmat17": [("rmat_2e17_deg16", lambda: synth.rmat(17, 16, seed=0))],
+    # name -> list of (matrix name, generator, precision)
+    "lap2d1024+rmat20": [("lap2d_1024", lambda: synth.laplacian2d(1024), "f64"),
+                         ("rmat_2e20_deg16", lambda: synth.rmat(20, 16, seed=0), "f64")],
+    "lap2d1024": [("lap2d_1024", lambda: synth.laplacian2d(1024), "f64")],
+    "rmat20": [("rmat_2e20_deg16", lambda: synth.rmat(20, 16, seed=0), "f64")],
+    "rmat20_f32c": [("rmat_2e20_deg16_f32", lambda: synth.rmat(20, 16, seed=0, dtype=np.float32), "f32c")],
+    "uniform10k": [("uniform_10k_d1e-3", lambda: synth.uniform_random(10_000, 10_000, 1e-3, seed=0), "f64")],
+    "rmat16": [("rmat_2e16_deg16", lambda: synth.rmat(16, 16, seed=0), "f64")],
+    "rmat17": [("rmat_2e17_deg16", lambda: synth.rmat(17, 16, seed=0), "f64")],
 }
 WORKLOAD_DESC = {
     "lap2d1024+rmat20": "C=A*A for A = 2D 5-point Laplacian 1024^2 (FP64 4/-1) and A = R-MAT 2^20 "
                         "vertices, 16*2^20 edge samples, (a,b,c,d)=(.57,.19,.19,.05), FP64 U[0,1], seed 0",
+    "rmat20_f32c": "C=A*A for A = R-MAT 2^20 vertices, degree 16, FP32 values U[0,1], seed 0; FP32 "
+                   "compensated accumulation, rows over the error bound recomputed in FP64",
 }
 
 
@@ -107,6 +110,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _traffic(kernel_file: str, workload: str):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, when it was
+    taken on this workload with the kernel source as it is now (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"k_num_window_{workload}.md")
+    src = os.path.join(ROOT, "paper_2004_13907_gb300", "csrc", kernel_file)
+    try:
+        want = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.lstrip().startswith("- "):
+                k, v = line.lstrip()[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("kernel source sha256[:16]") != want:
+            return None
+        return int(fields["dram bytes per launch"].replace(",", ""))
+    except Exception:
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -143,7 +166,9 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    mats = [(name, gen()) for name, gen in WORKLOADS[args.workload]]
+    specs = WORKLOADS[args.workload]
+    mats = [(name, gen()) for name, gen, _ in specs]
+    precs = {name: prec for name, _, prec in specs}
     dev = [(name, M, sp.DeviceCSR.from_host(M, "cuda")) for name, M in mats]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     opts = sp.spgemm_opts_default(record_timings=1)
@@ -151,7 +176,7 @@ def run_ours(args):
 
     def step(collect=None):
         for name, M, dM in dev:
-            plan = sp.spgemm_plan(dM, dM, "f64", opts)
+            plan = sp.spgemm_plan(dM, dM, precs[name], opts)
             sp.spgemm_symbolic(plan)
             C = sp.alloc_output(plan)
             sp.spgemm_numeric(plan, C)
@@ -224,7 +249,7 @@ def run_ours(args):
         roof = {"bound": "hbm", "kernel": f"k_num_window ({dom_mat})", "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": bytes_,
-                "launch_ms": round(dom_ms, 4), "traffic": None}
+                "launch_ms": round(dom_ms, 4), "traffic": _traffic("k_window.cu", args.workload)}
     breakdown = {}
     for name, d in per.items():
         info = d["info"]
@@ -245,7 +270,9 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if all(p == "f64" for p in precs.values()) else "f32 (compensated) + f64 rerun",
+        "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOAD_DESC.get(args.workload, args.workload),
                    "products_per_step": products_step, "l2": "flushed: 512 MB written between timed steps",
                    "parallelism": f"replicas x{ws} (independent products, no collective on the data path)"},
@@ -366,7 +393,7 @@ def run_reference(args):
     if rank != 0:
         return None, rank
     import oracle
-    mats = [(name, gen()) for name, gen in WORKLOADS[args.workload]]
+    mats = [(name, gen()) for name, gen, _ in WORKLOADS[args.workload]]
     Ps = [oracle.products_per_row(M, M) for _, M in mats]
     budget = int(args.ref_products_per_step)
     rng = np.random.default_rng(99)
