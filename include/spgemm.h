@@ -226,6 +226,38 @@ spgemm_status spgemm_multiply_host(const spgemm_csr_in* A_host, const spgemm_csr
                                    spgemm_csr_out* C_host, int64_t nnz_capacity,
                                    int64_t* nnz_c);
 
+/* ---- Batched products: C_j = A_j * B_j for n_jobs independent jobs, run as one product.
+ * The jobs are stacked into one block-diagonal product, so the whole batch takes the launches of
+ * a single product (plan, symbolic, numeric) instead of a set per job. A[j], B[j]: host arrays of
+ * descriptors of device CSR matrices (as for spgemm_plan; same precision for all jobs), which must
+ * stay valid while the batch is used. The call blocks `stream` (two reads, as plan and symbolic)
+ * and returns with the numeric pass enqueued; results are valid once `stream` reaches that point.
+ * The results are owned by the batch until spgemm_batch_destroy. Errors as spgemm_plan, plus
+ * INVALID_CSR when a job's column index exceeds its own matrix and UNSUPPORTED when the stacked
+ * batch has 2^31 or more rows or columns. */
+typedef struct spgemm_batch_s spgemm_batch_t;
+
+spgemm_status spgemm_batch(int64_t n_jobs, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                           spgemm_prec prec, const spgemm_opts* opts, const spgemm_allocator* alloc,
+                           void* stream, spgemm_batch_t** out_batch);
+
+/* Job j's result as a standalone CSR view into the batch's arrays (device pointers, int64
+ * row_ptr starting at 0, job-local column indices). */
+spgemm_status spgemm_batch_result(const spgemm_batch_t* batch, int64_t job, spgemm_csr_out* C);
+
+/* Counters of the stacked product (as spgemm_plan_get_info). */
+spgemm_status spgemm_batch_get_info(const spgemm_batch_t* batch, spgemm_plan_info* info);
+
+/* Waits for `stream` and reports the device-side consistency checks (as spgemm_plan_check). */
+spgemm_status spgemm_batch_check(spgemm_batch_t* batch, void* stream);
+
+/* Re-reads the jobs' current values (patterns unchanged) and recomputes every job's values, as
+ * one CUDA graph launch on `stream`: the first call captures the value refresh and the numeric
+ * pass into a graph, later calls launch it. FP64 batches only (UNSUPPORTED otherwise). */
+spgemm_status spgemm_batch_replay(spgemm_batch_t* batch, void* stream);
+
+spgemm_status spgemm_batch_destroy(spgemm_batch_t* batch);
+
 /* C = A*B without allocating any device memory, for callers that cannot allocate while they
  * call (for example code being captured into a CUDA graph, services that reserve the whole
  * device up front, or real-time loops that must not wait on an allocator). The paper has no

@@ -212,6 +212,80 @@ def multiply(A: DeviceCSR, B: DeviceCSR, prec=F64, opts: _native.Opts | None = N
     return C
 
 
+class _DevArray:
+    """__cuda_array_interface__ over library-owned device memory (no copy)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3}
+
+
+def _view(ptr: int, n: int, dtype: torch.dtype, device) -> torch.Tensor:
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device=device)
+    typestr = {torch.int32: "<i4", torch.int64: "<i8", torch.float64: "<f8", torch.float32: "<f4"}[dtype]
+    return torch.as_tensor(_DevArray(ptr, n, typestr), device=device)
+
+
+class Batch:
+    """Handle of a native batch (stacked block-diagonal product). The result tensors returned by
+    ``result`` are views of memory the batch owns: keep the Batch alive while using them."""
+
+    def __init__(self, handle: int, As, Bs, prec: int):
+        self.handle = handle
+        self.As, self.Bs, self.prec = As, Bs, prec
+        self.device = As[0].col.device if As else torch.device("cuda")
+
+    def __len__(self):
+        return len(self.As)
+
+    def result(self, j: int) -> DeviceCSR:
+        c = _native.CsrOut()
+        _native.check(lib().spgemm_batch_result(self.handle, j, ctypes.byref(c)))
+        vdt = _vdtype(self.prec)
+        return DeviceCSR(int(c.rows), int(c.cols), _view(c.row_ptr, c.rows + 1, torch.int64, self.device),
+                         _view(c.col, c.nnz, torch.int32, self.device), _view(c.val, c.nnz, vdt, self.device))
+
+    def info(self) -> dict:
+        info = _native.PlanInfo()
+        _native.check(lib().spgemm_batch_get_info(self.handle, ctypes.byref(info)))
+        return {name: (list(getattr(info, name)) if not isinstance(getattr(info, name), int) else getattr(info, name))
+                for name, _ in _native.PlanInfo._fields_}
+
+    def check(self, stream=None) -> None:
+        _native.check(lib().spgemm_batch_check(self.handle, _stream_handle(stream)))
+
+    def replay(self, stream=None) -> None:
+        _native.check(lib().spgemm_batch_replay(self.handle, _stream_handle(stream)))
+
+    def destroy(self) -> None:
+        if self.handle:
+            _native.check(lib().spgemm_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().spgemm_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def spgemm_batch(As, Bs, prec=F64, opts: _native.Opts | None = None, stream=None) -> Batch:
+    """C_j = A_j * B_j for every job, computed as one stacked product (see include/spgemm.h)."""
+    prec = _prec(prec)
+    n = len(As)
+    if n != len(Bs):
+        raise ValueError("As and Bs differ in length")
+    arr_a = (_native.CsrIn * n)(*[A.as_in() for A in As])
+    arr_b = (_native.CsrIn * n)(*[B.as_in() for B in Bs])
+    h = ctypes.c_void_p()
+    _native.check(lib().spgemm_batch(n, arr_a, arr_b, prec, ctypes.byref(opts) if opts is not None else None, None,
+                                     _stream_handle(stream), ctypes.byref(h)))
+    return Batch(h.value, list(As), list(Bs), prec)
+
+
 def spgemm_multiply_noalloc(A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, stream=None) -> int:
     """C = A*B into the caller's device arrays without any device allocation (small
     products: A.rows <= 65536, rows of C <= 4096 entries, FP64). ``C.col``/``C.val`` give the

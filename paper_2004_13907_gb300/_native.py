@@ -87,6 +87,13 @@ SIGNATURES = {
                                      ctypes.POINTER(CsrOut), c_i64, ctypes.POINTER(c_i64)]),
     "spgemm_multiply_noalloc": (c_i32, [ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut),
                                         c_i64, ctypes.POINTER(c_i64), c_vp]),
+    "spgemm_batch": (c_i32, [c_i64, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_i32, ctypes.POINTER(Opts),
+                             ctypes.POINTER(Allocator), c_vp, ctypes.POINTER(c_vp)]),
+    "spgemm_batch_result": (c_i32, [c_vp, c_i64, ctypes.POINTER(CsrOut)]),
+    "spgemm_batch_get_info": (c_i32, [c_vp, ctypes.POINTER(PlanInfo)]),
+    "spgemm_batch_check": (c_i32, [c_vp, c_vp]),
+    "spgemm_batch_replay": (c_i32, [c_vp, c_vp]),
+    "spgemm_batch_destroy": (c_i32, [c_vp]),
     "spgemm_last_error": (ctypes.c_char_p, []),
     "spgemm_version": (ctypes.c_char_p, []),
 }

@@ -23,7 +23,8 @@ template <int Mode>
 __global__ void __launch_bounds__(256) k_num_tiny(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
                                                   int64_t count, const int64_t* __restrict__ c_off,
                                                   int32_t* __restrict__ ccol, void* __restrict__ cval_,
-                                                  int32_t* __restrict__ row_flag, uint32_t* err) {
+                                                  int32_t* __restrict__ row_flag, const int32_t* __restrict__ abase,
+                                                  uint32_t* err) {
   __shared__ int32_t s_col[8][32];
   __shared__ double s_val[8][32];   // FP64 product (kModeF64, kModeF32R) or the FP32 high part
   __shared__ float s_lo[8][32];     // kModeF32C: the FP32 low part of the product
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(256) k_num_tiny(DevCsr A, DevCsr B, const int3
       for (unsigned m = leaders; m; m &= m - 1) rank += s_col[wid][__ffs(m) - 1] < col;
       if (rank < c_off[i + 1] - c_off[i]) {   // a miscount raises kErrCount, never writes out of the row
         const int64_t out = c_off[i] + rank;
-        ccol[out] = col;
+        ccol[out] = col - (abase ? abase[i] : 0);
         if constexpr (Mode == kModeF32C) {
           // compensated sum of the group's products in product order (Dot2)
           float sum = 0.f, comp = 0.f, mag = 0.f;
@@ -186,7 +187,7 @@ template <int LOG2S>
 __global__ void __launch_bounds__(256) k_num_warp(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
                                                   int64_t count, const int64_t* __restrict__ c_off,
                                                   int32_t* __restrict__ ccol, double* __restrict__ cval,
-                                                  uint32_t* err) {
+                                                  const int32_t* __restrict__ abase, uint32_t* err) {
   constexpr int S = 1 << LOG2S;
   extern __shared__ double smem_f64[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -227,8 +228,9 @@ __global__ void __launch_bounds__(256) k_num_warp(DevCsr A, DevCsr B, const int3
     __syncwarp();
     warp_bitonic(keys, vals, N);
     const int nw_out = cnt < len ? cnt : static_cast<int>(len);
+    const int32_t cb = abase ? abase[i] : 0;
     for (int t = lane; t < nw_out; t += 32) {
-      ccol[off + t] = keys[t];
+      ccol[off + t] = keys[t] - cb;
       cval[off + t] = vals[t];
     }
     __syncwarp();
@@ -239,7 +241,7 @@ template <int LOG2S, int NT>
 __global__ void __launch_bounds__(NT) k_num_block(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
                                                   int64_t count, const int64_t* __restrict__ c_off,
                                                   int32_t* __restrict__ ccol, double* __restrict__ cval,
-                                                  uint32_t* err) {
+                                                  const int32_t* __restrict__ abase, uint32_t* err) {
   constexpr int S = 1 << LOG2S;
   extern __shared__ double smem_f64[];
   double* vals = smem_f64;
@@ -278,8 +280,9 @@ __global__ void __launch_bounds__(NT) k_num_block(DevCsr A, DevCsr B, const int3
     __syncthreads();
     block_bitonic<NT>(keys, vals, N);
     const int nb_out = cnt < len ? cnt : static_cast<int>(len);
+    const int32_t cb = abase ? abase[i] : 0;
     for (int t = threadIdx.x; t < nb_out; t += NT) {
-      ccol[off + t] = keys[t];
+      ccol[off + t] = keys[t] - cb;
       cval[off + t] = vals[t];
     }
     __syncthreads();
@@ -296,28 +299,28 @@ inline unsigned grid_rows(int64_t count, int rows_per_block, int max_blocks) {
 }  // namespace
 
 int launch_num_tiny(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
-                    const int64_t* c_off, int32_t* ccol, void* cval, int32_t* row_flag, uint32_t* err,
-                    cudaStream_t s) {
+                    const int64_t* c_off, int32_t* ccol, void* cval, int32_t* row_flag, const int32_t* abase,
+                    uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   const unsigned g = grid_rows(count, 8, 152 * 64);
-  if (mode == kModeF32C) k_num_tiny<kModeF32C><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, err);
-  else if (mode == kModeF32R) k_num_tiny<kModeF32R><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, err);
-  else k_num_tiny<kModeF64><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, err);
+  if (mode == kModeF32C) k_num_tiny<kModeF32C><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, abase, err);
+  else if (mode == kModeF32R) k_num_tiny<kModeF32R><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, abase, err);
+  else k_num_tiny<kModeF64><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, abase, err);
   return 1;
 }
 
 int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                      int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
-                     uint32_t* err, cudaStream_t s) {
+                     const int32_t* abase, uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   const unsigned g = grid_rows(count, 8, 152 * 32);
   const size_t sm = size_t(8) * (size_t(1) << log2S) * 12;
   switch (log2S) {
-    case 6: k_num_warp<6><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, err); break;
-    case 8: k_num_warp<8><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, err); break;
+    case 6: k_num_warp<6><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, abase, err); break;
+    case 8: k_num_warp<8><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, abase, err); break;
     case 10:
       cudaFuncSetAttribute(k_num_warp<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-      k_num_warp<10><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, err);
+      k_num_warp<10><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, abase, err);
       break;
     default: break;
   }
@@ -326,16 +329,16 @@ int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* 
 
 int launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                       int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
-                      uint32_t* err, cudaStream_t s) {
+                      const int32_t* abase, uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   const size_t sm = (size_t(1) << log2S) * 12;
   if (log2S == 11) {
     k_num_block<11, 256><<<grid_rows(count, 1, 152 * 8), 256, sm, s>>>(A, B, perm, count, c_off, ccol,
-                                                                       cval, err);
+                                                                       cval, abase, err);
   } else if (log2S == 13) {
     cudaFuncSetAttribute(k_num_block<13, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     k_num_block<13, 512><<<grid_rows(count, 1, 152 * 4), 512, sm, s>>>(A, B, perm, count, c_off, ccol,
-                                                                       cval, err);
+                                                                       cval, abase, err);
   }
   return 1;
 }

@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
                                                                int32_t* __restrict__ win_slot,
                                                                uint16_t* __restrict__ blockcnt,
                                                                int64_t nblocks, int32_t* cursor,
-                                                               uint32_t* err) {
+                                                               const int32_t* __restrict__ abase,
+                                                               int64_t width, uint32_t* err) {
   extern __shared__ uint32_t bm[];  // kSymWinBits / 32 words
   __shared__ int32_t s_excl[kSymWinThreads];
   __shared__ int64_t s_bs[kSymWinThreads];
@@ -149,7 +150,6 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
   __shared__ unsigned long long s_total;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int kWarps = kSymWinThreads / 32;
-  const int64_t n = B.cols;
   for (;;) {
     if (threadIdx.x == 0) {
       s_idx = atomicAdd(counter, 1);
@@ -162,23 +162,26 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
     if (threadIdx.x == 0) win_slot[i] = static_cast<int32_t>(idx);
     const int64_t a0 = A.rp[i];
     const int64_t na = A.rp[i + 1] - a0;
+    const int64_t cb = abase ? abase[i] : 0;   // the row's columns are [cb, cb + width)
     uint16_t* cnts = blockcnt + idx * nblocks;
-    for (int64_t w0 = 0; w0 < n; w0 += kSymWinBits) {
-      const int64_t wend = (w0 + kSymWinBits < n) ? w0 + kSymWinBits : n;
+    for (int64_t r0 = 0; r0 < width; r0 += kSymWinBits) {
+      const int64_t w0 = cb + r0;
+      const int64_t wend = cb + ((r0 + kSymWinBits < width) ? r0 + kSymWinBits : width);
       const int nwords = static_cast<int>((wend - w0 + 31) >> 5);
       for (int t = threadIdx.x; t < nwords; t += kSymWinThreads) bm[t] = 0u;
       __syncthreads();
-      if (n <= kSymWinBits) {
+      if (width <= kSymWinBits) {
         // one window covers every column: no cursors, products handed out flattened
         block_for_each_product<kSymWinThreads>(A, B, a0, na, s_excl, s_bs, s_scan, [&](int64_t j, int64_t) {
-          const int32_t c = B.col[j];
-          atomicOr(&bm[c >> 5], 1u << (c & 31));
+          const int64_t rel = B.col[j] - w0;
+          if (rel >= 0 && rel < wend - w0) atomicOr(&bm[rel >> 5], 1u << (rel & 31));
+          else set_error(err, kErrWindowPlan);
         });
       } else {
         for (int64_t e = wid; e < na; e += kWarps) {
           const int32_t k = A.col[a0 + e];
           const int64_t bstart = B.rp[k], bend = B.rp[k + 1];
-          int64_t cur = (w0 == 0) ? bstart : bstart + cursor[a0 + e];
+          int64_t cur = (r0 == 0) ? bstart : bstart + cursor[a0 + e];
           while (cur < bend) {
             const int64_t j = cur + lane;
             const int32_t c = j < bend ? B.col[j] : kNoCol;
@@ -192,11 +195,12 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
         }
         __syncthreads();
       }
-      // per-block counts of this window (warp per block of kBlockWords words)
-      const int64_t b0 = w0 / kBlockCols;
-      const int64_t b1 = (wend + kBlockCols - 1) / kBlockCols;
+      // per-block counts of this window (warp per block of kBlockWords words); blocks are
+      // counted from the row's first column cb
+      const int64_t b0 = r0 / kBlockCols;
+      const int64_t b1 = (wend - cb + kBlockCols - 1) / kBlockCols;
       for (int64_t b = b0 + wid; b < b1; b += kWarps) {
-        const int wlo = static_cast<int>(b * kBlockWords - (w0 >> 5));
+        const int wlo = static_cast<int>(b * kBlockWords - (r0 >> 5));
         const int whi = wlo + kBlockWords < nwords ? wlo + kBlockWords : nwords;
         int c = 0;
         for (int t = wlo + lane; t < whi; t += 32) c += __popc(bm[t]);
@@ -258,8 +262,8 @@ int launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t*
 
 int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                        int32_t* counter, int32_t* nnz_row, int32_t* win_slot, uint16_t* blockcnt,
-                       int64_t nblocks, int32_t* cursor, int num_sms, uint32_t* err,
-                       cudaStream_t s) {
+                       int64_t nblocks, int32_t* cursor, const int32_t* abase, int64_t width,
+                       int num_sms, uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   const size_t sm = size_t(kSymWinBits / 32) * 4;
   cudaFuncSetAttribute(k_sym_window, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
@@ -267,7 +271,7 @@ int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int
   const int64_t g = count < num_sms ? count : num_sms;
   k_sym_window<<<static_cast<unsigned>(g), kSymWinThreads, sm, s>>>(A, B, perm, count, counter, nnz_row,
                                                                  win_slot, blockcnt, nblocks, cursor,
-                                                                 err);
+                                                                 abase, width, err);
   return 1;
 }
 

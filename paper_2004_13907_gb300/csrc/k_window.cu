@@ -66,7 +66,8 @@ static_assert(WinGeom<kModeF32C>::kSmemBytes + 1024 + 512 <= 227 * 1024, "shared
 
 // Split table: one warp per row k of B writes split[k * (nblocks + 1) + b] for b in
 // [0, nblocks]: the offset within row k of its first entry with column >= b * kBlockCols.
-__global__ void __launch_bounds__(256) k_bsplit(DevCsr B, int64_t nblocks, int32_t* __restrict__ split) {
+__global__ void __launch_bounds__(256) k_bsplit(DevCsr B, int64_t nblocks, const int32_t* __restrict__ bbase,
+                                                int32_t* __restrict__ split) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(256) k_bsplit(DevCsr B, int64_t nblocks, int32
   for (int64_t k = gw; k < B.rows; k += nw) {
     const int64_t s = B.rp[k];
     const int32_t len = static_cast<int32_t>(B.rp[k + 1] - s);
+    const int64_t bb = bbase ? bbase[k] : 0;   // blocks are counted from the row's first column
     int32_t* out = split + k * (nblocks + 1);
     if (len == 0) {
       for (int64_t b = lane; b <= nblocks; b += 32) out[b] = 0;
@@ -82,8 +84,8 @@ __global__ void __launch_bounds__(256) k_bsplit(DevCsr B, int64_t nblocks, int32
     for (int32_t t0 = 0; t0 < len; t0 += 32) {
       const int32_t t = t0 + lane;
       if (t < len) {
-        const int64_t bc = B.col[s + t] >> kShift;
-        const int64_t bp = t == 0 ? -1 : (B.col[s + t - 1] >> kShift);
+        const int64_t bc = (B.col[s + t] - bb) >> kShift;
+        const int64_t bp = t == 0 ? -1 : ((B.col[s + t - 1] - bb) >> kShift);
         for (int64_t b = bp + 1; b <= bc; ++b) out[b] = t;
         if (t == len - 1)
           for (int64_t b = bc + 1; b <= nblocks; ++b) out[b] = len;
@@ -147,7 +149,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     const int64_t* __restrict__ c_off, const int32_t* __restrict__ win_slot,
     const uint16_t* __restrict__ blockcnt, int64_t nblocks, int64_t nslots,
     const int32_t* __restrict__ split, int32_t merge_cap, int32_t* __restrict__ ccol,
-    void* __restrict__ cval_, int32_t* __restrict__ row_flag, uint32_t* err) {
+    void* __restrict__ cval_, int32_t* __restrict__ row_flag, const int32_t* __restrict__ abase,
+    int64_t width, uint32_t* err) {
   constexpr int kSmemVals = WinGeom<Mode>::kSmemVals;
   extern __shared__ __align__(16) unsigned char win_smem[];
   double* vals = reinterpret_cast<double*>(win_smem);        // kModeF64, kModeF32R
@@ -175,7 +178,6 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
   __shared__ int32_t s_ctl[8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int kWarps = kNumThreads / 32;
-  const int64_t n = B.cols;
   const double* av64 = static_cast<const double*>(A.val);
   const double* bv64 = static_cast<const double*>(B.val);
   const float* av32 = static_cast<const float*>(A.val);
@@ -251,6 +253,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     const uint16_t* gcnt = blockcnt + slot * nblocks;
     const int64_t a0 = A.rp[i];
     const int64_t na = A.rp[i + 1] - a0;
+    const int64_t cb = abase ? abase[i] : 0;   // the row's columns are [cb, cb + width)
     const bool resident = na <= kNumThreads;
     if (cnt_cached)
       for (int64_t b = threadIdx.x; b < nblocks; b += kNumThreads) s_cnt[b] = gcnt[b];
@@ -291,8 +294,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
       if (nwin == 0) break;
       for (int wi = 0; wi < nwin; ++wi) {
         const int64_t b0 = w_b0[wi], b1 = w_b1[wi];
-        const int64_t w0 = b0 * kBlockCols;
-        const int64_t w1 = b1 * kBlockCols < n ? b1 * kBlockCols : n;
+        const int64_t w0 = cb + b0 * kBlockCols;
+        const int64_t w1 = cb + (b1 * kBlockCols < width ? b1 * kBlockCols : width);
         const int32_t span = static_cast<int32_t>(w1 - w0);
         const int32_t expect = w_cnt[wi];
         const int nwords = (span + 31) >> 5;
@@ -455,7 +458,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
           bm[w] = 0u;
           int r = grp[w / kGroupWords] + pre[w];
           for (; m; m &= m - 1) {
-            if (r < kRankCap) colbuf[r] = static_cast<int32_t>(w0 + w * 32 + (__ffs(m) - 1));
+            if (r < kRankCap) colbuf[r] = static_cast<int32_t>(w0 - cb + w * 32 + (__ffs(m) - 1));
             ++r;
           }
         }
@@ -476,19 +479,19 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
 
 int64_t split_table_bytes(int64_t brows, int64_t nblocks) { return brows * (nblocks + 1) * 4; }
 
-int launch_bsplit(const DevCsr& B, int64_t nblocks, int32_t* split, cudaStream_t s) {
+int launch_bsplit(const DevCsr& B, int64_t nblocks, const int32_t* bbase, int32_t* split, cudaStream_t s) {
   if (B.rows <= 0) return 0;
   int64_t g = (B.rows * 32 + 255) / 256;
   if (g > 152 * 64) g = 152 * 64;
-  k_bsplit<<<static_cast<unsigned>(g), 256, 0, s>>>(B, nblocks, split);
+  k_bsplit<<<static_cast<unsigned>(g), 256, 0, s>>>(B, nblocks, bbase, split);
   return 1;
 }
 
 int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                       int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
-                      int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag, int num_sms,
-                      uint32_t* err, cudaStream_t s) {
+                      int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag,
+                      const int32_t* abase, int64_t width, int num_sms, uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   auto go = [&](auto kernel, int smem, int per_sm) {
@@ -496,7 +499,7 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
     const int64_t g = count < int64_t(per_sm) * num_sms ? count : int64_t(per_sm) * num_sms;
     kernel<<<static_cast<unsigned>(g), kNumThreads, smem, s>>>(A, B, perm, count, counter, c_off, win_slot,
                                                                blockcnt, nblocks, nslots, split, merge_cap,
-                                                               ccol, cval, row_flag, err);
+                                                               ccol, cval, row_flag, abase, width, err);
   };
   if (mode == kModeF32C) go(k_num_window<kModeF32C>, WinGeom<kModeF32C>::kSmemBytes, 1);
   else if (mode == kModeF32R) go(k_num_window<kModeF32R>, WinGeom<kModeF32R>::kSmemBytes, 2);

@@ -9,16 +9,22 @@
 
 namespace spg {
 
-namespace {
-
 template <typename T>
-T* ws_get(spgemm_plan_s* p, int64_t count, spgemm_status* st) {
+T* ws_alloc(spgemm_plan_s* p, int64_t count, spgemm_status* st) {
   if (*st != SPGEMM_OK) return nullptr;
   void* ptr = p->ws.get(static_cast<size_t>(count < 1 ? 1 : count) * sizeof(T));
   if (!ptr) *st = set_error_msg(SPGEMM_ERR_OOM, "device workspace allocation of %lld bytes failed",
                                 (long long)(count * (int64_t)sizeof(T)));
   return static_cast<T*>(ptr);
 }
+template int32_t* ws_alloc<int32_t>(spgemm_plan_s*, int64_t, spgemm_status*);
+template int64_t* ws_alloc<int64_t>(spgemm_plan_s*, int64_t, spgemm_status*);
+
+namespace {
+
+template <typename T>
+T* ws_get(spgemm_plan_s* p, int64_t count, spgemm_status* st) { return ws_alloc<T>(p, count, st); }
+
 
 spgemm_status read_summary(spgemm_plan_s* p, Summary* h, cudaStream_t s) {
   cudaError_t e = cudaMemcpyAsync(h, p->summary, sizeof(Summary), cudaMemcpyDeviceToHost, s);
@@ -96,7 +102,8 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   p->A = DevCsr{m, A->cols, A->nnz, arp, A->col, A->val};
   p->B = DevCsr{B->rows, n, B->nnz, brp, B->col, B->val};
   const spgemm_opts& o = p->opts;
-  p->cp.n = n;
+  if (p->width <= 0) p->width = n;
+  p->cp.n = p->width;
   p->cp.tiny_max = clampi(o.tiny_max, 0, 32);
   p->cp.warp_max = clampi(o.warp_max, 0, 1024);
   p->cp.block_max = clampi(o.block_max, p->cp.warp_max > 32 ? p->cp.warp_max : 32, 4096);
@@ -147,7 +154,7 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   }
   const int64_t nwin = p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0];
   if (nwin > 0) {
-    p->nblocks = (n + kBlockCols - 1) / kBlockCols;
+    p->nblocks = (p->width + kBlockCols - 1) / kBlockCols;
     const int64_t cnt_bytes = nwin * p->nblocks * 2;
     if (cnt_bytes > (int64_t(8) << 30))
       return set_error_msg(SPGEMM_ERR_UNSUPPORTED, "windowed rows need %lld bytes of block counts", (long long)cnt_bytes);
@@ -171,7 +178,7 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
     stage_begin(p, SPGEMM_STAGE_SYM_WINDOW, s);
     nl = launch_sym_window(p->A, p->B, seg(kSymWin0), p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0],
                            p->counters + 0, p->nnz_row, p->win_slot, p->blockcnt, p->nblocks, p->cursor,
-                           p->num_sms, err, s);
+                           p->abase, p->width, p->num_sms, err, s);
     stage_end(p, SPGEMM_STAGE_SYM_WINDOW, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_BLOCK, s);
     nl = launch_sym_block(13, p->A, p->B, seg(kSymBlock), cnt(kSymBlock), p->nnz_row, err, s);
@@ -239,28 +246,30 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       const int64_t bytes = split_table_bytes(p->B.rows, p->nblocks);
       if (bytes <= (int64_t(p->opts.window_split_max_mb) << 20)) {
         p->split = static_cast<int32_t*>(p->ws.get(static_cast<size_t>(bytes)));
-        if (p->split) nl += launch_bsplit(p->B, p->nblocks, p->split, s);
+        if (p->split) nl += launch_bsplit(p->B, p->nblocks, p->bbase, p->split, s);
       }
     }
     nl += launch_num_window(mode, p->A, p->B, seg(kNumWin0), nwin, p->counters + 1, p->c_off, p->win_slot,
                             p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
-                            p->rerun_flag, p->num_sms, err, s);
+                            p->rerun_flag, p->abase, p->width, p->num_sms, err, s);
     stage_end(p, SPGEMM_STAGE_NUM_WINDOW, nl, s);
     if (!f32c) {
       double* cval = static_cast<double*>(C->val);
       stage_begin(p, SPGEMM_STAGE_NUM_BLOCK, s);
-      nl = launch_num_block(13, p->A, p->B, seg(kNumBlock2), cnt(kNumBlock2), p->c_off, C->col, cval, err, s);
-      nl += launch_num_block(11, p->A, p->B, seg(kNumBlock1), cnt(kNumBlock1), p->c_off, C->col, cval, err, s);
+      nl = launch_num_block(13, p->A, p->B, seg(kNumBlock2), cnt(kNumBlock2), p->c_off, C->col, cval, p->abase,
+                            err, s);
+      nl += launch_num_block(11, p->A, p->B, seg(kNumBlock1), cnt(kNumBlock1), p->c_off, C->col, cval, p->abase,
+                             err, s);
       stage_end(p, SPGEMM_STAGE_NUM_BLOCK, nl, s);
       stage_begin(p, SPGEMM_STAGE_NUM_WARP, s);
-      nl = launch_num_warp(10, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, cval, err, s);
-      nl += launch_num_warp(8, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, cval, err, s);
-      nl += launch_num_warp(6, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, cval, err, s);
+      nl = launch_num_warp(10, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, cval, p->abase, err, s);
+      nl += launch_num_warp(8, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, cval, p->abase, err, s);
+      nl += launch_num_warp(6, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, cval, p->abase, err, s);
       stage_end(p, SPGEMM_STAGE_NUM_WARP, nl, s);
     }
     stage_begin(p, SPGEMM_STAGE_NUM_TINY, s);
     nl = launch_num_tiny(mode, p->A, p->B, seg(kNumTiny), cnt(kNumTiny), p->c_off, C->col, C->val, p->rerun_flag,
-                         err, s);
+                         p->abase, err, s);
     stage_end(p, SPGEMM_STAGE_NUM_TINY, nl, s);
     if (f32c && !p->opts.f32c_rerun_none) {
       // rows with an entry over the compensated bound are recomputed in FP64 and rounded once
@@ -277,8 +286,9 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       if (e != cudaSuccess) return cuda_status(e, "reading the FP64 rerun counts");
       nl += launch_num_window(kModeF32R, p->A, p->B, list_w, hc[0], p->counters + 2, p->c_off, p->win_slot,
                               p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
-                              nullptr, p->num_sms, err, s);
-      nl += launch_num_tiny(kModeF32R, p->A, p->B, list_t, hc[1], p->c_off, C->col, C->val, nullptr, err, s);
+                              nullptr, p->abase, p->width, p->num_sms, err, s);
+      nl += launch_num_tiny(kModeF32R, p->A, p->B, list_t, hc[1], p->c_off, C->col, C->val, nullptr, p->abase, err,
+                            s);
       stage_end(p, SPGEMM_STAGE_NUM_RERUN, nl, s);
       p->f32c_rerun_rows = int64_t(hc[0]) + hc[1];
     }

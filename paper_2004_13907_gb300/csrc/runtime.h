@@ -55,6 +55,12 @@ struct spgemm_plan_s {
   int64_t nblocks = 0;
   int32_t* cursor = nullptr;
   int32_t* split = nullptr;          // column-block split table of B (windowed numeric rows)
+  // Column space of the rows: [abase[i], abase[i] + width) for row i of A (and B's rows start at
+  // bbase[k]); a single product has no bases and width = n. A batch run as one block-diagonal
+  // product gives every row the columns of its job.
+  const int32_t* abase = nullptr;
+  const int32_t* bbase = nullptr;
+  int64_t width = 0;
   bool split_tried = false;
   // FP32-compensated path
   int32_t* rerun_flag = nullptr;     // per row: 1 = recompute in FP64
@@ -79,6 +85,8 @@ namespace spg {
 
 spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_csr_in* B,
                        cudaStream_t s);
+template <typename T>
+T* ws_alloc(spgemm_plan_s* p, int64_t count, spgemm_status* st);
 spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s);
 spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s);
 spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s);
