@@ -292,6 +292,99 @@ def run_ours(args):
     return line, rank
 
 
+def _batch_jobs(max_expected_products: float, limit: int = 4096):
+    """Jobs of the batch distribution (n log-uniform in [100, 50000], density log-uniform in
+    [1e-4, 1e-2]) whose expected product count n^3 d^2 is below the cap."""
+    out = []
+    for i in range(limit):
+        n, d = synth.batch_job_params(i, 0)
+        if n ** 3 * d * d < max_expected_products:
+            out.append((i,) + synth.batch_job(i, 0))
+    return out
+
+
+def run_batch(args):
+    """Batched form (one stacked product for every job) against the plain per-product launch
+    (plan, symbolic, allocate, numeric per job), same jobs, same GPU."""
+    import torch
+    import paper_2004_13907_gb300 as sp
+    cap = 1e6 if args.workload == "batch_small" else 1e7
+    jobs = _batch_jobs(cap)
+    dA = [sp.DeviceCSR.from_host(A, "cuda") for _, A, _ in jobs]
+    dB = [sp.DeviceCSR.from_host(B, "cuda") for _, _, B in jobs]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        b = sp.spgemm_batch(dA, dB)
+        return b
+
+    def per_product():
+        out = []
+        for a, b in zip(dA, dB):
+            out.append(sp.multiply(a, b))
+        return out
+
+    for _ in range(args.warmup):
+        b = batched()
+        b.destroy()
+        per_product()
+        flush.zero_()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    tb, tp, tr = [], [], []
+    launches = 0
+    products = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b = batched()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb.append(e0.elapsed_time(e1))
+        info = b.info()
+        products = info["products"]
+        launches += info["kernel_launches"]
+        # numeric-only recompute through the captured graph
+        b.replay()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tr.append(e0.elapsed_time(e1))
+        b.destroy()
+        flush.zero_()
+        e0.record(stream)
+        res = per_product()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp.append(e0.elapsed_time(e1))
+        del res
+    clocks = sampler.stop()
+    ms_b, ms_p, ms_r = float(np.mean(tb)), float(np.mean(tp)), float(np.mean(tr))
+    gf = lambda ms: round(2.0 * products / (ms * 1e-3) / 1e9, 3)
+    return {
+        "metric": METRIC, "value": gf(ms_b), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_b, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload,
+                   "description": f"{len(jobs)} jobs of the batch distribution with expected products below "
+                                  f"{cap:.0e} (n log-uniform [100, 50000], density log-uniform [1e-4, 1e-2], "
+                                  f"A_j, B_j independent, FP64 U[-1,1], seed 0)",
+                   "jobs": len(jobs), "products_per_step": products, "l2": "flushed between steps",
+                   "parallelism": "one GPU, one stacked product"},
+        "per_product_launch": {"value": gf(ms_p), "unit": UNIT, "ms_per_step": round(ms_p, 3),
+                               "what": "plan + symbolic + allocate + numeric for each job in turn"},
+        "batched_speedup": round(ms_p / ms_b, 2),
+        "graph_replay": {"value": gf(ms_r), "unit": UNIT, "ms_per_step": round(ms_r, 4),
+                         "what": "numeric-only recompute of every job as one CUDA graph launch"},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }, 0
+
+
 def _pinned(n: int, dtype, torch):
     """Page-locked host array of exactly n elements (numpy memory registered with CUDA)."""
     a = np.empty(max(n, 1), dtype=dtype)
@@ -445,7 +538,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lap2d1024+rmat20", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="lap2d1024+rmat20",
+                    choices=sorted(WORKLOADS) + ["batch_small", "batch_mid"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -456,6 +550,8 @@ def main():
         sys.stderr.write("note: fewer than 3 warm-up steps\n")
     if args.impl == "reference":
         line, rank = run_reference(args)
+    elif args.workload.startswith("batch"):
+        line, rank = run_batch(args)
     else:
         line, rank = run_ours(args)
     if rank == 0 and line is not None:
