@@ -278,6 +278,119 @@ spgemm_status spgemm_multiply_noalloc(const spgemm_csr_in* A, const spgemm_csr_i
                                       spgemm_csr_out* C, int64_t nnz_capacity, int64_t* nnz_c,
                                       void* stream);
 
+/* ---- Serving: a long-lived server that takes products one at a time, from any host thread, and
+ * runs them in fused batches (continuous batching). The paper has no counterpart; this is the
+ * library's serving layer over the batched product above.
+ * A scheduler thread gathers queued jobs in arrival order (up to max_batch_jobs, or until the
+ * jobs' input entries reach max_batch_entries; it waits up to batch_window_us after the oldest
+ * queued job arrived for more to come), stacks them as spgemm_batch does and runs the plan and
+ * symbolic pass. That pass gives the EXACT device bytes of the batch (stacked inputs, plan
+ * workspace, numeric tables and output); the numeric pass starts only when the bytes held by
+ * the server plus that figure fit mem_cap_bytes, else it waits for running batches to finish or
+ * for results to be released. A batch that does not fit the cap even alone is split in halves;
+ * a single job that does not fit alone is REJECTED. A batch whose preparation fails is retried
+ * job by job, so one bad job fails alone. Up to num_streams batches are in flight, each on a
+ * stream of its own, so one batch's symbolic pass overlaps another's numeric pass. Completion
+ * is signalled by a host callback on the batch's stream; a job's latency runs from its submit
+ * call until it is marked done. Results stay in device memory, counted against the cap, until
+ * spgemm_server_release. Every call is thread-safe. */
+typedef struct spgemm_server_s spgemm_server_t;
+
+typedef struct {
+  int64_t mem_cap_bytes;       /* device bytes the server's batches and results may hold
+                                  (default 32 GiB) */
+  int64_t max_batch_entries;   /* a batch stops growing once its jobs' nnz(A)+nnz(B) reach
+                                  this (default 2^26); a bigger job runs alone */
+  int32_t max_batch_jobs;      /* jobs per batch at most (default 1024) */
+  int32_t batch_window_us;     /* fill window after the oldest queued job (default 200) */
+  int32_t num_streams;         /* batches in flight, 1..8 (default 2) */
+  int32_t start_paused;        /* queue jobs but start none until spgemm_server_resume */
+  int32_t prec;                /* spgemm_prec of every job (default SPGEMM_F64) */
+  int32_t reserved_[3];
+  spgemm_opts opts;            /* options of each batch's plan */
+} spgemm_server_cfg;
+
+typedef enum {
+  SPGEMM_JOB_QUEUED = 0,
+  SPGEMM_JOB_RUNNING = 1,      /* in a batch being prepared, admitted or computed */
+  SPGEMM_JOB_DONE = 2,
+  SPGEMM_JOB_FAILED = 3,       /* status says why (spgemm_server_poll sets the message) */
+  SPGEMM_JOB_REJECTED = 4      /* needs more than mem_cap_bytes on its own */
+} spgemm_job_state;
+
+typedef struct {
+  int32_t state;               /* spgemm_job_state */
+  int32_t status;              /* spgemm_status of a finished job */
+  int64_t batch;               /* id of the batch it ran in (-1 if none) */
+  int64_t batch_jobs;          /* jobs in that batch */
+  int64_t rows, cols, nnz;     /* shape and nnz of C */
+  int64_t bytes;               /* device bytes of the job's result (row_ptr, col, val) */
+  int64_t needed_bytes;        /* exact bytes of the smallest batch that held it (for a
+                                  REJECTED job: what it alone would need) */
+  double queue_ms;             /* submit -> its batch started preparing */
+  double run_ms;               /* batch start -> done */
+  double latency_ms;           /* submit -> done */
+} spgemm_job_info;
+
+typedef struct {
+  int64_t submitted, completed, failed, rejected, queued, running;
+  int64_t batches;             /* batches completed */
+  int64_t splits;              /* batches split for the memory cap */
+  int64_t products;            /* partial products of completed batches */
+  int64_t nnz_out;             /* entries of completed results */
+  int64_t bytes_in_use;        /* device bytes held now (batches in flight + unreleased results) */
+  int64_t bytes_peak;          /* most bytes held at once */
+  int64_t mem_cap_bytes;
+  double latency_p50_ms, latency_p99_ms, latency_max_ms, latency_mean_ms;
+  double mean_batch_jobs;      /* jobs per completed batch */
+  double elapsed_s;            /* first submit to last completion */
+  double jobs_per_s;           /* completed jobs / elapsed_s */
+  double products_per_s;       /* products / elapsed_s */
+  int64_t reserved_[8];
+} spgemm_server_stats;
+
+spgemm_status spgemm_server_cfg_default(spgemm_server_cfg* cfg);
+
+/* Starts a server on the current device (its threads and num_streams streams). */
+spgemm_status spgemm_server_create(const spgemm_server_cfg* cfg, spgemm_server_t** out_server);
+
+/* Queues C = A*B. A, B: device CSR descriptors (as for spgemm_plan), in the server's precision;
+ * the arrays must stay valid and unchanged until the job reaches a final state. *job receives
+ * the job id. The server reads them on its own streams, which are not ordered after the caller's:
+ * the arrays must already be written (synchronize the stream that produced them). Shape errors
+ * are returned here (INVALID_ARG); errors found on the device fail the job. */
+spgemm_status spgemm_server_submit(spgemm_server_t* server, const spgemm_csr_in* A,
+                                   const spgemm_csr_in* B, int64_t* job);
+
+/* Job state now: OK when done, NOT_READY while queued or running, the job's status when it
+ * failed or was rejected (with its message in spgemm_last_error). info may be NULL. */
+spgemm_status spgemm_server_poll(spgemm_server_t* server, int64_t job, spgemm_job_info* info);
+
+/* As poll, but waits up to timeout_s seconds (< 0: no limit) for a final state; TIMEOUT if the
+ * job is still queued or running then. */
+spgemm_status spgemm_server_wait(spgemm_server_t* server, int64_t job, double timeout_s,
+                                 spgemm_job_info* info);
+
+/* A done job's result as a standalone CSR view (device pointers, int64 row_ptr from 0),
+ * valid until spgemm_server_release of that job. NOT_READY before it is done. */
+spgemm_status spgemm_server_result(spgemm_server_t* server, int64_t job, spgemm_csr_out* C);
+
+/* Forgets a finished job. Its result memory returns to the budget once every job of its batch
+ * has been released. NOT_READY for a job not yet finished, INVALID_ARG for an unknown id. */
+spgemm_status spgemm_server_release(spgemm_server_t* server, int64_t job);
+
+/* Stop / restart starting new batches (queued and submitted jobs wait). */
+spgemm_status spgemm_server_pause(spgemm_server_t* server);
+spgemm_status spgemm_server_resume(spgemm_server_t* server);
+
+/* Counters and latency percentiles since creation or the last reset. */
+spgemm_status spgemm_server_get_stats(spgemm_server_t* server, spgemm_server_stats* stats);
+spgemm_status spgemm_server_reset_stats(spgemm_server_t* server);
+
+/* Stops the scheduler, waits for the batches in flight, fails jobs still queued and frees every
+ * result. NULL is accepted. */
+spgemm_status spgemm_server_destroy(spgemm_server_t* server);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* spgemm_last_error(void);
 

@@ -25,8 +25,8 @@ __all__ = [
     "DeviceCSR", "Plan", "SpgemmError", "F64", "F32_COMPENSATED", "spgemm_opts_default",
     "spgemm_plan", "spgemm_symbolic", "spgemm_numeric", "spgemm_plan_get_info",
     "spgemm_plan_check", "spgemm_plan_get_timings", "spgemm_plan_destroy", "spgemm_multiply_host", "spgemm_multiply_noalloc",
-    "spgemm_last_error",
-    "spgemm_version", "multiply", "lib",
+    "spgemm_last_error", "spgemm_version", "multiply", "lib", "Batch", "spgemm_batch", "Server",
+    "spgemm_server_cfg_default",
 ]
 
 
@@ -331,3 +331,109 @@ def spgemm_multiply_host(A, B, prec=F64, opts: _native.Opts | None = None, strea
         n = int(nnz.value)
         return DeviceCSR(A.rows, B.cols, out.row_ptr, out.col[:n], out.val[:n])
     raise RuntimeError("spgemm_multiply_host: capacity retry failed")
+
+
+def spgemm_server_cfg_default(**overrides) -> _native.ServerCfg:
+    """Server configuration with the library defaults, then ``overrides`` (field=value; ``opts``
+    takes an ``Opts``, ``prec`` a precision name or code)."""
+    cfg = _native.ServerCfg()
+    _native.check(lib().spgemm_server_cfg_default(ctypes.byref(cfg)))
+    for k, v in overrides.items():
+        if k == "prec":
+            v = _prec(v)
+        if not hasattr(cfg, k):
+            raise AttributeError(f"spgemm_server_cfg has no field {k!r}")
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _job_dict(info: _native.JobInfo) -> dict:
+    d = {name: getattr(info, name) for name, _ in _native.JobInfo._fields_}
+    d["state"] = _native.JOB_STATES.get(info.state, str(info.state))
+    d["status"] = _native.STATUS_NAMES.get(info.status, str(info.status))
+    return d
+
+
+class Server:
+    """Handle of a native server (continuous batching, see include/spgemm.h). The Python object
+    keeps each job's input tensors alive until the job is released."""
+
+    def __init__(self, cfg: _native.ServerCfg | None = None, **overrides):
+        if cfg is None:
+            cfg = spgemm_server_cfg_default(**overrides)
+        self.prec = int(cfg.prec)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        _native.check(lib().spgemm_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self._inputs = {}
+
+    def submit(self, A: DeviceCSR, B: DeviceCSR, sync: bool = True) -> int:
+        """Queues C = A*B. The server reads A and B on its own streams, so they must be written
+        before this call: with ``sync`` the current stream is synchronized first."""
+        if sync:
+            torch.cuda.current_stream().synchronize()
+        a, b = A.as_in(), B.as_in()
+        job = ctypes.c_int64()
+        _native.check(lib().spgemm_server_submit(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(job)))
+        self._inputs[job.value] = (A, B)
+        return int(job.value)
+
+    def poll(self, job: int) -> dict:
+        """The job's state and timings; never raises for a failed job (see ``state``)."""
+        info = _native.JobInfo()
+        st = lib().spgemm_server_poll(self.handle, job, ctypes.byref(info))
+        if st == 1:
+            _native.check(st)
+        return _job_dict(info)
+
+    def wait(self, job: int, timeout: float | None = None) -> dict:
+        """Waits for a final state; raises SpgemmError (TIMEOUT, or the job's own error)."""
+        info = _native.JobInfo()
+        _native.check(lib().spgemm_server_wait(self.handle, job, -1.0 if timeout is None else float(timeout),
+                                               ctypes.byref(info)))
+        return _job_dict(info)
+
+    def result(self, job: int) -> DeviceCSR:
+        """View of a done job's result (valid until ``release``)."""
+        c = _native.CsrOut()
+        _native.check(lib().spgemm_server_result(self.handle, job, ctypes.byref(c)))
+        vdt = _vdtype(self.prec)
+        return DeviceCSR(int(c.rows), int(c.cols), _view(c.row_ptr, c.rows + 1, torch.int64, self.device),
+                         _view(c.col, c.nnz, torch.int32, self.device), _view(c.val, c.nnz, vdt, self.device))
+
+    def release(self, job: int) -> None:
+        _native.check(lib().spgemm_server_release(self.handle, job))
+        self._inputs.pop(job, None)
+
+    def pause(self) -> None:
+        _native.check(lib().spgemm_server_pause(self.handle))
+
+    def resume(self) -> None:
+        _native.check(lib().spgemm_server_resume(self.handle))
+
+    def stats(self) -> dict:
+        s = _native.ServerStats()
+        _native.check(lib().spgemm_server_get_stats(self.handle, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in _native.ServerStats._fields_ if name != "reserved_"}
+
+    def reset_stats(self) -> None:
+        _native.check(lib().spgemm_server_reset_stats(self.handle))
+
+    def close(self) -> None:
+        if self.handle:
+            _native.check(lib().spgemm_server_destroy(self.handle))
+            self.handle = None
+            self._inputs.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -71,6 +71,30 @@ class Timings(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 16), ("launches", c_i32 * 16)]
 
 
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("mem_cap_bytes", c_i64), ("max_batch_entries", c_i64), ("max_batch_jobs", c_i32),
+                ("batch_window_us", c_i32), ("num_streams", c_i32), ("start_paused", c_i32), ("prec", c_i32),
+                ("reserved_", c_i32 * 3), ("opts", Opts)]
+
+
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "rejected"}
+
+
+class JobInfo(ctypes.Structure):
+    _fields_ = [("state", c_i32), ("status", c_i32), ("batch", c_i64), ("batch_jobs", c_i64), ("rows", c_i64),
+                ("cols", c_i64), ("nnz", c_i64), ("bytes", c_i64), ("needed_bytes", c_i64),
+                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, c_i64) for n in ("submitted", "completed", "failed", "rejected", "queued", "running", "batches",
+                                     "splits", "products", "nnz_out", "bytes_in_use", "bytes_peak",
+                                     "mem_cap_bytes")] + \
+               [(n, ctypes.c_double) for n in ("latency_p50_ms", "latency_p99_ms", "latency_max_ms",
+                                               "latency_mean_ms", "mean_batch_jobs", "elapsed_s", "jobs_per_s",
+                                               "products_per_s")] + [("reserved_", c_i64 * 8)]
+
+
 # name -> (restype, argtypes); every symbol include/spgemm.h declares
 SIGNATURES = {
     "spgemm_opts_default": (None, [ctypes.POINTER(Opts)]),
@@ -94,6 +118,18 @@ SIGNATURES = {
     "spgemm_batch_check": (c_i32, [c_vp, c_vp]),
     "spgemm_batch_replay": (c_i32, [c_vp, c_vp]),
     "spgemm_batch_destroy": (c_i32, [c_vp]),
+    "spgemm_server_cfg_default": (c_i32, [ctypes.POINTER(ServerCfg)]),
+    "spgemm_server_create": (c_i32, [ctypes.POINTER(ServerCfg), ctypes.POINTER(c_vp)]),
+    "spgemm_server_submit": (c_i32, [c_vp, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(c_i64)]),
+    "spgemm_server_poll": (c_i32, [c_vp, c_i64, ctypes.POINTER(JobInfo)]),
+    "spgemm_server_wait": (c_i32, [c_vp, c_i64, ctypes.c_double, ctypes.POINTER(JobInfo)]),
+    "spgemm_server_result": (c_i32, [c_vp, c_i64, ctypes.POINTER(CsrOut)]),
+    "spgemm_server_release": (c_i32, [c_vp, c_i64]),
+    "spgemm_server_pause": (c_i32, [c_vp]),
+    "spgemm_server_resume": (c_i32, [c_vp]),
+    "spgemm_server_get_stats": (c_i32, [c_vp, ctypes.POINTER(ServerStats)]),
+    "spgemm_server_reset_stats": (c_i32, [c_vp]),
+    "spgemm_server_destroy": (c_i32, [c_vp]),
     "spgemm_last_error": (ctypes.c_char_p, []),
     "spgemm_version": (ctypes.c_char_p, []),
 }

@@ -17,7 +17,7 @@
 #include <string>
 #include <vector>
 
-#include "runtime.h"
+#include "batch.h"
 
 namespace spg {
 
@@ -127,10 +127,11 @@ struct spgemm_batch_s {
   cudaStream_t capture_stream = nullptr;   // private stream the graph is captured on
 };
 
-extern "C" spgemm_status spgemm_batch(int64_t n_jobs, const spgemm_csr_in* A, const spgemm_csr_in* B,
-                                      spgemm_prec prec, const spgemm_opts* opts, const spgemm_allocator* alloc,
-                                      void* stream, spgemm_batch_t** out) {
-  clear_error_msg();
+namespace spg {
+
+spgemm_status batch_prepare(int64_t n_jobs, const spgemm_csr_in* A, const spgemm_csr_in* B, spgemm_prec prec,
+                            const spgemm_opts* opts, const spgemm_allocator* alloc, void* stream,
+                            spgemm_batch_t** out) {
   if (!out) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n_jobs < 1 || !A || !B) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "need n_jobs >= 1 and job arrays");
@@ -275,21 +276,102 @@ extern "C" spgemm_status spgemm_batch(int64_t n_jobs, const spgemm_csr_in* A, co
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { cuda_status(e, "reading the batch row offsets"); return fail(SPGEMM_ERR_CUDA); }
   for (int64_t j = 0; j <= n_jobs; ++j) b->job_nnz0[j] = h_off[row0[j]];
+  *out = b;
+  return SPGEMM_OK;
+}
+
+void batch_prepare_bounds(int64_t n_jobs, const spgemm_csr_in* A, const spgemm_csr_in* B, spgemm_prec prec,
+                          int64_t* lo, int64_t* hi) {
+  const int vb = prec == SPGEMM_F64 ? 8 : 4;
+  int64_t rows = 0, inner = 0, a_nnz = 0, b_nnz = 0, width = 1, stack_tiles = 0, value_tiles = 0, rp_tiles = 0;
+  for (int64_t j = 0; j < n_jobs; ++j) {
+    rows += A[j].rows;
+    inner += B[j].rows;
+    a_nnz += A[j].nnz;
+    b_nnz += B[j].nnz;
+    width = B[j].cols > width ? B[j].cols : width;
+    auto t = [](int64_t c) { return (c + kTile - 1) / kTile; };
+    stack_tiles += t(A[j].rows) + t(A[j].nnz) + t(B[j].rows) + t(B[j].nnz);
+    value_tiles += t(A[j].nnz) + t(B[j].nnz);
+    rp_tiles += t(A[j].rows + 1);
+  }
+  const int64_t stacked = ws_rounded(int64_t(sizeof(Part)) * 2 * n_jobs) +
+                          ws_rounded(int64_t(sizeof(Tile)) * (stack_tiles + 1)) +
+                          ws_rounded(int64_t(sizeof(Tile)) * (value_tiles + 1)) +
+                          ws_rounded(int64_t(sizeof(Tile)) * (rp_tiles + 1)) + ws_rounded(8 * (rows + 1)) +
+                          ws_rounded(4 * a_nnz) + ws_rounded(vb * a_nnz) + ws_rounded(4 * rows) +
+                          ws_rounded(8 * (inner + 1)) + ws_rounded(4 * b_nnz) + ws_rounded(vb * b_nnz) +
+                          ws_rounded(4 * inner) + ws_rounded(4);
+  int64_t plo = 0, phi = 0;
+  plan_bytes_bounds(rows, a_nnz, width, 0, 0, inner, &plo, &phi);
+  *lo = stacked + plo;
+  *hi = stacked + phi;
+}
+
+int64_t batch_output_bytes(const spgemm_batch_t* b) {
+  const int vb = b->prec == SPGEMM_F64 ? 8 : 4;
+  const int64_t nnz = b->plan->nnz_c > 0 ? b->plan->nnz_c : 1;
+  return ws_rounded(4 * nnz) + ws_rounded(vb * nnz) + ws_rounded(8 * (b->rows + b->n_jobs));
+}
+
+int64_t batch_device_bytes(const spgemm_batch_t* b) {
+  return b->ws.total + (b->plan ? b->plan->ws.total : 0);
+}
+
+int64_t batch_needed_bytes(const spgemm_batch_t* b) {
+  return batch_device_bytes(b) + numeric_extra_bytes(b->plan) + batch_output_bytes(b);
+}
+
+int64_t batch_nnz(const spgemm_batch_t* b) { return b->plan ? b->plan->nnz_c : 0; }
+
+void batch_set_release_stream(spgemm_batch_t* b, void* stream) {
+  b->ws.stream = stream;
+  if (b->plan) b->plan->ws.stream = stream;
+}
+
+int64_t batch_products(const spgemm_batch_t* b) { return b->plan ? b->plan->total_products : 0; }
+
+int64_t batch_jobs(const spgemm_batch_t* b) { return b->n_jobs; }
+
+spgemm_status batch_execute(spgemm_batch_t* b, void* stream) {
+  spgemm_status st;
+  cudaError_t e;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  spgemm_plan_t* p = b->plan;
+  const int vb = b->prec == SPGEMM_F64 ? 8 : 4;
+  auto get = [&](size_t bytes) { return b->ws.get(bytes); };
+  const int64_t n_jobs = b->n_jobs;
   // outputs, owned by the batch
   const int64_t nnz = p->nnz_c;
   b->c_col = static_cast<int32_t*>(get(sizeof(int32_t) * (nnz > 0 ? nnz : 1)));
   b->c_val = get(static_cast<size_t>(vb) * (nnz > 0 ? nnz : 1));
   b->job_rp = static_cast<int64_t*>(get(sizeof(int64_t) * (b->rows + n_jobs)));
-  if (!b->c_col || !b->c_val || !b->job_rp) {
-    set_error_msg(SPGEMM_ERR_OOM, "device allocation of the batch output failed");
-    return fail(SPGEMM_ERR_OOM);
-  }
+  if (!b->c_col || !b->c_val || !b->job_rp) return set_error_msg(SPGEMM_ERR_OOM, "device allocation of the batch output failed");
   spgemm_csr_out C{b->rows, b->cols, nnz, 1, 0, p->c_off, b->c_col, b->c_val};
-  if ((st = numeric_run(p, &C, s)) != SPGEMM_OK) return fail(st);
+  if ((st = numeric_run(p, &C, s)) != SPGEMM_OK) return st;
   if (!b->rowptr_tiles.empty())
     k_job_rowptr<<<static_cast<unsigned>(b->rowptr_tiles.size()), 256, 0, s>>>(b->d_parts, b->d_rowptr_tiles,
                                                                                   p->c_off, b->job_rp);
-  if ((e = cudaGetLastError()) != cudaSuccess) { cuda_status(e, "launching the batch"); return fail(SPGEMM_ERR_CUDA); }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "launching the batch");
+  return SPGEMM_OK;
+}
+
+}  // namespace spg
+
+extern "C" spgemm_status spgemm_batch(int64_t n_jobs, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                                      spgemm_prec prec, const spgemm_opts* opts, const spgemm_allocator* alloc,
+                                      void* stream, spgemm_batch_t** out) {
+  clear_error_msg();
+  spgemm_batch_t* b = nullptr;
+  spgemm_status st = batch_prepare(n_jobs, A, B, prec, opts, alloc, stream, &b);
+  if (st != SPGEMM_OK) return st;
+  if ((st = batch_execute(b, stream)) != SPGEMM_OK) {
+    const std::string msg = spgemm_last_error();
+    cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    spgemm_batch_destroy(b);
+    set_error_msg(st, "%s", msg.c_str());
+    return st;
+  }
   *out = b;
   return SPGEMM_OK;
 }

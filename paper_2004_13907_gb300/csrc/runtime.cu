@@ -213,6 +213,33 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
   return SPGEMM_OK;
 }
 
+void plan_bytes_bounds(int64_t m, int64_t a_nnz, int64_t width, int a_rowptr32, int b_rowptr32, int64_t b_rows,
+                       int64_t* lo, int64_t* hi) {
+  const int64_t ntiles = (m + kTileRows - 1) / kTileRows;
+  int64_t fixed = ws_rounded(sizeof(Summary)) + ws_rounded(16 * 4) + ws_rounded(8 * m) + 3 * ws_rounded(4 * m) +
+                  ws_rounded(8 * (m + 1));
+  if (a_rowptr32) fixed += ws_rounded(8 * (m + 1));
+  if (b_rowptr32) fixed += ws_rounded(8 * (b_rows + 1));
+  const int64_t tiles = ws_rounded(4 * ntiles * kMaxClasses) + 3 * ws_rounded(8 * ntiles);
+  const int64_t nblocks = (width + kBlockCols - 1) / kBlockCols;
+  const int64_t window = ws_rounded(2 * m * nblocks) + ws_rounded(4 * m) + ws_rounded(4 * a_nnz);
+  *lo = fixed;
+  *hi = fixed + tiles + window;
+}
+
+int64_t numeric_extra_bytes(const spgemm_plan_s* p) {
+  const int64_t m = p->A.rows;
+  if (m <= 0) return 0;
+  int64_t extra = 0;
+  if (p->prec == SPGEMM_F32_COMPENSATED && !p->rerun_flag) extra += 2 * ws_rounded(4 * m);
+  const int64_t nwin = p->num_off[kNumWin3 + 1] - p->num_off[kNumWin0];
+  if (nwin > 0 && !p->split_tried) {
+    const int64_t bytes = split_table_bytes(p->B.rows, p->nblocks);
+    if (bytes <= (int64_t(p->opts.window_split_max_mb) << 20)) extra += ws_rounded(bytes);
+  }
+  return extra;
+}
+
 spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
   spgemm_status st = SPGEMM_OK;
   const int64_t m = p->A.rows;

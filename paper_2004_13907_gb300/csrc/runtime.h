@@ -90,6 +90,16 @@ T* ws_alloc(spgemm_plan_s* p, int64_t count, spgemm_status* st);
 spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s);
 spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s);
 spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s);
+// Device bytes the numeric pass of a plan past its symbolic pass will still allocate (FP32 rerun
+// lists, the split table of B), rounded as the workspace rounds them.
+int64_t numeric_extra_bytes(const spgemm_plan_s* p);
+// Bounds on the workspace bytes spgemm_plan and spgemm_symbolic allocate for an m-row A with
+// a_nnz entries and output rows `width` columns wide: *lo is always allocated, *hi is never
+// exceeded.
+void plan_bytes_bounds(int64_t m, int64_t a_nnz, int64_t width, int a_rowptr32, int b_rowptr32, int64_t b_rows,
+                       int64_t* lo, int64_t* hi);
+// Bytes the workspace takes for a request of `bytes`.
+inline int64_t ws_rounded(int64_t bytes) { return ((bytes <= 0 ? 16 : bytes) + 255) & ~int64_t(255); }
 void stage_begin(spgemm_plan_s* p, int stage, cudaStream_t s);
 void stage_end(spgemm_plan_s* p, int stage, int launches, cudaStream_t s);
 void destroy_events(spgemm_plan_s* p);

@@ -53,16 +53,20 @@ def test_struct_layout_matches_c(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "spgemm.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(spgemm_csr_in),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(spgemm_csr_in),"
         " sizeof(spgemm_csr_out), sizeof(spgemm_allocator), sizeof(spgemm_opts),"
         " sizeof(spgemm_plan_info), offsetof(spgemm_opts, rowptr32_limit),"
-        " offsetof(spgemm_plan_info, workspace_bytes)); return 0;}\n")
+        " offsetof(spgemm_plan_info, workspace_bytes), sizeof(spgemm_server_cfg),"
+        " offsetof(spgemm_server_cfg, opts), sizeof(spgemm_job_info), sizeof(spgemm_server_stats),"
+        " offsetof(spgemm_server_stats, latency_p50_ms)); return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(_native.CsrIn), ctypes.sizeof(_native.CsrOut), ctypes.sizeof(_native.Allocator),
             ctypes.sizeof(_native.Opts), ctypes.sizeof(_native.PlanInfo),
-            _native.Opts.rowptr32_limit.offset, _native.PlanInfo.workspace_bytes.offset]
+            _native.Opts.rowptr32_limit.offset, _native.PlanInfo.workspace_bytes.offset,
+            ctypes.sizeof(_native.ServerCfg), _native.ServerCfg.opts.offset, ctypes.sizeof(_native.JobInfo),
+            ctypes.sizeof(_native.ServerStats), _native.ServerStats.latency_p50_ms.offset]
     assert got == want
 
 
@@ -93,3 +97,24 @@ def test_python_binding_fails_loudly_without_library(tmp_path):
     from paper_2004_13907_gb300 import _native
     with pytest.raises(ImportError):
         _native.load(str(tmp_path / "missing.so"))
+
+
+def test_server_config_checks_on_host(lib):
+    """Server defaults, and configurations refused before any device call."""
+    from paper_2004_13907_gb300 import _native
+    cfg = _native.ServerCfg()
+    assert lib.spgemm_server_cfg_default(ctypes.byref(cfg)) == 0
+    assert cfg.mem_cap_bytes == 32 << 30 and cfg.num_streams == 2 and cfg.prec == 0
+    assert cfg.opts.validate == 1 and cfg.opts.window_hash_fill == 4096
+    h = ctypes.c_void_p()
+    for field, bad in [("num_streams", 0), ("num_streams", 9), ("mem_cap_bytes", 0), ("max_batch_jobs", 0),
+                       ("prec", 7), ("batch_window_us", -1)]:
+        c = _native.ServerCfg()
+        lib.spgemm_server_cfg_default(ctypes.byref(c))
+        setattr(c, field, bad)
+        assert lib.spgemm_server_create(ctypes.byref(c), ctypes.byref(h)) == 1, field
+        assert h.value is None
+    job = ctypes.c_int64()
+    a = _native.CsrIn(4, 5, 0, 0, 0, 1, 0, 0)
+    assert lib.spgemm_server_submit(None, ctypes.byref(a), ctypes.byref(a), ctypes.byref(job)) == 1
+    assert lib.spgemm_server_destroy(None) == 0
