@@ -385,6 +385,176 @@ def run_batch(args):
     }, 0
 
 
+def _serve_job(kind: str, param: int):
+    """Inputs of one served request (host CSR): A_i, B_i of the batch distribution, or a 3D
+    7-point Laplacian A with B = A (None)."""
+    if kind == "lap3d":
+        return synth.laplacian3d(param), None
+    return synth.batch_job(param, 0)
+
+
+def _serve_inputs(reqs, procs: int):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        return pool.starmap(_serve_job, [(r.kind, r.param) for r in reqs], chunksize=2)
+
+
+def _pct(v, q):
+    """Nearest-rank percentile (the server's own definition)."""
+    v = sorted(v)
+    if not v:
+        return 0.0
+    k = int(np.ceil(q * len(v)))
+    return float(v[max(k, 1) - 1])
+
+
+def run_serve(args):
+    """Serving: a Poisson stream of requests (90% jobs of the batch distribution, 10% A*A for a
+    3D 7-point Laplacian with g in 64..128), FP64, 32 GB admission cap. The server (continuous
+    batching) against the plain per-product launch (one product at a time, in arrival order):
+    saturated throughput with every request queued at once, and p50/p99 latency (arrival to
+    completion) at a Poisson rate of 0.8 x the plain path's saturated job throughput."""
+    import threading
+    import torch
+    import paper_2004_13907_gb300 as sp
+    R = args.serve_requests
+    reqs = synth.serve_stream(R, 1.0, seed=0)
+    t_gen = time.perf_counter()
+    host = _serve_inputs(reqs, max(1, min(16, os.cpu_count() or 1)))
+    t_gen = time.perf_counter() - t_gen
+    dev = []
+    for A, B in host:
+        dA = sp.DeviceCSR.from_host(A, "cuda")
+        dev.append((dA, dA if B is None else sp.DeviceCSR.from_host(B, "cuda")))
+    torch.cuda.synchronize()
+    in_bytes = sum(int(dA.col.numel()) * 12 + int(dB.col.numel()) * 12 for dA, dB in dev)
+    del host
+    cap = 32 << 30
+
+    def server(**kw):
+        return sp.Server(mem_cap_bytes=cap, batch_window_us=args.serve_window_us, num_streams=2, **kw)
+
+    def drain(srv, ids):
+        """Consumes results in submission order (each is released once it is done)."""
+        states = []
+        for i in ids:
+            try:
+                states.append(srv.wait(i, timeout=600)["state"])
+            except sp.SpgemmError as e:
+                if e.name not in ("REJECTED", "OOM"):
+                    raise
+                states.append("rejected")
+            srv.release(i)
+        return states
+
+    # warm-up: the plain path and the server on the first requests
+    for _ in range(args.warmup):
+        for dA, dB in dev[:16]:
+            sp.multiply(dA, dB)
+        with server() as srv:
+            drain(srv, [srv.submit(dA, dB, sync=False) for dA, dB in dev[:64]])
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    # saturated: every request queued at once
+    sat = []
+    rejected = set()
+    for _ in range(args.steps):
+        with server() as srv:
+            ids = [srv.submit(dA, dB, sync=False) for dA, dB in dev]
+            states = drain(srv, ids)
+            st = srv.stats()
+        rejected = {k for k, s_ in enumerate(states) if s_ != "done"}
+        sat.append(st)
+    products = sat[-1]["products"]
+    ms_srv = float(np.mean([x["elapsed_s"] for x in sat])) * 1e3
+    accepted = [k for k in range(R) if k not in rejected]
+    plain_ms = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in accepted:
+            C = sp.multiply(*dev[k])
+            del C
+        torch.cuda.synchronize()
+        plain_ms.append((time.perf_counter() - t0) * 1e3)
+    ms_plain = float(np.mean(plain_ms))
+    lam = 0.8 * len(accepted) / (ms_plain * 1e-3)
+    arrival = np.array([r.arrival_s for r in reqs]) / lam
+    # plain path at rate lam: each request runs when it has arrived and the previous one is done
+    lat_plain = []
+    t0 = time.perf_counter()
+    for k in accepted:
+        wait = t0 + arrival[k] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        C = sp.multiply(*dev[k])
+        torch.cuda.synchronize()
+        lat_plain.append((time.perf_counter() - t0 - arrival[k]) * 1e3)
+        del C
+    # server at rate lam: a submitter thread follows the arrival times, this thread consumes
+    with server() as srv:
+        ids = [None] * R
+        lag = [0.0]
+        ready = threading.Event()
+
+        def submitter():
+            t0s = time.perf_counter()
+            ready.set()
+            for k in range(R):
+                wait = t0s + arrival[k] - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                lag[0] = max(lag[0], time.perf_counter() - t0s - arrival[k])
+                ids[k] = srv.submit(*dev[k], sync=False)
+        th = threading.Thread(target=submitter)
+        th.start()
+        ready.wait()
+        for k in range(R):
+            while ids[k] is None:
+                time.sleep(1e-4)
+            try:
+                srv.wait(ids[k], timeout=600)
+            except sp.SpgemmError as e:
+                if e.name not in ("REJECTED", "OOM"):
+                    raise
+            srv.release(ids[k])
+        th.join()
+        live = srv.stats()
+    clocks = sampler.stop()
+    gf = lambda p, ms: round(2.0 * p / (ms * 1e-3) / 1e9, 3)
+    n_lap = sum(1 for r in reqs if r.kind == "lap3d")
+    return {
+        "metric": METRIC, "value": gf(products, ms_srv), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_srv, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serve",
+                   "description": f"{R} requests of a Poisson stream (seed 0): {R - n_lap} jobs A_i*B_i of the "
+                                  f"batch distribution (n log-uniform [100, 50000], density log-uniform "
+                                  f"[1e-4, 1e-2]), {n_lap} A*A for 3D 7-point Laplacians with g in 64..128; "
+                                  f"FP64; 32 GB admission cap; inputs resident on the device",
+                   "requests": R, "input_bytes": in_bytes, "products_per_step": products,
+                   "l2": "inputs larger than L2", "parallelism": "one GPU, continuous batching, 2 streams",
+                   "batch_window_us": args.serve_window_us, "input_generation_s": round(t_gen, 1)},
+        "saturated": {"server_ms": round(ms_srv, 3), "plain_ms": round(ms_plain, 3),
+                      "plain_value": gf(products, ms_plain), "speedup": round(ms_plain / ms_srv, 3),
+                      "server_jobs_per_s": round(sat[-1]["jobs_per_s"], 1),
+                      "mean_batch_jobs": round(sat[-1]["mean_batch_jobs"], 2),
+                      "rejected_over_cap": len(rejected), "splits": sat[-1]["splits"],
+                      "bytes_peak": sat[-1]["bytes_peak"]},
+        "latency": {"rate_per_s": round(lam, 2), "what": "arrival to completion, ms, at 0.8 x the plain "
+                                                          "path's saturated job rate",
+                    "server_p50_ms": round(live["latency_p50_ms"], 3), "server_p99_ms": round(live["latency_p99_ms"], 3),
+                    "server_max_ms": round(live["latency_max_ms"], 3),
+                    "plain_p50_ms": round(_pct(lat_plain, 0.5), 3), "plain_p99_ms": round(_pct(lat_plain, 0.99), 3),
+                    "plain_max_ms": round(max(lat_plain), 3),
+                    "server_mean_batch_jobs": round(live["mean_batch_jobs"], 2),
+                    "submit_lag_max_ms": round(lag[0] * 1e3, 3)},
+        "gpu_launches": int(sat[-1]["kernel_launches"]), "clocks": clocks,
+    }, 0
+
+
 def _pinned(n: int, dtype, torch):
     """Page-locked host array of exactly n elements (numpy memory registered with CUDA)."""
     a = np.empty(max(n, 1), dtype=dtype)
@@ -539,12 +709,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lap2d1024+rmat20",
-                    choices=sorted(WORKLOADS) + ["batch_small", "batch_mid"])
+                    choices=sorted(WORKLOADS) + ["batch_small", "batch_mid", "serve"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-products-per-step", type=float, default=2e8)
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-window-us", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         sys.stderr.write("note: fewer than 3 warm-up steps\n")
@@ -552,6 +724,8 @@ def main():
         line, rank = run_reference(args)
     elif args.workload.startswith("batch"):
         line, rank = run_batch(args)
+    elif args.workload == "serve":
+        line, rank = run_serve(args)
     else:
         line, rank = run_ours(args)
     if rank == 0 and line is not None:

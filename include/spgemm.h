@@ -300,7 +300,7 @@ typedef struct {
   int64_t mem_cap_bytes;       /* device bytes the server's batches and results may hold
                                   (default 32 GiB) */
   int64_t max_batch_entries;   /* a batch stops growing once its jobs' nnz(A)+nnz(B) reach
-                                  this (default 2^26); a bigger job runs alone */
+                                  this (default 2^24); a bigger job runs alone */
   int32_t max_batch_jobs;      /* jobs per batch at most (default 1024) */
   int32_t batch_window_us;     /* fill window after the oldest queued job (default 200) */
   int32_t num_streams;         /* batches in flight, 1..8 (default 2) */
@@ -346,7 +346,8 @@ typedef struct {
   double elapsed_s;            /* first submit to last completion */
   double jobs_per_s;           /* completed jobs / elapsed_s */
   double products_per_s;       /* products / elapsed_s */
-  int64_t reserved_[8];
+  int64_t kernel_launches;     /* kernels launched by completed batches */
+  int64_t reserved_[7];
 } spgemm_server_stats;
 
 spgemm_status spgemm_server_cfg_default(spgemm_server_cfg* cfg);

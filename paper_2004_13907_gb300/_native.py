@@ -92,7 +92,8 @@ class ServerStats(ctypes.Structure):
                                      "mem_cap_bytes")] + \
                [(n, ctypes.c_double) for n in ("latency_p50_ms", "latency_p99_ms", "latency_max_ms",
                                                "latency_mean_ms", "mean_batch_jobs", "elapsed_s", "jobs_per_s",
-                                               "products_per_s")] + [("reserved_", c_i64 * 8)]
+                                               "products_per_s")] + \
+               [("kernel_launches", c_i64), ("reserved_", c_i64 * 7)]
 
 
 # name -> (restype, argtypes); every symbol include/spgemm.h declares

@@ -36,6 +36,8 @@ struct Part {
   int64_t col_limit;      // the job's own column count (indices must be below it)
   int32_t base;           // column base of the job's rows in the stacked product
   int32_t idx64;
+  int32_t width;          // A side: the job's column count of C (the width of its rows)
+  int32_t pad_;
 };
 
 struct Tile {
@@ -47,7 +49,7 @@ struct Tile {
 __global__ void __launch_bounds__(256) k_stack(const Part* __restrict__ parts, const Tile* __restrict__ tiles,
                                                int64_t* __restrict__ rp_out, int32_t* __restrict__ col_out,
                                                unsigned char* __restrict__ val_out, int32_t* __restrict__ base_out,
-                                               int val_bytes, uint32_t* err) {
+                                               int32_t* __restrict__ width_out, int val_bytes, uint32_t* err) {
   const Tile t = tiles[blockIdx.x];
   const Part pt = parts[t.part];
   if (t.kind == 0) {
@@ -56,6 +58,7 @@ __global__ void __launch_bounds__(256) k_stack(const Part* __restrict__ parts, c
       const int64_t v = pt.idx64 ? static_cast<const int64_t*>(pt.rp)[r] : static_cast<const int32_t*>(pt.rp)[r];
       rp_out[pt.row0 + r] = v + pt.nnz0;
       base_out[pt.row0 + r] = pt.base;
+      if (width_out) width_out[pt.row0 + r] = pt.width;
     }
   } else {
     const int64_t end = t.start + kTile < pt.nnz ? t.start + kTile : pt.nnz;
@@ -112,6 +115,7 @@ struct spgemm_batch_s {
   int32_t* a_col = nullptr;
   void* a_val = nullptr;
   int32_t* abase = nullptr;
+  int32_t* awidth = nullptr;
   int64_t* b_rp = nullptr;
   int32_t* b_col = nullptr;
   void* b_val = nullptr;
@@ -125,6 +129,7 @@ struct spgemm_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t capture_stream = nullptr;   // private stream the graph is captured on
+  int64_t launches = 0;               // stacking and row-pointer kernels (the plan counts its own)
 };
 
 namespace spg {
@@ -169,10 +174,10 @@ spgemm_status batch_prepare(int64_t n_jobs, const spgemm_csr_in* A, const spgemm
     }
     Part& pa = b->parts[j];
     pa = Part{A[j].row_ptr, A[j].col, A[j].val, A[j].rows, A[j].nnz, b->rows, b->a_nnz, b->inner, A[j].cols,
-              static_cast<int32_t>(b->cols), A[j].idx64_rowptr};
+              static_cast<int32_t>(b->cols), A[j].idx64_rowptr, static_cast<int32_t>(B[j].cols), 0};
     Part& pb = b->parts[n_jobs + j];
     pb = Part{B[j].row_ptr, B[j].col, B[j].val, B[j].rows, B[j].nnz, b->inner, b->b_nnz, b->cols, B[j].cols,
-              static_cast<int32_t>(b->cols), B[j].idx64_rowptr};
+              static_cast<int32_t>(b->cols), B[j].idx64_rowptr, static_cast<int32_t>(B[j].cols), 0};
     b->rows += A[j].rows;
     b->inner += B[j].rows;
     b->cols += B[j].cols;
@@ -207,13 +212,14 @@ spgemm_status batch_prepare(int64_t n_jobs, const spgemm_csr_in* A, const spgemm
   b->a_col = static_cast<int32_t*>(get(sizeof(int32_t) * b->a_nnz));
   b->a_val = get(static_cast<size_t>(vb) * b->a_nnz);
   b->abase = static_cast<int32_t*>(get(sizeof(int32_t) * b->rows));
+  b->awidth = static_cast<int32_t*>(get(sizeof(int32_t) * b->rows));
   b->b_rp = static_cast<int64_t*>(get(sizeof(int64_t) * (b->inner + 1)));
   b->b_col = static_cast<int32_t*>(get(sizeof(int32_t) * b->b_nnz));
   b->b_val = get(static_cast<size_t>(vb) * b->b_nnz);
   b->bbase = static_cast<int32_t*>(get(sizeof(int32_t) * b->inner));
   b->err = static_cast<uint32_t*>(get(sizeof(uint32_t)));
   if (!b->d_parts || !b->d_stack_tiles || !b->d_value_tiles || !b->d_rowptr_tiles || !b->a_rp || !b->a_col ||
-      !b->a_val || !b->abase || !b->b_rp || !b->b_col || !b->b_val || !b->bbase || !b->err) {
+      !b->a_val || !b->abase || !b->awidth || !b->b_rp || !b->b_col || !b->b_val || !b->bbase || !b->err) {
     set_error_msg(SPGEMM_ERR_OOM, "device allocation of the stacked batch failed");
     return fail(SPGEMM_ERR_OOM);
   }
@@ -237,10 +243,13 @@ spgemm_status batch_prepare(int64_t n_jobs, const spgemm_csr_in* A, const spgemm
     const int64_t na = b->stack_a, nb = static_cast<int64_t>(b->stack_tiles.size()) - b->stack_a;
     if (na > 0)
       k_stack<<<static_cast<unsigned>(na), 256, 0, s>>>(b->d_parts, b->d_stack_tiles, b->a_rp, b->a_col,
-                                                        static_cast<unsigned char*>(b->a_val), b->abase, vb, b->err);
+                                                        static_cast<unsigned char*>(b->a_val), b->abase, b->awidth, vb,
+                                                        b->err);
     if (nb > 0)
       k_stack<<<static_cast<unsigned>(nb), 256, 0, s>>>(b->d_parts, b->d_stack_tiles + na, b->b_rp, b->b_col,
-                                                        static_cast<unsigned char*>(b->b_val), b->bbase, vb, b->err);
+                                                        static_cast<unsigned char*>(b->b_val), b->bbase, nullptr, vb,
+                                                        b->err);
+    b->launches += (na > 0) + (nb > 0);
   }
   uint32_t herr = 0;
   e = cudaMemcpyAsync(&herr, b->err, sizeof(herr), cudaMemcpyDeviceToHost, s);
@@ -261,6 +270,7 @@ spgemm_status batch_prepare(int64_t n_jobs, const spgemm_csr_in* A, const spgemm
   p->ws.stream = stream;
   if (alloc) { p->ws.alloc = *alloc; p->ws.has_alloc = true; }
   p->abase = b->abase;
+  p->awidth = b->awidth;
   p->bbase = b->bbase;
   p->width = width > 0 ? width : 1;
   b->plan = p;
@@ -299,7 +309,7 @@ void batch_prepare_bounds(int64_t n_jobs, const spgemm_csr_in* A, const spgemm_c
                           ws_rounded(int64_t(sizeof(Tile)) * (stack_tiles + 1)) +
                           ws_rounded(int64_t(sizeof(Tile)) * (value_tiles + 1)) +
                           ws_rounded(int64_t(sizeof(Tile)) * (rp_tiles + 1)) + ws_rounded(8 * (rows + 1)) +
-                          ws_rounded(4 * a_nnz) + ws_rounded(vb * a_nnz) + ws_rounded(4 * rows) +
+                          ws_rounded(4 * a_nnz) + ws_rounded(vb * a_nnz) + 2 * ws_rounded(4 * rows) +
                           ws_rounded(8 * (inner + 1)) + ws_rounded(4 * b_nnz) + ws_rounded(vb * b_nnz) +
                           ws_rounded(4 * inner) + ws_rounded(4);
   int64_t plo = 0, phi = 0;
@@ -349,9 +359,11 @@ spgemm_status batch_execute(spgemm_batch_t* b, void* stream) {
   if (!b->c_col || !b->c_val || !b->job_rp) return set_error_msg(SPGEMM_ERR_OOM, "device allocation of the batch output failed");
   spgemm_csr_out C{b->rows, b->cols, nnz, 1, 0, p->c_off, b->c_col, b->c_val};
   if ((st = numeric_run(p, &C, s)) != SPGEMM_OK) return st;
-  if (!b->rowptr_tiles.empty())
+  if (!b->rowptr_tiles.empty()) {
     k_job_rowptr<<<static_cast<unsigned>(b->rowptr_tiles.size()), 256, 0, s>>>(b->d_parts, b->d_rowptr_tiles,
                                                                                   p->c_off, b->job_rp);
+    ++b->launches;
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "launching the batch");
   return SPGEMM_OK;
 }
@@ -395,7 +407,9 @@ extern "C" spgemm_status spgemm_batch_result(const spgemm_batch_t* b, int64_t jo
 extern "C" spgemm_status spgemm_batch_get_info(const spgemm_batch_t* b, spgemm_plan_info* info) {
   clear_error_msg();
   if (!b || !info) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "NULL argument");
-  return spgemm_plan_get_info(b->plan, info);
+  const spgemm_status st = spgemm_plan_get_info(b->plan, info);
+  info->kernel_launches += b->launches;
+  return st;
 }
 
 extern "C" spgemm_status spgemm_batch_check(spgemm_batch_t* b, void* stream) {
@@ -431,10 +445,12 @@ extern "C" spgemm_status spgemm_batch_replay(spgemm_batch_t* b, void* stream) {
     const int64_t na = b->value_a, nb = static_cast<int64_t>(b->value_tiles.size()) - b->value_a;
     if (na > 0)
       k_stack<<<static_cast<unsigned>(na), 256, 0, cs>>>(b->d_parts, b->d_value_tiles, b->a_rp, b->a_col,
-                                                         static_cast<unsigned char*>(b->a_val), b->abase, vb, b->err);
+                                                         static_cast<unsigned char*>(b->a_val), b->abase, nullptr, vb,
+                                                         b->err);
     if (nb > 0)
       k_stack<<<static_cast<unsigned>(nb), 256, 0, cs>>>(b->d_parts, b->d_value_tiles + na, b->b_rp, b->b_col,
-                                                         static_cast<unsigned char*>(b->b_val), b->bbase, vb, b->err);
+                                                         static_cast<unsigned char*>(b->b_val), b->bbase, nullptr, vb,
+                                                         b->err);
     spgemm_csr_out C{b->rows, b->cols, p->nnz_c, 1, 0, p->c_off, b->c_col, b->c_val};
     spgemm_status st = numeric_run(p, &C, cs);
     cudaGraph_t g = nullptr;

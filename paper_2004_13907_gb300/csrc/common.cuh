@@ -59,7 +59,15 @@ struct ClassParams {
   int32_t block_max;      // block tables take <= block_max; larger rows are windowed
   int32_t force_window;
   int32_t window_all;     // every row that is not tiny takes the windowed path (FP32-compensated)
+  const int32_t* rwidth;  // per-row column count of C (device, NULL: every row has n columns)
 };
+
+// The column count of row `row` of C: its own width in a stacked batch, else n.
+__device__ inline ClassParams row_params(const ClassParams& cp, int64_t row) {
+  ClassParams c = cp;
+  if (cp.rwidth) c.n = cp.rwidth[row];
+  return c;
+}
 
 __host__ __device__ inline int win_subclass(int64_t P) {
   return P >= (int64_t(1) << 22) ? 0 : P >= (int64_t(1) << 20) ? 1 : P >= (int64_t(1) << 17) ? 2 : 3;

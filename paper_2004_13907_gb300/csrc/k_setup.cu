@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_count(DevCsr A, DevCsr B, ClassParams c
     int cls = kSymZero;
     if (valid) {
       const int32_t na32 = na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na);
-      cls = sym_class(p, na32, cp);
+      cls = sym_class(p, na32, row_params(cp, row));
       P[row] = p;
       if (cls == kSymZero) nnz_row[row] = 0;
       my_sum += static_cast<unsigned long long>(p);
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) k_scatter_sym(DevCsr A, ClassParams cp, c
     int cls = 0;
     if (valid) {
       const int64_t na = A.rp[row + 1] - A.rp[row];
-      cls = sym_class(P[row], na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na), cp);
+      cls = sym_class(P[row], na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na), row_params(cp, row));
     }
     const int32_t pos = aggregated_slot(base, cls, valid);
     if (valid) perm[pos] = static_cast<int32_t>(row);

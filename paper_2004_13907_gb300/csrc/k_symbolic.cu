@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
                                                                uint16_t* __restrict__ blockcnt,
                                                                int64_t nblocks, int32_t* cursor,
                                                                const int32_t* __restrict__ abase,
-                                                               int64_t width, uint32_t* err) {
+                                                               const int32_t* __restrict__ awidth,
+                                                               int64_t width_all, uint32_t* err) {
   extern __shared__ uint32_t bm[];  // kSymWinBits / 32 words
   __shared__ int32_t s_excl[kSymWinThreads];
   __shared__ int64_t s_bs[kSymWinThreads];
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
     const int64_t a0 = A.rp[i];
     const int64_t na = A.rp[i + 1] - a0;
     const int64_t cb = abase ? abase[i] : 0;   // the row's columns are [cb, cb + width)
+    const int64_t width = awidth ? awidth[i] : width_all;
     uint16_t* cnts = blockcnt + idx * nblocks;
     for (int64_t r0 = 0; r0 < width; r0 += kSymWinBits) {
       const int64_t w0 = cb + r0;
@@ -262,8 +264,8 @@ int launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t*
 
 int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                        int32_t* counter, int32_t* nnz_row, int32_t* win_slot, uint16_t* blockcnt,
-                       int64_t nblocks, int32_t* cursor, const int32_t* abase, int64_t width,
-                       int num_sms, uint32_t* err, cudaStream_t s) {
+                       int64_t nblocks, int32_t* cursor, const int32_t* abase, const int32_t* awidth,
+                       int64_t width, int num_sms, uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   const size_t sm = size_t(kSymWinBits / 32) * 4;
   cudaFuncSetAttribute(k_sym_window, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
@@ -271,7 +273,7 @@ int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int
   const int64_t g = count < num_sms ? count : num_sms;
   k_sym_window<<<static_cast<unsigned>(g), kSymWinThreads, sm, s>>>(A, B, perm, count, counter, nnz_row,
                                                                  win_slot, blockcnt, nblocks, cursor,
-                                                                 abase, width, err);
+                                                                 abase, awidth, width, err);
   return 1;
 }
 

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     const uint16_t* __restrict__ blockcnt, int64_t nblocks, int64_t nslots,
     const int32_t* __restrict__ split, int32_t merge_cap, int32_t* __restrict__ ccol,
     void* __restrict__ cval_, int32_t* __restrict__ row_flag, const int32_t* __restrict__ abase,
-    int64_t width, uint32_t* err) {
+    const int32_t* __restrict__ awidth, int64_t width_all, uint32_t* err) {
   constexpr int kSmemVals = WinGeom<Mode>::kSmemVals;
   extern __shared__ __align__(16) unsigned char win_smem[];
   double* vals = reinterpret_cast<double*>(win_smem);        // kModeF64, kModeF32R
@@ -254,9 +254,11 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     const int64_t a0 = A.rp[i];
     const int64_t na = A.rp[i + 1] - a0;
     const int64_t cb = abase ? abase[i] : 0;   // the row's columns are [cb, cb + width)
+    const int64_t width = awidth ? awidth[i] : width_all;
+    const int64_t row_blocks = (width + kBlockCols - 1) / kBlockCols;   // counted by the symbolic pass
     const bool resident = na <= kNumThreads;
     if (cnt_cached)
-      for (int64_t b = threadIdx.x; b < nblocks; b += kNumThreads) s_cnt[b] = gcnt[b];
+      for (int64_t b = threadIdx.x; b < row_blocks; b += kNumThreads) s_cnt[b] = gcnt[b];
     if (resident && threadIdx.x < na) {
       const int32_t k = A.col[a0 + threadIdx.x];
       e_k[threadIdx.x] = k;
@@ -274,12 +276,12 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
         int nw = 0;
         int64_t b = next_b;
         while (nw < kMaxWin) {
-          while (b < nblocks && cnts[b] == 0) ++b;
-          if (b >= nblocks) break;
+          while (b < row_blocks && cnts[b] == 0) ++b;
+          if (b >= row_blocks) break;
           int64_t e = b;
           int32_t sum = 0;
           do { sum += cnts[e]; ++e; }
-          while (e < nblocks && e - b < kSpanBlocks && sum + cnts[e] <= merge_cap);
+          while (e < row_blocks && e - b < kSpanBlocks && sum + cnts[e] <= merge_cap);
           w_b0[nw] = static_cast<int32_t>(b);
           w_b1[nw] = static_cast<int32_t>(e);
           w_cnt[nw] = sum;
@@ -491,7 +493,8 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
                       int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
                       int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag,
-                      const int32_t* abase, int64_t width, int num_sms, uint32_t* err, cudaStream_t s) {
+                      const int32_t* abase, const int32_t* awidth, int64_t width, int num_sms, uint32_t* err,
+                      cudaStream_t s) {
   if (count <= 0) return 0;
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   auto go = [&](auto kernel, int smem, int per_sm) {
@@ -499,7 +502,7 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
     const int64_t g = count < int64_t(per_sm) * num_sms ? count : int64_t(per_sm) * num_sms;
     kernel<<<static_cast<unsigned>(g), kNumThreads, smem, s>>>(A, B, perm, count, counter, c_off, win_slot,
                                                                blockcnt, nblocks, nslots, split, merge_cap,
-                                                               ccol, cval, row_flag, abase, width, err);
+                                                               ccol, cval, row_flag, abase, awidth, width, err);
   };
   if (mode == kModeF32C) go(k_num_window<kModeF32C>, WinGeom<kModeF32C>::kSmemBytes, 1);
   else if (mode == kModeF32R) go(k_num_window<kModeF32R>, WinGeom<kModeF32R>::kSmemBytes, 2);

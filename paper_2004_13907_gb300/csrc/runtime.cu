@@ -104,6 +104,7 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   const spgemm_opts& o = p->opts;
   if (p->width <= 0) p->width = n;
   p->cp.n = p->width;
+  p->cp.rwidth = p->awidth;
   p->cp.tiny_max = clampi(o.tiny_max, 0, 32);
   p->cp.warp_max = clampi(o.warp_max, 0, 1024);
   p->cp.block_max = clampi(o.block_max, p->cp.warp_max > 32 ? p->cp.warp_max : 32, 4096);
@@ -178,7 +179,7 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
     stage_begin(p, SPGEMM_STAGE_SYM_WINDOW, s);
     nl = launch_sym_window(p->A, p->B, seg(kSymWin0), p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0],
                            p->counters + 0, p->nnz_row, p->win_slot, p->blockcnt, p->nblocks, p->cursor,
-                           p->abase, p->width, p->num_sms, err, s);
+                           p->abase, p->awidth, p->width, p->num_sms, err, s);
     stage_end(p, SPGEMM_STAGE_SYM_WINDOW, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_BLOCK, s);
     nl = launch_sym_block(13, p->A, p->B, seg(kSymBlock), cnt(kSymBlock), p->nnz_row, err, s);
@@ -278,7 +279,7 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
     }
     nl += launch_num_window(mode, p->A, p->B, seg(kNumWin0), nwin, p->counters + 1, p->c_off, p->win_slot,
                             p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
-                            p->rerun_flag, p->abase, p->width, p->num_sms, err, s);
+                            p->rerun_flag, p->abase, p->awidth, p->width, p->num_sms, err, s);
     stage_end(p, SPGEMM_STAGE_NUM_WINDOW, nl, s);
     if (!f32c) {
       double* cval = static_cast<double*>(C->val);
@@ -313,7 +314,7 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       if (e != cudaSuccess) return cuda_status(e, "reading the FP64 rerun counts");
       nl += launch_num_window(kModeF32R, p->A, p->B, list_w, hc[0], p->counters + 2, p->c_off, p->win_slot,
                               p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
-                              nullptr, p->abase, p->width, p->num_sms, err, s);
+                              nullptr, p->abase, p->awidth, p->width, p->num_sms, err, s);
       nl += launch_num_tiny(kModeF32R, p->A, p->B, list_t, hc[1], p->c_off, C->col, C->val, nullptr, p->abase, err,
                             s);
       stage_end(p, SPGEMM_STAGE_NUM_RERUN, nl, s);

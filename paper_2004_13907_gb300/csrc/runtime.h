@@ -55,10 +55,11 @@ struct spgemm_plan_s {
   int64_t nblocks = 0;
   int32_t* cursor = nullptr;
   int32_t* split = nullptr;          // column-block split table of B (windowed numeric rows)
-  // Column space of the rows: [abase[i], abase[i] + width) for row i of A (and B's rows start at
-  // bbase[k]); a single product has no bases and width = n. A batch run as one block-diagonal
-  // product gives every row the columns of its job.
+  // Column space of the rows: [abase[i], abase[i] + awidth[i]) for row i of A (and B's rows start
+  // at bbase[k]); width is the widest row. A single product has no bases and width = n. A batch
+  // run as one block-diagonal product gives every row the columns of its own job.
   const int32_t* abase = nullptr;
+  const int32_t* awidth = nullptr;
   const int32_t* bbase = nullptr;
   int64_t width = 0;
   bool split_tried = false;

@@ -59,6 +59,7 @@ struct BatchRec {
   int64_t bytes = 0;      // exact bytes charged to the budget
   int64_t live = 0;       // jobs not yet released
   int64_t products = 0;
+  int64_t launches = 0;   // kernels the batch launched
   bool done = false;
 };
 
@@ -89,7 +90,7 @@ struct spgemm_server_s {
   int64_t running = 0;                // jobs in those batches
   // statistics since creation or the last reset
   int64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_rejected = 0;
-  int64_t n_batches = 0, n_splits = 0, n_products = 0, n_nnz = 0, n_batch_jobs = 0;
+  int64_t n_batches = 0, n_splits = 0, n_products = 0, n_nnz = 0, n_batch_jobs = 0, n_launches = 0;
   bool have_first = false;
   Clock::time_point first_submit, last_done;
   std::vector<double> latencies;
@@ -378,6 +379,8 @@ void completer_main(spgemm_server_s* S) {
     const std::string msg = st != SPGEMM_OK ? spgemm_last_error() : "";
     std::vector<spgemm_csr_out> outs(static_cast<size_t>(n));
     for (int64_t k = 0; k < n; ++k) spgemm_batch_result(b, k, &outs[k]);
+    spgemm_plan_info pinfo{};
+    spgemm_batch_get_info(b, &pinfo);
 
     lk.lock();
     const auto now = Clock::now();
@@ -392,6 +395,7 @@ void completer_main(spgemm_server_s* S) {
     --S->inflight;
     ++S->n_batches;
     S->n_products += rec.products;
+    S->n_launches += pinfo.kernel_launches;
     S->n_batch_jobs += n;
     S->last_done = now;
     S->cv_sched.notify_all();
@@ -444,7 +448,7 @@ extern "C" spgemm_status spgemm_server_cfg_default(spgemm_server_cfg* cfg) {
   if (!cfg) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "cfg is NULL");
   *cfg = spgemm_server_cfg{};
   cfg->mem_cap_bytes = int64_t(32) << 30;
-  cfg->max_batch_entries = int64_t(1) << 26;
+  cfg->max_batch_entries = int64_t(1) << 24;
   cfg->max_batch_jobs = 1024;
   cfg->batch_window_us = 200;
   cfg->num_streams = 2;
@@ -634,6 +638,7 @@ extern "C" spgemm_status spgemm_server_get_stats(spgemm_server_t* S, spgemm_serv
     st.bytes_in_use = S->in_use;
     st.bytes_peak = S->peak;
     st.mem_cap_bytes = S->cfg.mem_cap_bytes;
+    st.kernel_launches = S->n_launches;
     st.mean_batch_jobs = S->n_batches ? double(S->n_batch_jobs) / double(S->n_batches) : 0.0;
     if (S->have_first && S->n_batches > 0 && S->last_done > S->first_submit)
       st.elapsed_s = std::chrono::duration<double>(S->last_done - S->first_submit).count();
@@ -665,7 +670,7 @@ extern "C" spgemm_status spgemm_server_reset_stats(spgemm_server_t* S) {
   if (!S) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "server is NULL");
   std::lock_guard<std::mutex> g(S->mu);
   S->n_submitted = S->n_completed = S->n_failed = S->n_rejected = 0;
-  S->n_batches = S->n_splits = S->n_products = S->n_nnz = S->n_batch_jobs = 0;
+  S->n_batches = S->n_splits = S->n_products = S->n_nnz = S->n_batch_jobs = S->n_launches = 0;
   S->have_first = false;
   S->latencies.clear();
   S->peak = S->in_use;

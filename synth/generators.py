@@ -133,6 +133,18 @@ def _binomial_counts(m: int, n: int, d: float, seed: int, stream: int) -> np.nda
     return np.minimum(k, kmax).astype(np.int64)
 
 
+def _sorted_unique(a: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (np.unique by sorting; numpy's hash-based unique is far slower
+    on tens of millions of keys)."""
+    a = np.sort(a)
+    if a.shape[0] < 2:
+        return a
+    keep = np.empty(a.shape[0], dtype=bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
 def _distinct_columns(k: np.ndarray, n: int, seed: int, stream: int) -> tuple:
     """For each row i, k[i] distinct columns drawn uniformly from [0, n); sorted per row.
 
@@ -155,7 +167,7 @@ def _distinct_columns(k: np.ndarray, n: int, seed: int, stream: int) -> tuple:
         j = np.arange(rows_r.shape[0], dtype=np.int64) - start[rows_r]
         ctr = (rows_r.astype(np.uint64) << np.uint64(32)) | (np.uint64(rnd) << np.uint64(22)) | j.astype(np.uint64)
         c = np.minimum((counter_uniform(seed, stream, ctr) * n).astype(np.int64), n - 1)
-        chosen = np.unique(np.concatenate([chosen, rows_r * n + c]))
+        chosen = _sorted_unique(np.concatenate([chosen, rows_r * n + c]))
         have = np.bincount(chosen // n, minlength=m).astype(np.int64)
         need = np.where(sparse_mask, k - have, 0)
         rnd += 1
@@ -273,7 +285,7 @@ def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c:
             r |= rb << bit
             q |= cb << bit
         keys_parts.append((r << scale) | q)
-    keys = np.unique(np.concatenate(keys_parts))
+    keys = _sorted_unique(np.concatenate(keys_parts))
     rows = keys >> scale
     cols = keys & (n - 1)
     rp, col = _csr_from_sorted_keys(n, n, rows, cols)

@@ -110,3 +110,33 @@ def test_batch_rejects_bad_job():
     with pytest.raises(sp.SpgemmError) as ei:
         sp.spgemm_batch(dA, dB)
     assert ei.value.name == "INVALID_CSR"
+
+
+@pytest.mark.parametrize("force_window", [0, 1])
+def test_batch_mixed_widths(force_window):
+    """Jobs of very different widths in one batch: each row keeps its own job's column count
+    (class choice, windowed block counts), including a job wider than one symbolic window
+    (2^20 columns) next to narrow jobs with dense rows."""
+    import paper_2004_13907_gb300 as sp
+    jobs = [
+        (synth.uniform_random(300, 60, 0.5, seed=11), synth.uniform_random(60, 900, 0.3, seed=12)),
+        (synth.uniform_random(2000, 2000, 0.01, seed=13), synth.uniform_random(2000, 2_500_000, 2e-5, seed=14)),
+        (synth.uniform_random(200, 100, 0.6, seed=15), synth.uniform_random(100, 5000, 0.2, seed=16)),
+        (synth.laplacian3d(10),) * 2,
+    ]
+    dA = [sp.DeviceCSR.from_host(A, "cuda") for A, _ in jobs]
+    dB = [sp.DeviceCSR.from_host(B, "cuda") for _, B in jobs]
+    batch = sp.spgemm_batch(dA, dB, opts=sp.spgemm_opts_default(force_window=force_window))
+    batch.check()
+    torch.cuda.synchronize()
+    for j, (A, B) in enumerate(jobs):
+        _check_job(A, B, batch.result(j))
+    # every row takes the class it takes alone (the narrow jobs' rows have P far above their
+    # own column counts but below the widest job's)
+    want = np.zeros(16, dtype=np.int64)
+    for a, b in zip(dA, dB):
+        plan = sp.spgemm_plan(a, b, opts=sp.spgemm_opts_default(force_window=force_window))
+        want += np.array(sp.spgemm_plan_get_info(plan)["sym_class_rows"])
+        sp.spgemm_plan_destroy(plan)
+    assert np.array_equal(np.array(batch.info()["sym_class_rows"]), want)
+    batch.destroy()
