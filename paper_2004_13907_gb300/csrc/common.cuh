@@ -19,6 +19,8 @@ enum : uint32_t {
   kErrCount = 16u,         // a row wrote a different number of entries than counted
 };
 
+constexpr int kMicroNa = 8;   // micro rows: at most this many A entries (B rows merged per thread)
+
 // Row classes. A row's class fixes the kernel that handles it. The class order is the
 // order of the rows in the permutation, so the windowed classes come first, largest
 // work first, which lets persistent blocks take the heaviest rows earliest.
@@ -31,7 +33,8 @@ enum SymClass : int {
   kSymWarp3,      // warp table of 2048 keys (min(P_i,n) <= 1024)
   kSymWarp2,      // warp table of 512 keys  (<= 256)
   kSymWarp1,      // warp table of 128 keys  (<= 64)
-  kSymTiny,       // P_i <= tiny_max and nnz(A_i) <= 32: registers only
+  kSymTiny,       // P_i <= tiny_max and nnz(A_i) <= 32: registers only, one warp per row
+  kSymMicro,      // tiny with nnz(A_i) <= kMicroNa: one thread per row merges the B rows
   kSymZero,       // P_i == 0
   kSymNumClasses
 };
@@ -47,6 +50,7 @@ enum NumClass : int {
   kNumWarp2,      // warp hash of 256 slots  (nnz <= 128)
   kNumWarp1,      // warp hash of 64 slots   (nnz <= 32)
   kNumTiny,
+  kNumMicro,      // tiny with nnz(A_i) <= kMicroNa, FP64: one thread per row merges the B rows
   kNumZero,
   kNumNumClasses
 };
@@ -77,7 +81,7 @@ __host__ __device__ inline int sym_class(int64_t P, int32_t na, const ClassParam
   if (P == 0) return kSymZero;
   const int64_t U = P < cp.n ? P : cp.n;
   if (cp.force_window) return kSymWin0 + win_subclass(P);
-  if (P <= cp.tiny_max && na <= kWarp) return kSymTiny;
+  if (P <= cp.tiny_max && na <= kWarp) return na <= kMicroNa ? kSymMicro : kSymTiny;
   if (cp.window_all) return kSymWin0 + win_subclass(P);
   if (U <= 64 && cp.warp_max >= 64) return kSymWarp1;
   if (U <= 256 && cp.warp_max >= 256) return kSymWarp2;
@@ -90,7 +94,7 @@ __host__ __device__ inline int num_class(int64_t P, int32_t na, int32_t nnz,
                                          const ClassParams& cp) {
   if (nnz == 0) return kNumZero;
   if (cp.force_window) return kNumWin0 + win_subclass(P);
-  if (P <= cp.tiny_max && na <= kWarp) return kNumTiny;
+  if (P <= cp.tiny_max && na <= kWarp) return (na <= kMicroNa && !cp.window_all) ? kNumMicro : kNumTiny;
   if (cp.window_all) return kNumWin0 + win_subclass(P);
   if (nnz <= 32 && cp.warp_max >= 64) return kNumWarp1;
   if (nnz <= 128 && cp.warp_max >= 256) return kNumWarp2;

@@ -122,6 +122,66 @@ __global__ void __launch_bounds__(256) k_num_tiny(DevCsr A, DevCsr B, const int3
   }
 }
 
+// Micro rows (nnz(A_i) <= kMicroNa, P_i <= tiny_max), FP64: one thread per row merges the row's
+// sorted B rows head by head. The smallest head column is the next column of C; the products of
+// every head holding it are summed in A-entry order and those heads advance. The output comes out
+// sorted, with no shared memory and no atomics.
+__global__ void __launch_bounds__(256) k_num_micro(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
+                                                   int64_t count, const int64_t* __restrict__ c_off,
+                                                   int32_t* __restrict__ ccol, double* __restrict__ cval,
+                                                   const int32_t* __restrict__ abase, uint32_t* err) {
+  constexpr int NA = kMicroNa;
+  constexpr int32_t kEnd = 0x7fffffff;
+  const double* av64 = static_cast<const double*>(A.val);
+  const double* bv64 = static_cast<const double*>(B.val);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < count; r += stride) {
+    const int32_t i = perm[r];
+    const int64_t a0 = A.rp[i];
+    const int na = static_cast<int>(A.rp[i + 1] - a0);
+    int64_t out = c_off[i];
+    const int64_t out_end = c_off[i + 1];
+    const int32_t cb = abase ? abase[i] : 0;
+    int64_t pos[NA];
+    int32_t left[NA], hc[NA];
+    double av[NA];
+#pragma unroll
+    for (int h = 0; h < NA; ++h) {
+      pos[h] = 0; left[h] = 0; hc[h] = kEnd; av[h] = 0.0;
+      if (h < na) {
+        const int32_t k = A.col[a0 + h];
+        av[h] = av64[a0 + h];
+        pos[h] = B.rp[k];
+        left[h] = static_cast<int32_t>(B.rp[k + 1] - pos[h]);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < NA; ++h) if (left[h] > 0) hc[h] = B.col[pos[h]];
+    for (;;) {
+      int32_t m = hc[0];
+#pragma unroll
+      for (int h = 1; h < NA; ++h) m = hc[h] < m ? hc[h] : m;
+      if (m == kEnd) break;
+      double sum = 0.0;
+#pragma unroll
+      for (int h = 0; h < NA; ++h) {
+        if (hc[h] == m) {
+          sum += av[h] * bv64[pos[h]];
+          ++pos[h];
+          --left[h];
+          hc[h] = left[h] > 0 ? B.col[pos[h]] : kEnd;
+        }
+      }
+      if (out < out_end) {   // a miscount raises kErrCount, never writes out of the row
+        ccol[out] = m - cb;
+        cval[out] = sum;
+      }
+      ++out;
+    }
+    if (out != out_end) set_error(err, kErrCount);
+  }
+}
+
 // Accumulate v into the slot of `key` (linear probing; keys are columns, kEmpty = free).
 template <int LOG2S>
 __device__ __forceinline__ void hash_accumulate(int32_t* keys, double* vals, int32_t key, double v,
@@ -306,6 +366,14 @@ int launch_num_tiny(int mode, const DevCsr& A, const DevCsr& B, const int32_t* p
   if (mode == kModeF32C) k_num_tiny<kModeF32C><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, abase, err);
   else if (mode == kModeF32R) k_num_tiny<kModeF32R><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, abase, err);
   else k_num_tiny<kModeF64><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, abase, err);
+  return 1;
+}
+
+int launch_num_micro(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                     const int64_t* c_off, int32_t* ccol, double* cval, const int32_t* abase, uint32_t* err,
+                     cudaStream_t s) {
+  if (count <= 0) return 0;
+  k_num_micro<<<grid_rows(count, 256, 152 * 16), 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, abase, err);
   return 1;
 }
 

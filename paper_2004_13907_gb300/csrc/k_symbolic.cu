@@ -56,6 +56,51 @@ __global__ void __launch_bounds__(256) k_sym_tiny(DevCsr A, DevCsr B, const int3
   }
 }
 
+// Micro rows (nnz(A_i) <= kMicroNa, P_i <= tiny_max): one thread per row merges the row's sorted
+// B rows head by head (the smallest head column is the next column of C; every head holding it
+// advances) and counts the distinct columns.
+__global__ void __launch_bounds__(256) k_sym_micro(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
+                                                   int64_t count, int32_t* __restrict__ nnz_row) {
+  constexpr int NA = kMicroNa;
+  constexpr int32_t kEnd = 0x7fffffff;   // column of an exhausted head (every column is smaller)
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < count; r += stride) {
+    const int32_t i = perm[r];
+    const int64_t a0 = A.rp[i];
+    const int na = static_cast<int>(A.rp[i + 1] - a0);
+    int64_t pos[NA];
+    int32_t left[NA], hc[NA];
+#pragma unroll
+    for (int h = 0; h < NA; ++h) {
+      pos[h] = 0; left[h] = 0; hc[h] = kEnd;
+      if (h < na) {
+        const int32_t k = A.col[a0 + h];
+        pos[h] = B.rp[k];
+        left[h] = static_cast<int32_t>(B.rp[k + 1] - pos[h]);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < NA; ++h) if (left[h] > 0) hc[h] = B.col[pos[h]];
+    int32_t n = 0;
+    for (;;) {
+      int32_t m = hc[0];
+#pragma unroll
+      for (int h = 1; h < NA; ++h) m = hc[h] < m ? hc[h] : m;
+      if (m == kEnd) break;
+      ++n;
+#pragma unroll
+      for (int h = 0; h < NA; ++h) {
+        if (hc[h] == m) {
+          ++pos[h];
+          --left[h];
+          hc[h] = left[h] > 0 ? B.col[pos[h]] : kEnd;
+        }
+      }
+    }
+    nnz_row[i] = n;
+  }
+}
+
 // Insert `key` into an open-addressing table (linear probing). Returns 1 if it was new.
 template <int LOG2S>
 __device__ __forceinline__ int insert_key(int32_t* table, int32_t key, uint32_t* err) {
@@ -232,6 +277,13 @@ int launch_sym_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64
                      int32_t* nnz_row, cudaStream_t s) {
   if (count <= 0) return 0;
   k_sym_tiny<<<grid_rows(count, 8, 152 * 64), 256, 0, s>>>(A, B, perm, count, nnz_row);
+  return 1;
+}
+
+int launch_sym_micro(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                     int32_t* nnz_row, cudaStream_t s) {
+  if (count <= 0) return 0;
+  k_sym_micro<<<grid_rows(count, 256, 152 * 16), 256, 0, s>>>(A, B, perm, count, nnz_row);
   return 1;
 }
 

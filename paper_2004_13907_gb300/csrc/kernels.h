@@ -49,6 +49,9 @@ int launch_write_rowptr(const int64_t* c_off, int64_t m1, void* out, int idx64, 
 // ---- symbolic kernels (k_symbolic.cu). Each handles perm[start, start+count).
 int launch_sym_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                      int32_t* nnz_row, cudaStream_t s);
+// Micro rows (nnz(A_i) <= kMicroNa): one thread per row merges the B rows.
+int launch_sym_micro(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                     int32_t* nnz_row, cudaStream_t s);
 int launch_sym_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                      int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s);
 int launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
@@ -65,6 +68,9 @@ int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int
 int launch_num_tiny(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                     const int64_t* c_off, int32_t* ccol, void* cval, int32_t* row_flag, const int32_t* abase,
                     uint32_t* err, cudaStream_t s);
+int launch_num_micro(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                     const int64_t* c_off, int32_t* ccol, double* cval, const int32_t* abase, uint32_t* err,
+                     cudaStream_t s);
 int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                      int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
                      const int32_t* abase, uint32_t* err, cudaStream_t s);

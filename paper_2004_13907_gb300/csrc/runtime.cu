@@ -191,6 +191,7 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
     stage_end(p, SPGEMM_STAGE_SYM_WARP, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_TINY, s);
     nl = launch_sym_tiny(p->A, p->B, seg(kSymTiny), cnt(kSymTiny), p->nnz_row, s);
+    nl += launch_sym_micro(p->A, p->B, seg(kSymMicro), cnt(kSymMicro), p->nnz_row, s);
     stage_end(p, SPGEMM_STAGE_SYM_TINY, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_SCAN, s);
     nl = launch_num_tiles(p->A, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum, &p->summary->cls_sums[0][0], s);
@@ -259,6 +260,7 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
     if (f32c) {
       for (int c = kNumBlock2; c <= kNumWarp1; ++c)
         if (cnt(c)) return set_error_msg(SPGEMM_ERR_INTERNAL, "FP32-compensated rows outside the windowed path");
+      if (cnt(kNumMicro)) return set_error_msg(SPGEMM_ERR_INTERNAL, "FP32-compensated rows in the FP64 micro path");
       if (!p->rerun_flag) {
         p->rerun_flag = ws_get<int32_t>(p, m, &st);
         p->rerun_list = ws_get<int32_t>(p, m, &st);
@@ -298,6 +300,9 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
     stage_begin(p, SPGEMM_STAGE_NUM_TINY, s);
     nl = launch_num_tiny(mode, p->A, p->B, seg(kNumTiny), cnt(kNumTiny), p->c_off, C->col, C->val, p->rerun_flag,
                          p->abase, err, s);
+    if (!f32c)
+      nl += launch_num_micro(p->A, p->B, seg(kNumMicro), cnt(kNumMicro), p->c_off, C->col,
+                             static_cast<double*>(C->val), p->abase, err, s);
     stage_end(p, SPGEMM_STAGE_NUM_TINY, nl, s);
     if (f32c && !p->opts.f32c_rerun_none) {
       // rows with an entry over the compensated bound are recomputed in FP64 and rounded once

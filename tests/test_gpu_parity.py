@@ -122,6 +122,35 @@ def test_int32_output_refused_when_too_large():
     assert ei.value.name == "INDEX_OVERFLOW"
 
 
+def _short_rows(m, k, n, na_of, blen_max, seed):
+    """A with na_of(i) entries in row i, B with 0..blen_max entries per row over n columns."""
+    rng = np.random.default_rng(seed)
+    na = np.array([na_of(i) for i in range(m)], dtype=np.int64)
+    arp = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(na, out=arp[1:])
+    acol = np.concatenate([np.sort(rng.choice(k, int(x), replace=False)) for x in na]).astype(np.int32)
+    blen = rng.integers(0, blen_max + 1, k)
+    brp = np.zeros(k + 1, dtype=np.int64)
+    np.cumsum(blen, out=brp[1:])
+    bcol = np.concatenate([np.sort(rng.choice(n, int(x), replace=False)) for x in blen]).astype(np.int32)
+    A = synth.CSR(m, k, arp, acol, rng.uniform(-1, 1, int(arp[-1])))
+    B = synth.CSR(k, n, brp, bcol, rng.uniform(-1, 1, int(brp[-1])))
+    return A, B
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(tiny_max=0), dict(validate=0)])
+def test_micro_and_tiny_rows(kw):
+    """Rows around the micro/tiny boundary (nnz(A_i) from 0 to 12, B rows of 0-3 entries over
+    300 columns, so heads collide often and some rows exceed 32 products)."""
+    A, B = _short_rows(4000, 5000, 300, lambda i: i % 13, 3, seed=40)
+    rp, col, val, _, info, _ = run_gpu(A, B, opts=opts(**kw))
+    assert_parity(A, B, rp, col, val)
+    if not kw:
+        import paper_2004_13907_gb300 as sp
+        cls = dict(zip(sp._native.NUM_CLASSES, info["num_class_rows"]))
+        assert cls["micro"] > 0 and cls["tiny"] > 0
+
+
 def test_identity_exact():
     A = synth.uniform_random(3000, 2500, 3e-3, seed=15)
     I = synth.identity(2500)
