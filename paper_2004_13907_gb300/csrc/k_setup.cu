@@ -22,28 +22,33 @@ __global__ void k_rowptr_to64(const int32_t* __restrict__ in, int64_t* __restric
 
 // One warp per row: row pointers in range and non-decreasing, columns strictly increasing
 // in [0, cols). Any violation sets kErrInvalidCsr.
-__global__ void k_validate(DevCsr M, uint32_t* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  if (warp0 == 0 && lane == 0) {
-    if (M.rp[0] != 0 || M.rp[M.rows] != M.nnz) set_error(err, kErrInvalidCsr);
-  }
-  for (int64_t i = warp0; i < M.rows; i += nwarps) {
+// Canonical-CSR check in two bandwidth-shaped passes. Rows: a thread per row checks its row
+// pointers and marks the row's first entry in a bitmap over the entries. Entries: a thread per
+// entry checks its column range and, unless the entry starts a row, that it is larger than the
+// entry before it.
+__global__ void __launch_bounds__(256) k_validate_rows(DevCsr M, uint32_t* __restrict__ starts, uint32_t* err) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t0 == 0 && (M.rp[0] != 0 || M.rp[M.rows] != M.nnz)) set_error(err, kErrInvalidCsr);
+  bool bad = false;
+  for (int64_t i = t0; i < M.rows; i += stride) {
     const int64_t s = M.rp[i], e = M.rp[i + 1];
-    bool bad = (s < 0) || (e < s) || (e > M.nnz);
-    if (__any_sync(0xffffffffu, bad)) {
-      if (lane == 0) set_error(err, kErrInvalidCsr);
-      continue;
-    }
-    for (int64_t j = s + lane; j < e; j += 32) {
-      const int32_t c = M.col[j];
-      bool b = (c < 0) || (c >= M.cols);
-      if (j > s) b = b || (M.col[j - 1] >= c);
-      if (b) bad = true;
-    }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(err, kErrInvalidCsr);
+    if (s < 0 || e < s || e > M.nnz) bad = true;
+    else if (s < e) atomicOr(&starts[s >> 5], 1u << (s & 31));
   }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_error(err, kErrInvalidCsr);
+}
+
+__global__ void __launch_bounds__(256) k_validate_cols(DevCsr M, const uint32_t* __restrict__ starts,
+                                                       uint32_t* err) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  bool bad = false;
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < M.nnz; j += stride) {
+    const int32_t c = M.col[j];
+    bad |= c < 0 || c >= M.cols;
+    if (j > 0 && !((starts[j >> 5] >> (j & 31)) & 1u)) bad |= M.col[j - 1] >= c;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_error(err, kErrInvalidCsr);
 }
 
 // Warp-aggregated increment of a shared counter per class; returns this lane's slot.
@@ -207,14 +212,31 @@ __global__ void __launch_bounds__(256) k_num_tiles(DevCsr A, ClassParams cp, con
     const int64_t row = t * kTileRows + r * 256 + threadIdx.x;
     const bool valid = row < A.rows;
     int cls = 0;
+    unsigned long long vp = 0, vn = 0, vz = 0;
     if (valid) {
       const int64_t na = A.rp[row + 1] - A.rp[row];
       const int32_t z = nnz_row[row];
       cls = num_class(P[row], na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na), z, cp);
       my += static_cast<unsigned long long>(z);
-      atomicAdd(&s_cls[cls][0], static_cast<unsigned long long>(P[row]));
-      atomicAdd(&s_cls[cls][1], static_cast<unsigned long long>(na));
-      atomicAdd(&s_cls[cls][2], static_cast<unsigned long long>(z));
+      vp = static_cast<unsigned long long>(P[row]);
+      vn = static_cast<unsigned long long>(na);
+      vz = static_cast<unsigned long long>(z);
+    }
+    // per-class sums: one warp reduction per distinct class of the warp (a stencil has one), so
+    // the shared counters see one atomic per class and warp instead of one per row
+    unsigned todo = __ballot_sync(0xffffffffu, valid);
+    while (todo) {
+      const int lc = __shfl_sync(0xffffffffu, cls, __ffs(todo) - 1);
+      const bool mine = valid && cls == lc;
+      const unsigned long long sp = warp_sum(mine ? vp : 0ull);
+      const unsigned long long sn = warp_sum(mine ? vn : 0ull);
+      const unsigned long long sz = warp_sum(mine ? vz : 0ull);
+      if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_cls[lc][0], sp);
+        atomicAdd(&s_cls[lc][1], sn);
+        atomicAdd(&s_cls[lc][2], sz);
+      }
+      todo &= ~__ballot_sync(0xffffffffu, mine);
     }
     aggregated_slot(hist, cls, valid);
   }
@@ -304,10 +326,13 @@ int launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t
   return 1;
 }
 
-int launch_validate(const DevCsr& M, uint32_t* err, cudaStream_t s) {
-  const int64_t warps = M.rows > 0 ? M.rows : 1;
-  k_validate<<<grid_for(warps * 32, 256), 256, 0, s>>>(M, err);
-  return 1;
+int64_t validate_words(int64_t nnz) { return (nnz + 31) / 32 + 1; }
+
+int launch_validate(const DevCsr& M, uint32_t* starts, uint32_t* err, cudaStream_t s) {
+  cudaMemsetAsync(starts, 0, sizeof(uint32_t) * validate_words(M.nnz), s);
+  k_validate_rows<<<grid_for(M.rows > 0 ? M.rows : 1, 256, 152 * 16), 256, 0, s>>>(M, starts, err);
+  if (M.nnz > 0) k_validate_cols<<<grid_for(M.nnz, 256, 152 * 16), 256, 0, s>>>(M, starts, err);
+  return M.nnz > 0 ? 2 : 1;
 }
 
 int launch_count(const DevCsr& A, const DevCsr& B, ClassParams cp, int64_t* P, int32_t* nnz_row,

@@ -268,28 +268,49 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     const uint16_t* cnts = cnt_cached ? s_cnt : gcnt;
     int64_t out = c_off[i];
     const int64_t out_end = c_off[i + 1];
-    int64_t next_b = 0;   // meaningful in thread 0 only
+    int64_t next_b = 0;   // meaningful in warp 0 only
     __syncthreads();
     for (;;) {
       // plan a batch of windows: runs of consecutive blocks holding <= merge_cap entries of C
-      if (threadIdx.x == 0) {
+      if (wid == 0) {
         int nw = 0;
         int64_t b = next_b;
         while (nw < kMaxWin) {
-          while (b < row_blocks && cnts[b] == 0) ++b;
-          if (b >= row_blocks) break;
-          int64_t e = b;
-          int32_t sum = 0;
-          do { sum += cnts[e]; ++e; }
-          while (e < row_blocks && e - b < kSpanBlocks && sum + cnts[e] <= merge_cap);
-          w_b0[nw] = static_cast<int32_t>(b);
-          w_b1[nw] = static_cast<int32_t>(e);
-          w_cnt[nw] = sum;
+          bool found = false;
+          while (b < row_blocks) {
+            const int64_t q = b + lane;
+            const unsigned m = __ballot_sync(0xffffffffu, q < row_blocks && cnts[q] != 0);
+            if (m) { b += __ffs(m) - 1; found = true; break; }
+            b += 32;
+          }
+          if (!found) { b = row_blocks; break; }
+          int32_t sum = cnts[b];
+          int64_t e = b + 1;
+          for (;;) {
+            const int64_t q = e + lane;
+            const bool in = q < row_blocks && q - b < kSpanBlocks;
+            int32_t incl = in ? cnts[q] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+              const int32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+              if (lane >= d) incl += v;
+            }
+            const unsigned okm = __ballot_sync(0xffffffffu, in && sum + incl <= merge_cap);
+            const int run = __popc(okm);
+            if (run > 0) sum += __shfl_sync(0xffffffffu, incl, run - 1);
+            e += run;
+            if (run < 32) break;
+          }
+          if (lane == 0) {
+            w_b0[nw] = static_cast<int32_t>(b);
+            w_b1[nw] = static_cast<int32_t>(e);
+            w_cnt[nw] = sum;
+          }
           ++nw;
           b = e;
         }
         next_b = b;
-        s_ctl[1] = nw;
+        if (lane == 0) s_ctl[1] = nw;
       }
       __syncthreads();
       const int nwin = s_ctl[1];

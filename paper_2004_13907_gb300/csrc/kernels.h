@@ -30,7 +30,9 @@ struct Summary {
 
 // ---- setup / scan kernels (k_setup.cu)
 int launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t s);
-int launch_validate(const DevCsr& M, uint32_t* err, cudaStream_t s);
+// starts: scratch of validate_words(M.nnz) words (the row-start bitmap).
+int64_t validate_words(int64_t nnz);
+int launch_validate(const DevCsr& M, uint32_t* starts, uint32_t* err, cudaStream_t s);
 int launch_count(const DevCsr& A, const DevCsr& B, ClassParams cp, int64_t* P, int32_t* nnz_row,
                   int32_t* tile_hist, int64_t* tile_sum, int64_t* tile_max, cudaStream_t s);
 int launch_class_scan(int64_t ntiles, int nclasses, int32_t* tile_hist, const int64_t* tile_sum,

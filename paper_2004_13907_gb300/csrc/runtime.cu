@@ -130,8 +130,10 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
 
   Summary h;
   if (o.validate) {
-    conv += launch_validate(p->A, &p->summary->err, s);
-    conv += launch_validate(p->B, &p->summary->err, s);
+    uint32_t* starts = ws_get<uint32_t>(p, validate_words(A->nnz > B->nnz ? A->nnz : B->nnz), &st);
+    if (st) return st;
+    conv += launch_validate(p->A, starts, &p->summary->err, s);
+    conv += launch_validate(p->B, starts, &p->summary->err, s);
     stage_end(p, SPGEMM_STAGE_VALIDATE, conv, s);
     if ((st = cuda_status(cudaGetLastError(), "launching validation")) != SPGEMM_OK) return st;
     if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
@@ -216,12 +218,13 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
 }
 
 void plan_bytes_bounds(int64_t m, int64_t a_nnz, int64_t width, int a_rowptr32, int b_rowptr32, int64_t b_rows,
-                       int64_t* lo, int64_t* hi) {
+                       int64_t b_nnz, int validate, int64_t* lo, int64_t* hi) {
   const int64_t ntiles = (m + kTileRows - 1) / kTileRows;
   int64_t fixed = ws_rounded(sizeof(Summary)) + ws_rounded(16 * 4) + ws_rounded(8 * m) + 3 * ws_rounded(4 * m) +
                   ws_rounded(8 * (m + 1));
   if (a_rowptr32) fixed += ws_rounded(8 * (m + 1));
   if (b_rowptr32) fixed += ws_rounded(8 * (b_rows + 1));
+  if (validate) fixed += ws_rounded(4 * validate_words(a_nnz > b_nnz ? a_nnz : b_nnz));
   const int64_t tiles = ws_rounded(4 * ntiles * kMaxClasses) + 3 * ws_rounded(8 * ntiles);
   const int64_t nblocks = (width + kBlockCols - 1) / kBlockCols;
   const int64_t window = ws_rounded(2 * m * nblocks) + ws_rounded(4 * m) + ws_rounded(4 * a_nnz);

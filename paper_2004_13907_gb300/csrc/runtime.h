@@ -98,7 +98,7 @@ int64_t numeric_extra_bytes(const spgemm_plan_s* p);
 // a_nnz entries and output rows `width` columns wide: *lo is always allocated, *hi is never
 // exceeded.
 void plan_bytes_bounds(int64_t m, int64_t a_nnz, int64_t width, int a_rowptr32, int b_rowptr32, int64_t b_rows,
-                       int64_t* lo, int64_t* hi);
+                       int64_t b_nnz, int validate, int64_t* lo, int64_t* hi);
 // Bytes the workspace takes for a request of `bytes`.
 inline int64_t ws_rounded(int64_t bytes) { return ((bytes <= 0 ? 16 : bytes) + 255) & ~int64_t(255); }
 void stage_begin(spgemm_plan_s* p, int stage, cudaStream_t s);

@@ -215,7 +215,7 @@ void scheduler_main(spgemm_server_s* S) {
     // bytes of the preparation from the sizes: split a group whose preparation could not fit
     // the cap, reject a job whose preparation alone is over it
     int64_t lo = 0, hi = 0;
-    batch_prepare_bounds(n, As.data(), Bs.data(), prec, &lo, &hi);
+    batch_prepare_bounds(n, As.data(), Bs.data(), prec, S->cfg.opts.validate, &lo, &hi);
     if (n > 1 && hi > S->cfg.mem_cap_bytes) {
       S->requeue_front(group, n / 2);
       ++S->n_splits;

@@ -207,6 +207,23 @@ def test_invalid_csr_is_reported():
     with pytest.raises(sp.SpgemmError) as ei:
         sp.spgemm_plan(dA, dA)
     assert ei.value.name == "INVALID_CSR"
+    col3 = A.col.copy()
+    col3[s + 1] = col3[s]                            # repeated column in a row
+    dA = sp.DeviceCSR.from_host(synth.CSR(A.rows, A.cols, A.row_ptr, col3, A.val), "cuda")
+    with pytest.raises(sp.SpgemmError) as ei:
+        sp.spgemm_plan(dA, dA)
+    assert ei.value.name == "INVALID_CSR"
+    rp4 = A.row_ptr.copy()
+    rp4[r + 1], rp4[r + 2] = rp4[r + 2], rp4[r + 1]  # decreasing row pointers (inside [0, nnz])
+    if rp4[r + 1] != rp4[r + 2]:
+        dA = sp.DeviceCSR.from_host(synth.CSR(A.rows, A.cols, rp4, A.col, A.val), "cuda")
+        with pytest.raises(sp.SpgemmError) as ei:
+            sp.spgemm_plan(dA, dA)
+        assert ei.value.name == "INVALID_CSR"
+    # a valid matrix whose rows start below the previous row's last column passes
+    ok = synth.CSR(3, 6, np.array([0, 2, 3, 5]), np.array([3, 5, 0, 1, 4], dtype=np.int32), np.ones(5))
+    sp.spgemm_plan_destroy(sp.spgemm_plan(sp.DeviceCSR.from_host(ok, "cuda"),
+                                          sp.DeviceCSR.from_host(synth.identity(6), "cuda")))
 
 
 def test_host_entry_matches_oracle():
