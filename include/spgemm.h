@@ -105,19 +105,22 @@ typedef struct spgemm_opts {
                                  rows take the windowed path (default 4096) */
   int32_t window_hash_fill;   /* windowed rows: consecutive column blocks are merged into one
                                  window while it holds at most this many entries of C (default
-                                 and maximum 8192; a single block is always one window) */
+                                 and maximum 4096; a single block is always one window) */
   int32_t force_window;       /* 1: every non-empty row takes the windowed path (tests) */
   int64_t rowptr32_limit;     /* nnz(C) >= this requires an int64 row_ptr (default 2^31-1;
                                  tests lower it) */
   int32_t f32c_rerun_all;     /* 1: recompute every F32 row in FP64 (tests) */
   int32_t f32c_rerun_none;    /* 1: never recompute (tests measure the bound alone) */
-  int32_t num_streams;        /* concurrent streams for the row classes (default 4) */
+  int32_t num_streams;        /* unused (kept for the layout; default 4) */
   int32_t record_timings;     /* 1: record CUDA events around every stage of the passes
                                  (read them with spgemm_plan_get_timings); default 0 */
   int32_t window_split_max_mb;/* device memory budget (MiB) of the column-block split table
                                  of B used by the windowed rows (default 4096); when the table
                                  would be larger, those rows binary-search B instead (0: always) */
-  int32_t reserved[13];
+  int32_t max_sms;            /* grids of the persistent and grid-stride kernels are sized for
+                                 this many SMs (0, default: all), leaving room on the device for
+                                 work on other streams */
+  int32_t reserved[12];
 } spgemm_opts;
 
 /* Opaque plan: the work description of one product (row counts, row classes, row
@@ -258,6 +261,32 @@ spgemm_status spgemm_batch_replay(spgemm_batch_t* batch, void* stream);
 
 spgemm_status spgemm_batch_destroy(spgemm_batch_t* batch);
 
+/* ---- Autotuning of the batched form. Times the caller's batch (spgemm_batch with the same
+ * arguments) under candidate row-class thresholds and window merge caps and returns the fastest
+ * options. Coordinate descent from `base` (library defaults when NULL): window_hash_fill in
+ * {1024, 2048, 4096}, block_max in {1024, 2048, 4096}, warp_max in {64, 256, 1024}, tiny_max in
+ * {0, 16, 32}, each trial the best of `reps` (>= 1) runs of the whole batch, timed with CUDA events
+ * on `stream`. Every candidate gives the same exact pattern and in-tolerance values; only the time
+ * differs. Blocks until done (about 12 trials). *best receives the chosen options; report (may be
+ * NULL) the trials in order. The paper has no counterpart: it chooses the thresholds of this
+ * library's row classes. */
+#define SPGEMM_TUNE_MAX_TRIALS 32
+typedef struct {
+  int32_t trials;             /* trials timed (the first is the starting options) */
+  int32_t reps;
+  double default_ms;          /* time of the starting options */
+  double best_ms;             /* time of the chosen options */
+  double trial_ms[SPGEMM_TUNE_MAX_TRIALS];
+  int32_t trial_tiny_max[SPGEMM_TUNE_MAX_TRIALS];
+  int32_t trial_warp_max[SPGEMM_TUNE_MAX_TRIALS];
+  int32_t trial_block_max[SPGEMM_TUNE_MAX_TRIALS];
+  int32_t trial_window_fill[SPGEMM_TUNE_MAX_TRIALS];
+} spgemm_tune_report;
+
+spgemm_status spgemm_autotune_batch(int64_t n_jobs, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                                    spgemm_prec prec, const spgemm_opts* base, int32_t reps,
+                                    void* stream, spgemm_opts* best, spgemm_tune_report* report);
+
 /* C = A*B without allocating any device memory, for callers that cannot allocate while they
  * call (for example code being captured into a CUDA graph, services that reserve the whole
  * device up front, or real-time loops that must not wait on an allocator). The paper has no
@@ -283,8 +312,8 @@ spgemm_status spgemm_multiply_noalloc(const spgemm_csr_in* A, const spgemm_csr_i
  * library's serving layer over the batched product above.
  * A scheduler thread gathers queued jobs in arrival order (up to max_batch_jobs, or until the
  * jobs' input entries reach max_batch_entries; it waits up to batch_window_us after the oldest
- * queued job arrived for more to come), stacks them as spgemm_batch does and runs the plan and
- * symbolic pass. That pass gives the EXACT device bytes of the batch (stacked inputs, plan
+ * queued job arrived for more to come; small jobs may overtake a large one for up to
+ * max_defer_ms), stacks them as spgemm_batch does and runs the plan and symbolic pass. That pass gives the EXACT device bytes of the batch (stacked inputs, plan
  * workspace, numeric tables and output); the numeric pass starts only when the bytes held by
  * the server plus that figure fit mem_cap_bytes, else it waits for running batches to finish or
  * for results to be released. A batch that does not fit the cap even alone is split in halves;
@@ -306,7 +335,17 @@ typedef struct {
   int32_t num_streams;         /* batches in flight, 1..8 (default 2) */
   int32_t start_paused;        /* queue jobs but start none until spgemm_server_resume */
   int32_t prec;                /* spgemm_prec of every job (default SPGEMM_F64) */
-  int32_t reserved_[3];
+  int32_t reserve_sms;         /* with 2+ streams, a batch holding at least half of
+                                  max_batch_entries runs its kernels on all SMs but this many
+                                  (opts.max_sms), so a batch of small jobs on another stream is not
+                                  held behind it (default 0: off) */
+  int32_t small_products;      /* jobs whose expected partial products, nnz(A)*nnz(B)/B.rows,
+                                  are at most this are small: while the oldest queued job is larger
+                                  and has waited less than max_defer_ms, batches take only small
+                                  jobs, which so overtake it (default 2^26; 0: strict arrival
+                                  order) */
+  int32_t max_defer_ms;        /* longest a large job at the head of the queue is overtaken
+                                  (default 250) */
   spgemm_opts opts;            /* options of each batch's plan */
 } spgemm_server_cfg;
 

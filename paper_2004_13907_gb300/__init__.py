@@ -26,7 +26,7 @@ __all__ = [
     "spgemm_plan", "spgemm_symbolic", "spgemm_numeric", "spgemm_plan_get_info",
     "spgemm_plan_check", "spgemm_plan_get_timings", "spgemm_plan_destroy", "spgemm_multiply_host", "spgemm_multiply_noalloc",
     "spgemm_last_error", "spgemm_version", "multiply", "lib", "Batch", "spgemm_batch", "Server",
-    "spgemm_server_cfg_default",
+    "spgemm_server_cfg_default", "spgemm_autotune_batch",
 ]
 
 
@@ -284,6 +284,26 @@ def spgemm_batch(As, Bs, prec=F64, opts: _native.Opts | None = None, stream=None
     _native.check(lib().spgemm_batch(n, arr_a, arr_b, prec, ctypes.byref(opts) if opts is not None else None, None,
                                      _stream_handle(stream), ctypes.byref(h)))
     return Batch(h.value, list(As), list(Bs), prec)
+
+
+def spgemm_autotune_batch(As, Bs, prec=F64, base: _native.Opts | None = None, reps: int = 2,
+                          stream=None) -> tuple:
+    """Row-class thresholds and window merge cap for this batch, chosen by timing it (see
+    include/spgemm.h). Returns (options, report) with the report's trials as a list of dicts."""
+    prec = _prec(prec)
+    n = len(As)
+    if n != len(Bs):
+        raise ValueError("As and Bs differ in length")
+    arr_a = (_native.CsrIn * n)(*[A.as_in() for A in As])
+    arr_b = (_native.CsrIn * n)(*[B.as_in() for B in Bs])
+    best = _native.Opts()
+    rep = _native.TuneReport()
+    _native.check(lib().spgemm_autotune_batch(n, arr_a, arr_b, prec, ctypes.byref(base) if base is not None else None,
+                                              reps, _stream_handle(stream), ctypes.byref(best), ctypes.byref(rep)))
+    k = min(rep.trials, _native.TUNE_MAX_TRIALS)
+    trials = [{"ms": rep.trial_ms[t], "tiny_max": rep.trial_tiny_max[t], "warp_max": rep.trial_warp_max[t],
+               "block_max": rep.trial_block_max[t], "window_hash_fill": rep.trial_window_fill[t]} for t in range(k)]
+    return best, {"trials": trials, "default_ms": rep.default_ms, "best_ms": rep.best_ms, "reps": rep.reps}
 
 
 def spgemm_multiply_noalloc(A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, stream=None) -> int:

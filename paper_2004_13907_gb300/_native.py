@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("validate", c_i32), ("tiny_max", c_i32), ("warp_max", c_i32), ("block_max", c_i32),
                 ("window_hash_fill", c_i32), ("force_window", c_i32), ("rowptr32_limit", c_i64),
                 ("f32c_rerun_all", c_i32), ("f32c_rerun_none", c_i32), ("num_streams", c_i32),
-                ("record_timings", c_i32), ("window_split_max_mb", c_i32), ("reserved", c_i32 * 13)]
+                ("record_timings", c_i32), ("window_split_max_mb", c_i32), ("max_sms", c_i32),
+                ("reserved", c_i32 * 12)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -74,7 +75,7 @@ class Timings(ctypes.Structure):
 class ServerCfg(ctypes.Structure):
     _fields_ = [("mem_cap_bytes", c_i64), ("max_batch_entries", c_i64), ("max_batch_jobs", c_i32),
                 ("batch_window_us", c_i32), ("num_streams", c_i32), ("start_paused", c_i32), ("prec", c_i32),
-                ("reserved_", c_i32 * 3), ("opts", Opts)]
+                ("reserve_sms", c_i32), ("small_products", c_i32), ("max_defer_ms", c_i32), ("opts", Opts)]
 
 
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "rejected"}
@@ -94,6 +95,16 @@ class ServerStats(ctypes.Structure):
                                                "latency_mean_ms", "mean_batch_jobs", "elapsed_s", "jobs_per_s",
                                                "products_per_s")] + \
                [("kernel_launches", c_i64), ("reserved_", c_i64 * 7)]
+
+
+TUNE_MAX_TRIALS = 32
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("trials", c_i32), ("reps", c_i32), ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double),
+                ("trial_ms", ctypes.c_double * TUNE_MAX_TRIALS), ("trial_tiny_max", c_i32 * TUNE_MAX_TRIALS),
+                ("trial_warp_max", c_i32 * TUNE_MAX_TRIALS), ("trial_block_max", c_i32 * TUNE_MAX_TRIALS),
+                ("trial_window_fill", c_i32 * TUNE_MAX_TRIALS)]
 
 
 # name -> (restype, argtypes); every symbol include/spgemm.h declares
@@ -131,6 +142,9 @@ SIGNATURES = {
     "spgemm_server_get_stats": (c_i32, [c_vp, ctypes.POINTER(ServerStats)]),
     "spgemm_server_reset_stats": (c_i32, [c_vp]),
     "spgemm_server_destroy": (c_i32, [c_vp]),
+    "spgemm_autotune_batch": (c_i32, [c_i64, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_i32,
+                                      ctypes.POINTER(Opts), c_i32, c_vp, ctypes.POINTER(Opts),
+                                      ctypes.POINTER(TuneReport)]),
     "spgemm_last_error": (ctypes.c_char_p, []),
     "spgemm_version": (ctypes.c_char_p, []),
 }

@@ -360,9 +360,9 @@ inline unsigned grid_rows(int64_t count, int rows_per_block, int max_blocks) {
 
 int launch_num_tiny(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                     const int64_t* c_off, int32_t* ccol, void* cval, int32_t* row_flag, const int32_t* abase,
-                    uint32_t* err, cudaStream_t s) {
+                    uint32_t* err, int num_sms, cudaStream_t s) {
   if (count <= 0) return 0;
-  const unsigned g = grid_rows(count, 8, 152 * 64);
+  const unsigned g = grid_rows(count, 8, num_sms * 64);
   if (mode == kModeF32C) k_num_tiny<kModeF32C><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, abase, err);
   else if (mode == kModeF32R) k_num_tiny<kModeF32R><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, abase, err);
   else k_num_tiny<kModeF64><<<g, 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, row_flag, abase, err);
@@ -371,17 +371,17 @@ int launch_num_tiny(int mode, const DevCsr& A, const DevCsr& B, const int32_t* p
 
 int launch_num_micro(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                      const int64_t* c_off, int32_t* ccol, double* cval, const int32_t* abase, uint32_t* err,
-                     cudaStream_t s) {
+                     int num_sms, cudaStream_t s) {
   if (count <= 0) return 0;
-  k_num_micro<<<grid_rows(count, 256, 152 * 16), 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, abase, err);
+  k_num_micro<<<grid_rows(count, 256, num_sms * 16), 256, 0, s>>>(A, B, perm, count, c_off, ccol, cval, abase, err);
   return 1;
 }
 
 int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                      int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
-                     const int32_t* abase, uint32_t* err, cudaStream_t s) {
+                     const int32_t* abase, uint32_t* err, int num_sms, cudaStream_t s) {
   if (count <= 0) return 0;
-  const unsigned g = grid_rows(count, 8, 152 * 32);
+  const unsigned g = grid_rows(count, 8, num_sms * 32);
   const size_t sm = size_t(8) * (size_t(1) << log2S) * 12;
   switch (log2S) {
     case 6: k_num_warp<6><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, abase, err); break;
@@ -397,15 +397,15 @@ int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* 
 
 int launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                       int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
-                      const int32_t* abase, uint32_t* err, cudaStream_t s) {
+                      const int32_t* abase, uint32_t* err, int num_sms, cudaStream_t s) {
   if (count <= 0) return 0;
   const size_t sm = (size_t(1) << log2S) * 12;
   if (log2S == 11) {
-    k_num_block<11, 256><<<grid_rows(count, 1, 152 * 8), 256, sm, s>>>(A, B, perm, count, c_off, ccol,
+    k_num_block<11, 256><<<grid_rows(count, 1, num_sms * 8), 256, sm, s>>>(A, B, perm, count, c_off, ccol,
                                                                        cval, abase, err);
   } else if (log2S == 13) {
     cudaFuncSetAttribute(k_num_block<13, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_num_block<13, 512><<<grid_rows(count, 1, 152 * 4), 512, sm, s>>>(A, B, perm, count, c_off, ccol,
+    k_num_block<13, 512><<<grid_rows(count, 1, num_sms * 4), 512, sm, s>>>(A, B, perm, count, c_off, ccol,
                                                                        cval, abase, err);
   }
   return 1;

@@ -274,23 +274,23 @@ inline unsigned grid_rows(int64_t count, int rows_per_block, int max_blocks) {
 }  // namespace
 
 int launch_sym_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
-                     int32_t* nnz_row, cudaStream_t s) {
+                     int32_t* nnz_row, int num_sms, cudaStream_t s) {
   if (count <= 0) return 0;
-  k_sym_tiny<<<grid_rows(count, 8, 152 * 64), 256, 0, s>>>(A, B, perm, count, nnz_row);
+  k_sym_tiny<<<grid_rows(count, 8, num_sms * 64), 256, 0, s>>>(A, B, perm, count, nnz_row);
   return 1;
 }
 
 int launch_sym_micro(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
-                     int32_t* nnz_row, cudaStream_t s) {
+                     int32_t* nnz_row, int num_sms, cudaStream_t s) {
   if (count <= 0) return 0;
-  k_sym_micro<<<grid_rows(count, 256, 152 * 16), 256, 0, s>>>(A, B, perm, count, nnz_row);
+  k_sym_micro<<<grid_rows(count, 256, num_sms * 16), 256, 0, s>>>(A, B, perm, count, nnz_row);
   return 1;
 }
 
 int launch_sym_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
-                     int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s) {
+                     int64_t count, int32_t* nnz_row, uint32_t* err, int num_sms, cudaStream_t s) {
   if (count <= 0) return 0;
-  const unsigned g = grid_rows(count, 8, 152 * 32);
+  const unsigned g = grid_rows(count, 8, num_sms * 32);
   const size_t sm = size_t(8) << log2S << 2;
   switch (log2S) {
     case 7: k_sym_warp<7><<<g, 256, sm, s>>>(A, B, perm, count, nnz_row, err); break;
@@ -305,11 +305,11 @@ int launch_sym_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* 
 }
 
 int launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
-                      int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s) {
+                      int64_t count, int32_t* nnz_row, uint32_t* err, int num_sms, cudaStream_t s) {
   if (count <= 0) return 0;
   const size_t sm = size_t(4) << log2S;
   if (log2S == 13) {
-    k_sym_block<13, 512><<<grid_rows(count, 1, 152 * 8), 512, sm, s>>>(A, B, perm, count, nnz_row, err);
+    k_sym_block<13, 512><<<grid_rows(count, 1, num_sms * 8), 512, sm, s>>>(A, B, perm, count, nnz_row, err);
   }
   return 1;
 }

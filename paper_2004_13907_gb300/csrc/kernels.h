@@ -50,14 +50,14 @@ int launch_write_rowptr(const int64_t* c_off, int64_t m1, void* out, int idx64, 
 
 // ---- symbolic kernels (k_symbolic.cu). Each handles perm[start, start+count).
 int launch_sym_tiny(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
-                     int32_t* nnz_row, cudaStream_t s);
+                     int32_t* nnz_row, int num_sms, cudaStream_t s);
 // Micro rows (nnz(A_i) <= kMicroNa): one thread per row merges the B rows.
 int launch_sym_micro(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
-                     int32_t* nnz_row, cudaStream_t s);
+                     int32_t* nnz_row, int num_sms, cudaStream_t s);
 int launch_sym_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
-                     int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s);
+                     int64_t count, int32_t* nnz_row, uint32_t* err, int num_sms, cudaStream_t s);
 int launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
-                      int64_t count, int32_t* nnz_row, uint32_t* err, cudaStream_t s);
+                      int64_t count, int32_t* nnz_row, uint32_t* err, int num_sms, cudaStream_t s);
 // abase (per row of A, may be NULL = 0) and awidth (per row, may be NULL = width) give each
 // row's column space [abase[i], abase[i] + awidth[i]); blocks are counted from abase[i]. nblocks
 // (the block-count stride of a row) covers the widest row.
@@ -69,16 +69,16 @@ int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int
 // ---- numeric kernels, FP64 (k_numeric.cu)
 int launch_num_tiny(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                     const int64_t* c_off, int32_t* ccol, void* cval, int32_t* row_flag, const int32_t* abase,
-                    uint32_t* err, cudaStream_t s);
+                    uint32_t* err, int num_sms, cudaStream_t s);
 int launch_num_micro(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                      const int64_t* c_off, int32_t* ccol, double* cval, const int32_t* abase, uint32_t* err,
-                     cudaStream_t s);
+                     int num_sms, cudaStream_t s);
 int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                      int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
-                     const int32_t* abase, uint32_t* err, cudaStream_t s);
+                     const int32_t* abase, uint32_t* err, int num_sms, cudaStream_t s);
 int launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
                       int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
-                      const int32_t* abase, uint32_t* err, cudaStream_t s);
+                      const int32_t* abase, uint32_t* err, int num_sms, cudaStream_t s);
 
 // ---- windowed numeric pass and the column-block split table of B (k_window.cu)
 int64_t split_table_bytes(int64_t brows, int64_t nblocks);

@@ -82,6 +82,7 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   spgemm_status st = SPGEMM_OK;
   const int64_t m = A->rows, n = B->cols;
   p->num_sms = device_sm_count();
+  if (p->opts.max_sms > 0 && p->opts.max_sms < p->num_sms) p->num_sms = p->opts.max_sms;
   // internal int64 row pointers
   const int64_t* arp = static_cast<const int64_t*>(A->row_ptr);
   const int64_t* brp = static_cast<const int64_t*>(B->row_ptr);
@@ -184,16 +185,16 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
                            p->abase, p->awidth, p->width, p->num_sms, err, s);
     stage_end(p, SPGEMM_STAGE_SYM_WINDOW, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_BLOCK, s);
-    nl = launch_sym_block(13, p->A, p->B, seg(kSymBlock), cnt(kSymBlock), p->nnz_row, err, s);
+    nl = launch_sym_block(13, p->A, p->B, seg(kSymBlock), cnt(kSymBlock), p->nnz_row, err, p->num_sms, s);
     stage_end(p, SPGEMM_STAGE_SYM_BLOCK, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_WARP, s);
-    nl = launch_sym_warp(11, p->A, p->B, seg(kSymWarp3), cnt(kSymWarp3), p->nnz_row, err, s);
-    nl += launch_sym_warp(9, p->A, p->B, seg(kSymWarp2), cnt(kSymWarp2), p->nnz_row, err, s);
-    nl += launch_sym_warp(7, p->A, p->B, seg(kSymWarp1), cnt(kSymWarp1), p->nnz_row, err, s);
+    nl = launch_sym_warp(11, p->A, p->B, seg(kSymWarp3), cnt(kSymWarp3), p->nnz_row, err, p->num_sms, s);
+    nl += launch_sym_warp(9, p->A, p->B, seg(kSymWarp2), cnt(kSymWarp2), p->nnz_row, err, p->num_sms, s);
+    nl += launch_sym_warp(7, p->A, p->B, seg(kSymWarp1), cnt(kSymWarp1), p->nnz_row, err, p->num_sms, s);
     stage_end(p, SPGEMM_STAGE_SYM_WARP, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_TINY, s);
-    nl = launch_sym_tiny(p->A, p->B, seg(kSymTiny), cnt(kSymTiny), p->nnz_row, s);
-    nl += launch_sym_micro(p->A, p->B, seg(kSymMicro), cnt(kSymMicro), p->nnz_row, s);
+    nl = launch_sym_tiny(p->A, p->B, seg(kSymTiny), cnt(kSymTiny), p->nnz_row, p->num_sms, s);
+    nl += launch_sym_micro(p->A, p->B, seg(kSymMicro), cnt(kSymMicro), p->nnz_row, p->num_sms, s);
     stage_end(p, SPGEMM_STAGE_SYM_TINY, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_SCAN, s);
     nl = launch_num_tiles(p->A, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum, &p->summary->cls_sums[0][0], s);
@@ -290,22 +291,25 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       double* cval = static_cast<double*>(C->val);
       stage_begin(p, SPGEMM_STAGE_NUM_BLOCK, s);
       nl = launch_num_block(13, p->A, p->B, seg(kNumBlock2), cnt(kNumBlock2), p->c_off, C->col, cval, p->abase,
-                            err, s);
+                            err, p->num_sms, s);
       nl += launch_num_block(11, p->A, p->B, seg(kNumBlock1), cnt(kNumBlock1), p->c_off, C->col, cval, p->abase,
-                             err, s);
+                             err, p->num_sms, s);
       stage_end(p, SPGEMM_STAGE_NUM_BLOCK, nl, s);
       stage_begin(p, SPGEMM_STAGE_NUM_WARP, s);
-      nl = launch_num_warp(10, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, cval, p->abase, err, s);
-      nl += launch_num_warp(8, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, cval, p->abase, err, s);
-      nl += launch_num_warp(6, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, cval, p->abase, err, s);
+      nl = launch_num_warp(10, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, cval, p->abase, err,
+                           p->num_sms, s);
+      nl += launch_num_warp(8, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, cval, p->abase, err,
+                            p->num_sms, s);
+      nl += launch_num_warp(6, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, cval, p->abase, err,
+                            p->num_sms, s);
       stage_end(p, SPGEMM_STAGE_NUM_WARP, nl, s);
     }
     stage_begin(p, SPGEMM_STAGE_NUM_TINY, s);
     nl = launch_num_tiny(mode, p->A, p->B, seg(kNumTiny), cnt(kNumTiny), p->c_off, C->col, C->val, p->rerun_flag,
-                         p->abase, err, s);
+                         p->abase, err, p->num_sms, s);
     if (!f32c)
       nl += launch_num_micro(p->A, p->B, seg(kNumMicro), cnt(kNumMicro), p->c_off, C->col,
-                             static_cast<double*>(C->val), p->abase, err, s);
+                             static_cast<double*>(C->val), p->abase, err, p->num_sms, s);
     stage_end(p, SPGEMM_STAGE_NUM_TINY, nl, s);
     if (f32c && !p->opts.f32c_rerun_none) {
       // rows with an entry over the compensated bound are recomputed in FP64 and rounded once
@@ -323,7 +327,7 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       nl += launch_num_window(kModeF32R, p->A, p->B, list_w, hc[0], p->counters + 2, p->c_off, p->win_slot,
                               p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
                               nullptr, p->abase, p->awidth, p->width, p->num_sms, err, s);
-      nl += launch_num_tiny(kModeF32R, p->A, p->B, list_t, hc[1], p->c_off, C->col, C->val, nullptr, p->abase, err,
+      nl += launch_num_tiny(kModeF32R, p->A, p->B, list_t, hc[1], p->c_off, C->col, C->val, nullptr, p->abase, err, p->num_sms,
                             s);
       stage_end(p, SPGEMM_STAGE_NUM_RERUN, nl, s);
       p->f32c_rerun_rows = int64_t(hc[0]) + hc[1];

@@ -44,6 +44,7 @@ struct Job {
   spgemm_status status = SPGEMM_OK;
   std::string msg;
   int64_t entries = 0;     // nnz(A) + nnz(B)
+  double work = 0.0;       // expected partial products, nnz(A) * nnz(B) / B.rows
   int64_t max_group = 1;   // largest batch it may join; halved when a batch is split for memory
   int64_t batch = -1;
   int64_t index = 0;       // position within its batch
@@ -82,6 +83,7 @@ struct spgemm_server_s {
   std::deque<int64_t> finished;
   int64_t next_job = 1, next_batch = 1;
   int num_streams = 1;
+  int sm_count = 0;
   cudaStream_t streams[kMaxStreams]{};
   bool slot_busy[kMaxStreams]{};
   cudaStream_t release_stream = nullptr;
@@ -107,28 +109,44 @@ struct spgemm_server_s {
     peak = std::max(peak, in_use);
   }
 
-  // Number of queued jobs, from the front, that the next batch takes; *limited is set when a
-  // limit (rather than the end of the queue) stops it.
-  int64_t group_size(bool* limited) {
-    int64_t n = 0, entries = 0, rows = 0, inner = 0, cols = 0;
-    int64_t cap = cfg.max_batch_jobs;
+  bool is_small(const Job& j) const { return j.work <= static_cast<double>(cfg.small_products); }
+
+  // Positions in the queue of the jobs the next batch takes, in queue order; *limited is set when
+  // a limit (rather than the end of the queue) stops it. Jobs are taken in arrival order, except
+  // that while the oldest job is large (over small_products) and has waited less than
+  // max_defer_ms, only small jobs are taken (they overtake it), so a burst of small requests does
+  // not wait behind a long product.
+  std::vector<size_t> pick_group(bool* limited) {
+    std::vector<size_t> pos;
     *limited = false;
-    for (int64_t id : pending) {
-      const Job& j = jobs.at(id);
+    if (pending.empty()) return pos;
+    bool small_only = false;
+    if (cfg.small_products > 0) {
+      const Job& front = jobs.at(pending.front());
+      const double waited = ms_between(front.t_submit, Clock::now());
+      if (!is_small(front) && waited < cfg.max_defer_ms)
+        for (int64_t id : pending)
+          if (is_small(jobs.at(id))) { small_only = true; break; }
+    }
+    int64_t entries = 0, rows = 0, inner = 0, cols = 0;
+    int64_t cap = cfg.max_batch_jobs;
+    for (size_t q = 0; q < pending.size(); ++q) {
+      const Job& j = jobs.at(pending[q]);
+      if (small_only && !is_small(j)) continue;
       cap = std::min(cap, j.max_group);
-      const bool over = n > 0 && (entries + j.entries > cfg.max_batch_entries || rows + j.A.rows >= kIndexLimit ||
-                                  inner + j.B.rows >= kIndexLimit || cols + j.B.cols >= kIndexLimit);
-      if (n >= cap || over) {
+      const bool over = !pos.empty() && (entries + j.entries > cfg.max_batch_entries || rows + j.A.rows >= kIndexLimit ||
+                                         inner + j.B.rows >= kIndexLimit || cols + j.B.cols >= kIndexLimit);
+      if (static_cast<int64_t>(pos.size()) >= cap || over) {
         *limited = true;
         break;
       }
-      ++n;
+      pos.push_back(q);
       entries += j.entries;
       rows += j.A.rows;
       inner += j.B.rows;
       cols += j.B.cols;
     }
-    return n;
+    return pos;
   }
 
   void finish_job(int64_t id, int32_t state, spgemm_status st, const std::string& msg, Clock::time_point now) {
@@ -196,17 +214,31 @@ void scheduler_main(spgemm_server_s* S) {
     // fill window: wait for more jobs until the oldest queued one has waited batch_window_us
     const auto deadline = S->jobs.at(S->pending.front()).t_submit + std::chrono::microseconds(S->cfg.batch_window_us);
     bool limited = false;
-    S->group_size(&limited);
+    S->pick_group(&limited);
     while (!S->stop && !S->paused && !limited && Clock::now() < deadline) {
       S->cv_sched.wait_until(lk, deadline);
       if (S->pending.empty()) break;
-      S->group_size(&limited);
+      S->pick_group(&limited);
     }
     if (S->stop) break;
     if (S->paused || S->pending.empty()) continue;
-    const int64_t n = S->group_size(&limited);
-    std::vector<int64_t> group(S->pending.begin(), S->pending.begin() + n);
-    S->pending.erase(S->pending.begin(), S->pending.begin() + n);
+    const std::vector<size_t> picked = S->pick_group(&limited);
+    const int64_t n = static_cast<int64_t>(picked.size());
+    std::vector<int64_t> group;
+    group.reserve(picked.size());
+    {
+      std::deque<int64_t> rest;
+      size_t k = 0;
+      for (size_t q = 0; q < S->pending.size(); ++q) {
+        if (k < picked.size() && picked[k] == q) {
+          group.push_back(S->pending[q]);
+          ++k;
+        } else {
+          rest.push_back(S->pending[q]);
+        }
+      }
+      S->pending.swap(rest);
+    }
     std::vector<spgemm_csr_in> As(n), Bs(n);
     for (int64_t k = 0; k < n; ++k) {
       As[k] = S->jobs.at(group[k]).A;
@@ -248,7 +280,17 @@ void scheduler_main(spgemm_server_s* S) {
     S->slot_busy[slot] = true;
     ++S->inflight;
     const cudaStream_t stream = S->streams[slot];
-    const spgemm_opts opts = S->cfg.opts;
+    spgemm_opts opts = S->cfg.opts;
+    {
+      // a large batch leaves reserve_sms SMs to the batches on the other streams
+      int64_t entries = 0;
+      for (int64_t k = 0; k < n; ++k) entries += As[k].nnz + Bs[k].nnz;
+      if (S->num_streams > 1 && S->cfg.reserve_sms > 0 && 2 * entries >= S->cfg.max_batch_entries &&
+          S->sm_count > S->cfg.reserve_sms) {
+        const int cap = S->sm_count - S->cfg.reserve_sms;
+        if (opts.max_sms <= 0 || opts.max_sms > cap) opts.max_sms = cap;
+      }
+    }
     lk.unlock();
 
     spgemm_batch_t* b = nullptr;
@@ -454,6 +496,9 @@ extern "C" spgemm_status spgemm_server_cfg_default(spgemm_server_cfg* cfg) {
   cfg->num_streams = 2;
   cfg->start_paused = 0;
   cfg->prec = SPGEMM_F64;
+  cfg->reserve_sms = 0;
+  cfg->small_products = 1 << 26;
+  cfg->max_defer_ms = 250;
   spgemm_opts_default(&cfg->opts);
   return SPGEMM_OK;
 }
@@ -468,7 +513,8 @@ extern "C" spgemm_status spgemm_server_create(const spgemm_server_cfg* cfg, spge
   if (c.prec != SPGEMM_F64 && c.prec != SPGEMM_F32_COMPENSATED)
     return set_error_msg(SPGEMM_ERR_INVALID_ARG, "unknown precision %d", int(c.prec));
   if (c.mem_cap_bytes <= 0 || c.max_batch_jobs < 1 || c.max_batch_entries < 1 || c.batch_window_us < 0 ||
-      c.num_streams < 1 || c.num_streams > kMaxStreams)
+      c.num_streams < 1 || c.num_streams > kMaxStreams || c.reserve_sms < 0 || c.small_products < 0 ||
+      c.max_defer_ms < 0)
     return set_error_msg(SPGEMM_ERR_INVALID_ARG, "bad server configuration");
   spgemm_server_s* S = new (std::nothrow) spgemm_server_s();
   if (!S) return set_error_msg(SPGEMM_ERR_OOM, "host allocation of the server failed");
@@ -476,6 +522,7 @@ extern "C" spgemm_status spgemm_server_create(const spgemm_server_cfg* cfg, spge
   S->paused = c.start_paused != 0;
   S->num_streams = c.num_streams;
   cudaError_t e = cudaGetDevice(&S->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, S->device);
   for (int i = 0; e == cudaSuccess && i < S->num_streams; ++i)
     e = cudaStreamCreateWithFlags(&S->streams[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->release_stream, cudaStreamNonBlocking);
@@ -510,6 +557,7 @@ extern "C" spgemm_status spgemm_server_submit(spgemm_server_t* S, const spgemm_c
     j.A = *A;
     j.B = *B;
     j.entries = A->nnz + B->nnz;
+    j.work = B->rows > 0 ? static_cast<double>(A->nnz) * static_cast<double>(B->nnz) / static_cast<double>(B->rows) : 0.0;
     j.max_group = S->cfg.max_batch_jobs;
     j.t_submit = Clock::now();
     if (!S->have_first) {

@@ -58,7 +58,8 @@ def test_struct_layout_matches_c(tmp_path):
         " sizeof(spgemm_plan_info), offsetof(spgemm_opts, rowptr32_limit),"
         " offsetof(spgemm_plan_info, workspace_bytes), sizeof(spgemm_server_cfg),"
         " offsetof(spgemm_server_cfg, opts), sizeof(spgemm_job_info), sizeof(spgemm_server_stats),"
-        " offsetof(spgemm_server_stats, latency_p50_ms)); return 0;}\n")
+        " offsetof(spgemm_server_stats, latency_p50_ms)); printf(\"%zu %zu\\n\", sizeof(spgemm_tune_report),"
+        " offsetof(spgemm_tune_report, trial_window_fill)); return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
@@ -66,7 +67,8 @@ def test_struct_layout_matches_c(tmp_path):
             ctypes.sizeof(_native.Opts), ctypes.sizeof(_native.PlanInfo),
             _native.Opts.rowptr32_limit.offset, _native.PlanInfo.workspace_bytes.offset,
             ctypes.sizeof(_native.ServerCfg), _native.ServerCfg.opts.offset, ctypes.sizeof(_native.JobInfo),
-            ctypes.sizeof(_native.ServerStats), _native.ServerStats.latency_p50_ms.offset]
+            ctypes.sizeof(_native.ServerStats), _native.ServerStats.latency_p50_ms.offset,
+            ctypes.sizeof(_native.TuneReport), _native.TuneReport.trial_window_fill.offset]
     assert got == want
 
 
@@ -106,9 +108,11 @@ def test_server_config_checks_on_host(lib):
     assert lib.spgemm_server_cfg_default(ctypes.byref(cfg)) == 0
     assert cfg.mem_cap_bytes == 32 << 30 and cfg.num_streams == 2 and cfg.prec == 0
     assert cfg.opts.validate == 1 and cfg.opts.window_hash_fill == 4096
+    assert cfg.reserve_sms == 0 and cfg.opts.max_sms == 0
+    assert cfg.small_products == 1 << 26 and cfg.max_defer_ms == 250
     h = ctypes.c_void_p()
     for field, bad in [("num_streams", 0), ("num_streams", 9), ("mem_cap_bytes", 0), ("max_batch_jobs", 0),
-                       ("prec", 7), ("batch_window_us", -1)]:
+                       ("prec", 7), ("batch_window_us", -1), ("reserve_sms", -1), ("small_products", -1), ("max_defer_ms", -1)]:
         c = _native.ServerCfg()
         lib.spgemm_server_cfg_default(ctypes.byref(c))
         setattr(c, field, bad)

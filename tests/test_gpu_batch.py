@@ -140,3 +140,24 @@ def test_batch_mixed_widths(force_window):
         sp.spgemm_plan_destroy(plan)
     assert np.array_equal(np.array(batch.info()["sym_class_rows"]), want)
     batch.destroy()
+
+
+def test_autotuned_batch_matches_oracle():
+    """The autotuner times every candidate on the batch and returns the fastest options; the batch
+    run with them is exact job by job."""
+    import paper_2004_13907_gb300 as sp
+    jobs = _jobs(40, seed=3)
+    jobs.append((synth.rmat(11, 16, seed=12),) * 2)
+    jobs.append((synth.laplacian2d(60),) * 2)
+    dA = [sp.DeviceCSR.from_host(A, "cuda") for A, _ in jobs]
+    dB = [sp.DeviceCSR.from_host(B, "cuda") for _, B in jobs]
+    best, rep = sp.spgemm_autotune_batch(dA, dB, reps=1)
+    assert len(rep["trials"]) == 9 and rep["best_ms"] <= rep["default_ms"]
+    assert min(t["ms"] for t in rep["trials"]) == rep["best_ms"]
+    assert best.window_hash_fill in (1024, 2048, 4096) and best.tiny_max in (0, 16, 32)
+    batch = sp.spgemm_batch(dA, dB, opts=best)
+    batch.check()
+    torch.cuda.synchronize()
+    for j, (A, B) in enumerate(jobs):
+        _check_job(A, B, batch.result(j))
+    batch.destroy()

@@ -68,6 +68,7 @@ def test_rmat_small_full(scale):
     dict(force_window=1, window_hash_fill=1),
     dict(force_window=1, window_split_max_mb=0),
     dict(validate=0),
+    dict(max_sms=7),
 ])
 def test_forced_paths_rmat(kw):
     A = synth.rmat(12, 16, seed=5)

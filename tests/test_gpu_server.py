@@ -212,3 +212,27 @@ def test_f32c_server():
         for (A, B), (dA, dB), i in zip(jobs, dev, ids):
             assert srv.wait(i, timeout=120)["state"] == "done"
             _same_as_alone(A, B, srv.result(i), sp.multiply(dA, dB, prec="f32c"), f32=True)
+
+
+def test_small_jobs_overtake_a_large_one_for_a_bounded_time():
+    """With a paused queue holding a large job followed by small ones, the small jobs run first
+    (they overtake it), and with max_defer_ms=0 strict arrival order holds."""
+    import paper_2004_13907_gb300 as sp
+    big = synth.uniform_random(10_000, 10_000, 2e-2, seed=110)     # about 4e8 expected products
+    smalls = [synth.batch_job(i, seed=111, n_lo=200, n_hi=400) for i in range(5)]
+    dbig = sp.DeviceCSR.from_host(big, "cuda")
+    dsm = [(sp.DeviceCSR.from_host(A, "cuda"), sp.DeviceCSR.from_host(B, "cuda")) for A, B in smalls]
+    for defer, small_first in ((10_000, True), (0, False)):
+        with sp.Server(start_paused=1, num_streams=1, batch_window_us=0, max_batch_jobs=1,
+                       max_defer_ms=defer) as srv:
+            jb = srv.submit(dbig, dbig)
+            js = [srv.submit(a, b) for a, b in dsm]
+            srv.resume()
+            ib = srv.wait(jb, timeout=120)
+            iss = [srv.wait(j, timeout=120) for j in js]
+            if small_first:
+                assert all(x["batch"] < ib["batch"] for x in iss)
+            else:
+                assert all(x["batch"] > ib["batch"] for x in iss)
+            for (A, B), (a, b), j in zip(smalls, dsm, js):
+                _same_as_alone(A, B, srv.result(j), sp.multiply(a, b))
