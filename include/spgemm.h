@@ -120,7 +120,12 @@ typedef struct spgemm_opts {
   int32_t max_sms;            /* grids of the persistent and grid-stride kernels are sized for
                                  this many SMs (0, default: all), leaving room on the device for
                                  work on other streams */
-  int32_t reserved[12];
+  int32_t window_cols_max_mb; /* device memory budget (MiB) in which the symbolic pass stores the
+                                 column bitmaps of windowed rows (those within 2^20 columns; 512
+                                 bytes per 4096 columns of the row), so the numeric pass copies
+                                 them instead of marking every partial product again; rows beyond
+                                 the budget are marked again (default 49152; 0: never store) */
+  int32_t reserved[11];
 } spgemm_opts;
 
 /* Opaque plan: the work description of one product (row counts, row classes, row

@@ -146,6 +146,7 @@ void spgemm_opts_default(spgemm_opts* o) {
   o->num_streams = 4;
   o->record_timings = 0;
   o->window_split_max_mb = 4096;
+  o->window_cols_max_mb = 49152;
 }
 
 const char* spgemm_last_error(void) { return g_last_error.c_str(); }

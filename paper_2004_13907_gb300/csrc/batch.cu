@@ -291,7 +291,7 @@ spgemm_status batch_prepare(int64_t n_jobs, const spgemm_csr_in* A, const spgemm
 }
 
 void batch_prepare_bounds(int64_t n_jobs, const spgemm_csr_in* A, const spgemm_csr_in* B, spgemm_prec prec,
-                          int validate, int64_t* lo, int64_t* hi) {
+                          const spgemm_opts* opts, int64_t* lo, int64_t* hi) {
   const int vb = prec == SPGEMM_F64 ? 8 : 4;
   int64_t rows = 0, inner = 0, a_nnz = 0, b_nnz = 0, width = 1, stack_tiles = 0, value_tiles = 0, rp_tiles = 0;
   for (int64_t j = 0; j < n_jobs; ++j) {
@@ -313,7 +313,7 @@ void batch_prepare_bounds(int64_t n_jobs, const spgemm_csr_in* A, const spgemm_c
                           ws_rounded(8 * (inner + 1)) + ws_rounded(4 * b_nnz) + ws_rounded(vb * b_nnz) +
                           ws_rounded(4 * inner) + ws_rounded(4);
   int64_t plo = 0, phi = 0;
-  plan_bytes_bounds(rows, a_nnz, width, 0, 0, inner, b_nnz, validate, &plo, &phi);
+  plan_bytes_bounds(rows, a_nnz, width, 0, 0, inner, b_nnz, opts->validate, opts->window_cols_max_mb, &plo, &phi);
   *lo = stacked + plo;
   *hi = stacked + phi;
 }

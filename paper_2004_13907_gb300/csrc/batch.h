@@ -13,7 +13,7 @@ spgemm_status batch_prepare(int64_t n_jobs, const spgemm_csr_in* A, const spgemm
 // Bounds, from the jobs' sizes alone, on the device bytes batch_prepare allocates: *lo is always
 // allocated, *hi never exceeded.
 void batch_prepare_bounds(int64_t n_jobs, const spgemm_csr_in* A, const spgemm_csr_in* B, spgemm_prec prec,
-                          int validate, int64_t* lo, int64_t* hi);
+                          const spgemm_opts* opts, int64_t* lo, int64_t* hi);
 // Device bytes the prepared batch holds now, and the bytes its output will take.
 int64_t batch_device_bytes(const spgemm_batch_t* b);
 int64_t batch_output_bytes(const spgemm_batch_t* b);

@@ -187,13 +187,16 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
                                                                int64_t nblocks, int32_t* cursor,
                                                                const int32_t* __restrict__ abase,
                                                                const int32_t* __restrict__ awidth,
-                                                               int64_t width_all, uint32_t* err) {
+                                                               int64_t width_all, uint32_t* __restrict__ wbits,
+                                                               int64_t wcap, unsigned long long* wcur,
+                                                               int64_t* __restrict__ woff, uint32_t* err) {
   extern __shared__ uint32_t bm[];  // kSymWinBits / 32 words
   __shared__ int32_t s_excl[kSymWinThreads];
   __shared__ int64_t s_bs[kSymWinThreads];
   __shared__ int32_t s_scan[33];
   __shared__ int32_t s_idx;
   __shared__ unsigned long long s_total;
+  __shared__ long long s_woff;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int kWarps = kSymWinThreads / 32;
   for (;;) {
@@ -211,6 +214,9 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
     const int64_t cb = abase ? abase[i] : 0;   // the row's columns are [cb, cb + width)
     const int64_t width = awidth ? awidth[i] : width_all;
     uint16_t* cnts = blockcnt + idx * nblocks;
+    // a row inside one window stores its bitmap (for the numeric pass) when wbits has room
+    const bool store = wbits != nullptr && width <= kSymWinBits;
+    if (threadIdx.x == 0 && woff) woff[idx] = -1;
     for (int64_t r0 = 0; r0 < width; r0 += kSymWinBits) {
       const int64_t w0 = cb + r0;
       const int64_t wend = cb + ((r0 + kSymWinBits < width) ? r0 + kSymWinBits : width);
@@ -258,6 +264,32 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
         }
       }
       __syncthreads();
+      if (store) {
+        // the row's bitmap (its blocks, 128 words each) goes to wbits for the numeric pass
+        const int nb = static_cast<int>(b1);   // a stored row has one window, starting at block 0
+        const int64_t words = int64_t(nb) * kBlockWords;
+        if (threadIdx.x == 0) {
+          const unsigned long long off = atomicAdd(wcur, static_cast<unsigned long long>(words));
+          s_woff = off + words <= static_cast<unsigned long long>(wcap) ? static_cast<long long>(off) : -1ll;
+          woff[idx] = s_woff;
+        }
+        __syncthreads();
+        const long long wo = s_woff;
+        if (wo >= 0) {
+          // words past the row's width (the tail of its last block) are stored as zero
+          uint4* dst = reinterpret_cast<uint4*>(wbits + wo);
+          for (int64_t q = threadIdx.x; q < words / 4; q += kSymWinThreads) {
+            const int w = static_cast<int>(q * 4);
+            uint4 v;
+            v.x = w + 0 < nwords ? bm[w + 0] : 0u;
+            v.y = w + 1 < nwords ? bm[w + 1] : 0u;
+            v.z = w + 2 < nwords ? bm[w + 2] : 0u;
+            v.w = w + 3 < nwords ? bm[w + 3] : 0u;
+            dst[q] = v;
+          }
+        }
+        __syncthreads();
+      }
     }
     if (threadIdx.x == 0) nnz_row[i] = static_cast<int32_t>(s_total);
     __syncthreads();
@@ -317,7 +349,8 @@ int launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t*
 int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                        int32_t* counter, int32_t* nnz_row, int32_t* win_slot, uint16_t* blockcnt,
                        int64_t nblocks, int32_t* cursor, const int32_t* abase, const int32_t* awidth,
-                       int64_t width, int num_sms, uint32_t* err, cudaStream_t s) {
+                       int64_t width, uint32_t* wbits, int64_t wcap, unsigned long long* wcur, int64_t* woff,
+                       int num_sms, uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   const size_t sm = size_t(kSymWinBits / 32) * 4;
   cudaFuncSetAttribute(k_sym_window, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
@@ -325,7 +358,7 @@ int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int
   const int64_t g = count < num_sms ? count : num_sms;
   k_sym_window<<<static_cast<unsigned>(g), kSymWinThreads, sm, s>>>(A, B, perm, count, counter, nnz_row,
                                                                  win_slot, blockcnt, nblocks, cursor,
-                                                                 abase, awidth, width, err);
+                                                                 abase, awidth, width, wbits, wcap, wcur, woff, err);
   return 1;
 }
 

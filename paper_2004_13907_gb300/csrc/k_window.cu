@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     const uint16_t* __restrict__ blockcnt, int64_t nblocks, int64_t nslots,
     const int32_t* __restrict__ split, int32_t merge_cap, int32_t* __restrict__ ccol,
     void* __restrict__ cval_, int32_t* __restrict__ row_flag, const int32_t* __restrict__ abase,
-    const int32_t* __restrict__ awidth, int64_t width_all, uint32_t* err) {
+    const int32_t* __restrict__ awidth, int64_t width_all, const uint32_t* __restrict__ wbits,
+    const int64_t* __restrict__ woff, uint32_t* err) {
   constexpr int kSmemVals = WinGeom<Mode>::kSmemVals;
   extern __shared__ __align__(16) unsigned char win_smem[];
   double* vals = reinterpret_cast<double*>(win_smem);        // kModeF64, kModeF32R
@@ -268,6 +269,9 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     const uint16_t* cnts = cnt_cached ? s_cnt : gcnt;
     int64_t out = c_off[i];
     const int64_t out_end = c_off[i + 1];
+    // the symbolic pass stored this row's column bitmap: windows copy it instead of marking
+    const int64_t toff = woff ? woff[slot] : -1;
+    const bool stored = toff >= 0;
     int64_t next_b = 0;   // meaningful in warp 0 only
     __syncthreads();
     for (;;) {
@@ -323,8 +327,13 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
         const int32_t expect = w_cnt[wi];
         const int nwords = (span + 31) >> 5;
 
-        // pass 1: mark the window's columns
-        for (int64_t base = 0; base < na; base += kNumThreads) {
+        // pass 1: mark the window's columns (copy the stored bitmap when the row has one)
+        if (stored) {
+          const uint32_t* src = wbits + toff + b0 * kBlockWords;
+          for (int w = threadIdx.x; w < nwords; w += kNumThreads) bm[w] = src[w];
+          __syncthreads();
+        }
+        for (int64_t base = 0; base < (stored ? 0 : na); base += kNumThreads) {
           build_chunk(a0, na, base, resident, b0, b1, w0, w1);
           const int nent = s_ctl[6];
           const int32_t total = s_ctl[7];
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
         if (threadIdx.x == 0 && cnt != expect) set_error(err, kErrCount);
         // pass 2: accumulate a_ik * b_kj by rank
         for (int64_t base = 0; base < na; base += kNumThreads) {
-          if (na > kNumThreads) build_chunk(a0, na, base, resident, b0, b1, w0, w1);
+          if (na > kNumThreads || stored) build_chunk(a0, na, base, resident, b0, b1, w0, w1);
           const int nent = s_ctl[6];    // the single chunk of a resident row is kept from pass 1
           const int32_t total = s_ctl[7];
           int32_t per = (total + kWarps - 1) / kWarps;
@@ -428,7 +437,12 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
                 const int32_t rel = static_cast<int32_t>(c[u] - w0);
                 if (rel < 0 || rel >= span) continue;
                 const int wd = rel >> 5;
-                const int r = grp[wd / kGroupWords] + pre[wd] + __popc(bm[wd] & ((1u << (rel & 31)) - 1u));
+                const uint32_t word = bm[wd];
+                if (stored && !((word >> (rel & 31)) & 1u)) {   // a product outside the stored columns
+                  set_error(err, kErrWindowPlan);
+                  continue;
+                }
+                const int r = grp[wd / kGroupWords] + pre[wd] + __popc(word & ((1u << (rel & 31)) - 1u));
                 if (r >= kRankCap) continue;
                 if constexpr (Mode == kModeF32C) {
                   // error-free product a*b = ph + pl (TwoProduct with fmaf); the sum's own rounding
@@ -514,8 +528,8 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
                       int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
                       int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag,
-                      const int32_t* abase, const int32_t* awidth, int64_t width, int num_sms, uint32_t* err,
-                      cudaStream_t s) {
+                      const int32_t* abase, const int32_t* awidth, int64_t width, const uint32_t* wbits,
+                      const int64_t* woff, int num_sms, uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   auto go = [&](auto kernel, int smem, int per_sm) {
@@ -523,7 +537,8 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
     const int64_t g = count < int64_t(per_sm) * num_sms ? count : int64_t(per_sm) * num_sms;
     kernel<<<static_cast<unsigned>(g), kNumThreads, smem, s>>>(A, B, perm, count, counter, c_off, win_slot,
                                                                blockcnt, nblocks, nslots, split, merge_cap,
-                                                               ccol, cval, row_flag, abase, awidth, width, err);
+                                                               ccol, cval, row_flag, abase, awidth, width, wbits,
+                                                               woff, err);
   };
   if (mode == kModeF32C) go(k_num_window<kModeF32C>, WinGeom<kModeF32C>::kSmemBytes, 1);
   else if (mode == kModeF32R) go(k_num_window<kModeF32R>, WinGeom<kModeF32R>::kSmemBytes, 2);

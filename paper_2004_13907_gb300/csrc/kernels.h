@@ -60,11 +60,15 @@ int launch_sym_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t*
                       int64_t count, int32_t* nnz_row, uint32_t* err, int num_sms, cudaStream_t s);
 // abase (per row of A, may be NULL = 0) and awidth (per row, may be NULL = width) give each
 // row's column space [abase[i], abase[i] + awidth[i]); blocks are counted from abase[i]. nblocks
-// (the block-count stride of a row) covers the widest row.
+// (the block-count stride of a row) covers the widest row. wbits (may be NULL) receives, for each
+// row no wider than one symbolic window, its column bitmap (128 words per block of the row) at
+// word woff[slot], reserved from the cursor *wcur; -1 when the wcap words are used up or the row
+// is wider.
 int launch_sym_window(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                        int32_t* counter, int32_t* nnz_row, int32_t* win_slot, uint16_t* blockcnt,
                        int64_t nblocks, int32_t* cursor, const int32_t* abase, const int32_t* awidth,
-                       int64_t width, int num_sms, uint32_t* err, cudaStream_t s);
+                       int64_t width, uint32_t* wbits, int64_t wcap, unsigned long long* wcur, int64_t* woff,
+                       int num_sms, uint32_t* err, cudaStream_t s);
 
 // ---- numeric kernels, FP64 (k_numeric.cu)
 int launch_num_tiny(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
@@ -87,8 +91,8 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
                       int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
                       int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag,
-                      const int32_t* abase, const int32_t* awidth, int64_t width, int num_sms, uint32_t* err,
-                      cudaStream_t s);
+                      const int32_t* abase, const int32_t* awidth, int64_t width, const uint32_t* wbits,
+                      const int64_t* woff, int num_sms, uint32_t* err, cudaStream_t s);
 // F32-compensated rerun lists: the rows of perm[0, count) whose flag is set (all rows when
 // `all`), appended to list at list_count (a device counter)
 int launch_collect_flagged(const int32_t* perm, int64_t count, const int32_t* row_flag, int all,

@@ -166,6 +166,17 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
     p->win_slot = ws_get<int32_t>(p, m, &st);
     p->cursor = ws_get<int32_t>(p, A->nnz, &st);
     if (st) return st;
+    // room for the windowed rows' column bitmaps (one 128-word block per 4096 columns of the row),
+    // within the budget; rows that find it full keep the marking pass in the numeric kernel
+    const int64_t budget = (int64_t(p->opts.window_cols_max_mb > 0 ? p->opts.window_cols_max_mb : 0) << 20) / 4;
+    const int64_t need = nwin * p->nblocks * kBlockWords;
+    p->wcap = need < budget ? need : budget;
+    if (p->wcap > 0) {
+      p->wbits = ws_get<uint32_t>(p, p->wcap, &st);
+      p->wcur = ws_get<unsigned long long>(p, 1, &st);
+      p->woff = ws_get<int64_t>(p, nwin, &st);
+      if (st) return st;
+    }
   }
   p->state = 0;
   return SPGEMM_OK;
@@ -180,9 +191,11 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
   if (m > 0) {
     int nl;
     stage_begin(p, SPGEMM_STAGE_SYM_WINDOW, s);
+    if (p->wcur) cudaMemsetAsync(p->wcur, 0, sizeof(unsigned long long), s);
     nl = launch_sym_window(p->A, p->B, seg(kSymWin0), p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0],
                            p->counters + 0, p->nnz_row, p->win_slot, p->blockcnt, p->nblocks, p->cursor,
-                           p->abase, p->awidth, p->width, p->num_sms, err, s);
+                           p->abase, p->awidth, p->width, p->wbits, p->wcap, p->wcur, p->woff, p->num_sms, err,
+                           s);
     stage_end(p, SPGEMM_STAGE_SYM_WINDOW, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_BLOCK, s);
     nl = launch_sym_block(13, p->A, p->B, seg(kSymBlock), cnt(kSymBlock), p->nnz_row, err, p->num_sms, s);
@@ -219,7 +232,7 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
 }
 
 void plan_bytes_bounds(int64_t m, int64_t a_nnz, int64_t width, int a_rowptr32, int b_rowptr32, int64_t b_rows,
-                       int64_t b_nnz, int validate, int64_t* lo, int64_t* hi) {
+                       int64_t b_nnz, int validate, int32_t wbits_mb, int64_t* lo, int64_t* hi) {
   const int64_t ntiles = (m + kTileRows - 1) / kTileRows;
   int64_t fixed = ws_rounded(sizeof(Summary)) + ws_rounded(16 * 4) + ws_rounded(8 * m) + 3 * ws_rounded(4 * m) +
                   ws_rounded(8 * (m + 1));
@@ -228,7 +241,12 @@ void plan_bytes_bounds(int64_t m, int64_t a_nnz, int64_t width, int a_rowptr32, 
   if (validate) fixed += ws_rounded(4 * validate_words(a_nnz > b_nnz ? a_nnz : b_nnz));
   const int64_t tiles = ws_rounded(4 * ntiles * kMaxClasses) + 3 * ws_rounded(8 * ntiles);
   const int64_t nblocks = (width + kBlockCols - 1) / kBlockCols;
-  const int64_t window = ws_rounded(2 * m * nblocks) + ws_rounded(4 * m) + ws_rounded(4 * a_nnz);
+  const int64_t stored_words = wbits_mb > 0 ? (int64_t(wbits_mb) << 20) / 4 : 0;
+  const int64_t row_words = m * nblocks * kBlockWords;
+  const int64_t stored = stored_words > 0 ? ws_rounded(4 * (row_words < stored_words ? row_words : stored_words)) +
+                                                ws_rounded(8) + ws_rounded(8 * m)
+                                          : 0;
+  const int64_t window = ws_rounded(2 * m * nblocks) + ws_rounded(4 * m) + ws_rounded(4 * a_nnz) + stored;
   *lo = fixed;
   *hi = fixed + tiles + window;
 }
@@ -285,7 +303,7 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
     }
     nl += launch_num_window(mode, p->A, p->B, seg(kNumWin0), nwin, p->counters + 1, p->c_off, p->win_slot,
                             p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
-                            p->rerun_flag, p->abase, p->awidth, p->width, p->num_sms, err, s);
+                            p->rerun_flag, p->abase, p->awidth, p->width, p->wbits, p->woff, p->num_sms, err, s);
     stage_end(p, SPGEMM_STAGE_NUM_WINDOW, nl, s);
     if (!f32c) {
       double* cval = static_cast<double*>(C->val);
@@ -326,7 +344,7 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       if (e != cudaSuccess) return cuda_status(e, "reading the FP64 rerun counts");
       nl += launch_num_window(kModeF32R, p->A, p->B, list_w, hc[0], p->counters + 2, p->c_off, p->win_slot,
                               p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
-                              nullptr, p->abase, p->awidth, p->width, p->num_sms, err, s);
+                              nullptr, p->abase, p->awidth, p->width, p->wbits, p->woff, p->num_sms, err, s);
       nl += launch_num_tiny(kModeF32R, p->A, p->B, list_t, hc[1], p->c_off, C->col, C->val, nullptr, p->abase, err, p->num_sms,
                             s);
       stage_end(p, SPGEMM_STAGE_NUM_RERUN, nl, s);

@@ -55,6 +55,10 @@ struct spgemm_plan_s {
   int64_t nblocks = 0;
   int32_t* cursor = nullptr;
   int32_t* split = nullptr;          // column-block split table of B (windowed numeric rows)
+  uint32_t* wbits = nullptr;         // column bitmaps of windowed rows, stored by the symbolic pass
+  int64_t wcap = 0;                  // words wbits holds
+  unsigned long long* wcur = nullptr;   // device cursor into wbits
+  int64_t* woff = nullptr;           // per windowed row slot: its first word in wbits, or -1
   // Column space of the rows: [abase[i], abase[i] + awidth[i]) for row i of A (and B's rows start
   // at bbase[k]); width is the widest row. A single product has no bases and width = n. A batch
   // run as one block-diagonal product gives every row the columns of its own job.
@@ -98,7 +102,7 @@ int64_t numeric_extra_bytes(const spgemm_plan_s* p);
 // a_nnz entries and output rows `width` columns wide: *lo is always allocated, *hi is never
 // exceeded.
 void plan_bytes_bounds(int64_t m, int64_t a_nnz, int64_t width, int a_rowptr32, int b_rowptr32, int64_t b_rows,
-                       int64_t b_nnz, int validate, int64_t* lo, int64_t* hi);
+                       int64_t b_nnz, int validate, int32_t wbits_mb, int64_t* lo, int64_t* hi);
 // Bytes the workspace takes for a request of `bytes`.
 inline int64_t ws_rounded(int64_t bytes) { return ((bytes <= 0 ? 16 : bytes) + 255) & ~int64_t(255); }
 void stage_begin(spgemm_plan_s* p, int stage, cudaStream_t s);

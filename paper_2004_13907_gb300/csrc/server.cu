@@ -247,7 +247,7 @@ void scheduler_main(spgemm_server_s* S) {
     // bytes of the preparation from the sizes: split a group whose preparation could not fit
     // the cap, reject a job whose preparation alone is over it
     int64_t lo = 0, hi = 0;
-    batch_prepare_bounds(n, As.data(), Bs.data(), prec, S->cfg.opts.validate, &lo, &hi);
+    batch_prepare_bounds(n, As.data(), Bs.data(), prec, &S->cfg.opts, &lo, &hi);
     if (n > 1 && hi > S->cfg.mem_cap_bytes) {
       S->requeue_front(group, n / 2);
       ++S->n_splits;
@@ -518,6 +518,9 @@ extern "C" spgemm_status spgemm_server_create(const spgemm_server_cfg* cfg, spge
     return set_error_msg(SPGEMM_ERR_INVALID_ARG, "bad server configuration");
   spgemm_server_s* S = new (std::nothrow) spgemm_server_s();
   if (!S) return set_error_msg(SPGEMM_ERR_OOM, "host allocation of the server failed");
+  // the stored-column workspace of a batch counts against the cap: at most an eighth of it
+  const int64_t cols_mb = (c.mem_cap_bytes >> 20) / 8;
+  if (c.opts.window_cols_max_mb > cols_mb) c.opts.window_cols_max_mb = static_cast<int32_t>(cols_mb);
   S->cfg = c;
   S->paused = c.start_paused != 0;
   S->num_streams = c.num_streams;

@@ -69,6 +69,8 @@ def test_rmat_small_full(scale):
     dict(force_window=1, window_split_max_mb=0),
     dict(validate=0),
     dict(max_sms=7),
+    dict(force_window=1, window_cols_max_mb=0),
+    dict(force_window=1, window_cols_max_mb=1),
 ])
 def test_forced_paths_rmat(kw):
     A = synth.rmat(12, 16, seed=5)
