@@ -130,6 +130,22 @@ def _traffic(kernel_file: str, workload: str):
         return None
 
 
+def _max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks, on every rank (a step is as slow as its slowest replica)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_gflops(products_per_rank: int, ranks: int, ms: float) -> float:
+    """Whole-job GFLOP/s: every rank multiplies its own replica of the workload (2 flops per partial
+    product) in the slowest rank's time."""
+    return 2.0 * products_per_rank * ranks / (ms * 1e-3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -228,12 +244,8 @@ def run_ours(args):
 
     products_step = sum(per[n]["info"]["products"] for n, _, _ in dev)
     ms_local = float(np.mean(step_ms))
-    ms = ms_local
-    if dist:
-        t = torch.tensor([ms_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = 2.0 * products_step * ws / (ms * 1e-3) / 1e9
+    ms = _max_over_ranks(ms_local, dist, "cuda")
+    value = _job_gflops(products_step, ws, ms)
 
     # dominant kernel: the stage with the largest device time across the step
     stage_tot = {}
@@ -628,12 +640,8 @@ def run_e2e(args, mats, nnz_c, products_step, sp, torch, dist):
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     ws, _, _ = _dist()
-    t = float(np.mean(times))
-    if dist:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    return {"value": round(2.0 * products_step * ws / t / 1e9, 3), "unit": UNIT,
+    t = _max_over_ranks(float(np.mean(times)), dist, "cuda")
+    return {"value": round(_job_gflops(products_step, ws, t * 1e3), 3), "unit": UNIT,
             "h2d_bytes_per_step": int(sum(h[4] for h in hosts)),
             "d2h_bytes_per_step": int(sum(h[5] for h in hosts)),
             "ms_per_step": round(t * 1e3, 3), "host_buffers": "pinned" if pinned_ok else "pageable (pinning failed)",
