@@ -33,35 +33,36 @@ namespace spg {
 namespace {
 
 constexpr int kRankCap = 4096;                     // entries of C per window (>= kBlockCols)
-constexpr int kSpanBlocks = 64;                    // blocks a window may span (256K columns)
-constexpr int kSpanWords = kSpanBlocks * kBlockWords;    // bitmap words, 16384
 constexpr int kGroupWords = 64;                    // words per prefix group
 constexpr int kNumThreads = 512;                   // threads of the windowed numeric kernel
-constexpr int kWordsPerThread = kSpanWords / kNumThreads;
 constexpr int kCntCache = 1024;                    // block counts kept in shared memory
 constexpr int kMaxWin = 256;                       // windows planned per batch
 constexpr int kUnroll = 4;                         // partial products in flight per thread
-constexpr int kSmemBits = kSpanWords * 4;
-constexpr int kSmemPre = kSpanWords * 2;
-constexpr int kSmemGrp = (kSpanWords / kGroupWords) * 4;
 // per entry: B row start, a_ik, B row number; per non-empty segment: start, prefix, entry
 constexpr int kSmemEnt = kNumThreads * (8 + 8 + 4) + kNumThreads * (8 + 4 + 4) + 16;
 // Per rank the windowed kernel keeps an FP64 sum (kModeF64, kModeF32R) or, in kModeF32C, an FP32
-// sum, its compensation, sum|p| and the term count.
+// sum, its compensation, sum|p| and the term count. A window spans at most kSpanBlocks blocks:
+// 64 (256K columns) in FP64, 32 with the larger FP32 state, so that two blocks fit on an SM in
+// every mode.
 template <int Mode>
 struct WinGeom {
+  static constexpr int kSpanBlocks = Mode == kModeF32C ? 32 : 64;
+  static constexpr int kSpanWords = kSpanBlocks * kBlockWords;   // bitmap words
+  static constexpr int kWordsPerThread = kSpanWords / kNumThreads;
+  static constexpr int kSmemBits = kSpanWords * 4;
+  static constexpr int kSmemPre = kSpanWords * 2;
+  static constexpr int kSmemGrp = (kSpanWords / kGroupWords) * 4;
   static constexpr int kValBytes = Mode == kModeF32C ? 16 : 8;
   static constexpr int kSmemVals = kRankCap * kValBytes;
   static constexpr int kSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemGrp + kSmemEnt + kCntCache * 2 +
                                     kMaxWin * 12;
-  static constexpr int kBlocksPerSm = Mode == kModeF32C ? 1 : 2;
+  static constexpr int kBlocksPerSm = 2;
+  static_assert(kWordsPerThread * kNumThreads == kSpanWords, "words per thread");
+  static_assert(kGroupWords % kWordsPerThread == 0, "a thread's words lie in one group");
+  static_assert(kSmemVals % 16 == 0, "vector clearing of the values");
+  static_assert(2 * (kSmemBytes + 1024 + 512) <= 228 * 1024, "two blocks per SM");
 };
-constexpr int kWinSmemBytes = WinGeom<kModeF64>::kSmemBytes;
 static_assert(kRankCap >= kBlockCols, "a window must hold any single block");
-static_assert(kWordsPerThread * kNumThreads == kSpanWords, "words per thread");
-static_assert(kGroupWords % kWordsPerThread == 0, "a thread's words lie in one group");
-static_assert(2 * (kWinSmemBytes + 1024 + 512) <= 228 * 1024, "two blocks per SM");
-static_assert(WinGeom<kModeF32C>::kSmemBytes + 1024 + 512 <= 227 * 1024, "shared memory budget");
 
 
 // Split table: one warp per row k of B writes split[k * (nblocks + 1) + b] for b in
@@ -152,6 +153,12 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     void* __restrict__ cval_, int32_t* __restrict__ row_flag, const int32_t* __restrict__ abase,
     const int32_t* __restrict__ awidth, int64_t width_all, const uint32_t* __restrict__ wbits,
     const int64_t* __restrict__ woff, uint32_t* err) {
+  using G = WinGeom<Mode>;
+  constexpr int kSmemBits = G::kSmemBits;
+  constexpr int kSmemPre = G::kSmemPre;
+  constexpr int kSmemGrp = G::kSmemGrp;
+  constexpr int kSpanBlocks = G::kSpanBlocks;
+  constexpr int kWordsPerThread = G::kWordsPerThread;
   constexpr int kSmemVals = WinGeom<Mode>::kSmemVals;
   extern __shared__ __align__(16) unsigned char win_smem[];
   double* vals = reinterpret_cast<double*>(win_smem);        // kModeF64, kModeF32R
@@ -540,7 +547,7 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
                                                                ccol, cval, row_flag, abase, awidth, width, wbits,
                                                                woff, err);
   };
-  if (mode == kModeF32C) go(k_num_window<kModeF32C>, WinGeom<kModeF32C>::kSmemBytes, 1);
+  if (mode == kModeF32C) go(k_num_window<kModeF32C>, WinGeom<kModeF32C>::kSmemBytes, 2);
   else if (mode == kModeF32R) go(k_num_window<kModeF32R>, WinGeom<kModeF32R>::kSmemBytes, 2);
   else go(k_num_window<kModeF64>, WinGeom<kModeF64>::kSmemBytes, 2);
   return 1;

@@ -85,6 +85,13 @@ int launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t*
                       const int32_t* abase, uint32_t* err, int num_sms, cudaStream_t s);
 
 // ---- windowed numeric pass and the column-block split table of B (k_window.cu)
+// ---- FP64 recomputation of flagged windowed FP32 rows (k_rerun.cu): groups of group_rows rows
+// share `dense` (group_rows * width FP64), every partial product added with a global atomic.
+int64_t rerun_group_rows(int64_t width, int64_t budget_bytes);
+int launch_rerun_dense(const DevCsr& A, const DevCsr& B, const int32_t* rows, int64_t nrows, const int64_t* c_off,
+                       int32_t* ccol, float* cval, const int32_t* abase, int64_t width, double* dense,
+                       int64_t group_rows, int num_sms, uint32_t* err, cudaStream_t s);
+
 int64_t split_table_bytes(int64_t brows, int64_t nblocks);
 int launch_bsplit(const DevCsr& B, int64_t nblocks, const int32_t* bbase, int32_t* split, cudaStream_t s);
 int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,

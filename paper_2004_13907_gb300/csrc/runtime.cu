@@ -255,8 +255,11 @@ int64_t numeric_extra_bytes(const spgemm_plan_s* p) {
   const int64_t m = p->A.rows;
   if (m <= 0) return 0;
   int64_t extra = 0;
-  if (p->prec == SPGEMM_F32_COMPENSATED && !p->rerun_flag) extra += 2 * ws_rounded(4 * m);
   const int64_t nwin = p->num_off[kNumWin3 + 1] - p->num_off[kNumWin0];
+  if (p->prec == SPGEMM_F32_COMPENSATED && !p->rerun_flag) {
+    extra += 2 * ws_rounded(4 * m);
+    if (nwin > 0) extra += ws_rounded(8 * rerun_group_rows(p->width, kRerunScratchBytes) * p->width);
+  }
   if (nwin > 0 && !p->split_tried) {
     const int64_t bytes = split_table_bytes(p->B.rows, p->nblocks);
     if (bytes <= (int64_t(p->opts.window_split_max_mb) << 20)) extra += ws_rounded(bytes);
@@ -286,6 +289,10 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       if (!p->rerun_flag) {
         p->rerun_flag = ws_get<int32_t>(p, m, &st);
         p->rerun_list = ws_get<int32_t>(p, m, &st);
+        if (nwin > 0) {
+          p->rerun_group = rerun_group_rows(p->width, kRerunScratchBytes);
+          p->rerun_dense = ws_get<double>(p, p->rerun_group * p->width, &st);
+        }
         if (st) return st;
       }
       cudaMemsetAsync(p->rerun_flag, 0, sizeof(int32_t) * m, s);
@@ -342,9 +349,9 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       cudaError_t e = cudaMemcpyAsync(hc, p->counters + 4, sizeof(hc), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return cuda_status(e, "reading the FP64 rerun counts");
-      nl += launch_num_window(kModeF32R, p->A, p->B, list_w, hc[0], p->counters + 2, p->c_off, p->win_slot,
-                              p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
-                              nullptr, p->abase, p->awidth, p->width, p->wbits, p->woff, p->num_sms, err, s);
+      if (hc[0] > 0)
+        nl += launch_rerun_dense(p->A, p->B, list_w, hc[0], p->c_off, C->col, static_cast<float*>(C->val), p->abase,
+                                 p->width, p->rerun_dense, p->rerun_group, p->num_sms, err, s);
       nl += launch_num_tiny(kModeF32R, p->A, p->B, list_t, hc[1], p->c_off, C->col, C->val, nullptr, p->abase, err, p->num_sms,
                             s);
       stage_end(p, SPGEMM_STAGE_NUM_RERUN, nl, s);

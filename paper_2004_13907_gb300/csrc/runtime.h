@@ -59,6 +59,8 @@ struct spgemm_plan_s {
   int64_t wcap = 0;                  // words wbits holds
   unsigned long long* wcur = nullptr;   // device cursor into wbits
   int64_t* woff = nullptr;           // per windowed row slot: its first word in wbits, or -1
+  double* rerun_dense = nullptr;     // FP64 rows of a rerun group (FP32-compensated plans)
+  int64_t rerun_group = 0;           // rows per rerun group
   // Column space of the rows: [abase[i], abase[i] + awidth[i]) for row i of A (and B's rows start
   // at bbase[k]); width is the widest row. A single product has no bases and width = n. A batch
   // run as one block-diagonal product gives every row the columns of its own job.
@@ -95,8 +97,10 @@ T* ws_alloc(spgemm_plan_s* p, int64_t count, spgemm_status* st);
 spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s);
 spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s);
 spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s);
+// Bytes of FP64 scratch the FP32 rerun of windowed rows works in (rows of the plan's width).
+constexpr int64_t kRerunScratchBytes = int64_t(256) << 20;
 // Device bytes the numeric pass of a plan past its symbolic pass will still allocate (FP32 rerun
-// lists, the split table of B), rounded as the workspace rounds them.
+// lists and scratch, the split table of B), rounded as the workspace rounds them.
 int64_t numeric_extra_bytes(const spgemm_plan_s* p);
 // Bounds on the workspace bytes spgemm_plan and spgemm_symbolic allocate for an m-row A with
 // a_nnz entries and output rows `width` columns wide: *lo is always allocated, *hi is never
