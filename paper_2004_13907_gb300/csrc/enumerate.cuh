@@ -100,4 +100,95 @@ __device__ __forceinline__ void block_for_each_product(const DevCsr& A, const De
   }
 }
 
+// Owner of each lane's partial product in a warp-contiguous range. The non-empty segments of a
+// chunk of A entries are numbered 0..nent-1 with exclusive prefix c_excl (c_excl[nent] = total).
+// For the 32 consecutive products p0..p0+31 whose first owner is `o`, lane t looks at the
+// boundary c_excl[o + 1 + t]; the boundaries inside the group form a bit mask, and lane l's owner
+// is o plus the number of boundaries at or before position l. Segments are non-empty, so at most
+// 31 boundaries fall inside a group of 32 products.
+__device__ __forceinline__ int group_owner(const int32_t* c_excl, int nent, int o, int32_t p0) {
+  const int lane = threadIdx.x & 31;
+  const int t = o + 1 + lane;
+  const int32_t rel = (t <= nent ? c_excl[t] : 0x7fffffff) - p0;
+  const unsigned bit = (rel >= 0 && rel < 32) ? (1u << rel) : 0u;
+  const unsigned q = __reduce_or_sync(0xffffffffu, bit);
+  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  return o + __popc(q & upto);
+}
+
+// Largest o in [0, nent) with c_excl[o] <= p.
+__device__ __forceinline__ int search_owner(const int32_t* c_excl, int nent, int32_t p) {
+  int lo = 0, hi = nent - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (c_excl[mid] <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Block-wide enumeration by contiguous ranges (NT threads): for each chunk of NT A entries the
+// non-empty B rows are compacted and their products numbered; each warp takes one contiguous
+// range of the numbers and walks it 32 at a time (lane l takes number p0 + l), finding the lanes'
+// B rows with group_owner, so loads of B are coalesced along each row. f is called with U
+// indices into B (-1: none) per step, so a caller can issue its loads before using them.
+// Shared scratch: s_excl[NT + 1], s_bs[NT], s_scan64[33], s_ctl[2]. All threads call this
+// together; it ends with __syncthreads. The products of one chunk must fit int32.
+template <int NT, int U, typename F>
+__device__ __forceinline__ void block_range_for_each_product(const DevCsr& A, const DevCsr& B, int64_t a0,
+                                                             int64_t na, int32_t* s_excl, int64_t* s_bs,
+                                                             long long* s_scan64, int32_t* s_ctl, F&& f) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int kWarps = NT / 32;
+  for (int64_t base = 0; base < na; base += NT) {
+    const int64_t e = base + threadIdx.x;
+    int64_t bs = 0;
+    int32_t len = 0;
+    if (e < na) {
+      const int32_t k = A.col[a0 + e];
+      bs = B.rp[k];
+      len = static_cast<int32_t>(B.rp[k + 1] - bs);
+    }
+    const long long packed = (static_cast<long long>(len > 0) << 32) | static_cast<long long>(len);
+    long long tot;
+    const long long ex = block_excl_scan<long long>(packed, s_scan64, &tot);
+    if (len > 0) {
+      const int pos = static_cast<int>(ex >> 32);
+      s_bs[pos] = bs;
+      s_excl[pos] = static_cast<int32_t>(ex & 0xffffffffLL);
+    }
+    if (threadIdx.x == 0) {
+      const int nent = static_cast<int>(tot >> 32);
+      s_excl[nent] = static_cast<int32_t>(tot & 0xffffffffLL);
+      s_ctl[0] = nent;
+      s_ctl[1] = static_cast<int32_t>(tot & 0xffffffffLL);
+    }
+    __syncthreads();
+    const int nent = s_ctl[0];
+    const int32_t total = s_ctl[1];
+    int32_t per = (total + kWarps - 1) / kWarps;
+    per = (per + 31) & ~31;
+    const int32_t lo = wid * per;
+    const int32_t hi = total < lo + per ? total : lo + per;
+    if (lo < hi) {
+      int o = search_owner(s_excl, nent, lo);
+      for (int32_t p0 = lo; p0 < hi; p0 += 32 * U) {
+        int64_t j[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int32_t g0 = p0 + 32 * u;
+          j[u] = -1;
+          if (g0 < hi) {
+            const int my = group_owner(s_excl, nent, o, g0);
+            if (g0 + lane < hi) j[u] = s_bs[my] + (g0 + lane - s_excl[my]);
+            o = __shfl_sync(0xffffffffu, my, 31);
+          }
+        }
+        f(j);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace spg

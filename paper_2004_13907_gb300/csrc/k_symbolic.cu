@@ -191,9 +191,11 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
                                                                int64_t wcap, unsigned long long* wcur,
                                                                int64_t* __restrict__ woff, uint32_t* err) {
   extern __shared__ uint32_t bm[];  // kSymWinBits / 32 words
-  __shared__ int32_t s_excl[kSymWinThreads];
+  __shared__ int32_t s_excl[kSymWinThreads + 1];
   __shared__ int64_t s_bs[kSymWinThreads];
   __shared__ int32_t s_scan[33];
+  __shared__ long long s_scan64[33];
+  __shared__ int32_t s_ctl[2];
   __shared__ int32_t s_idx;
   __shared__ unsigned long long s_total;
   __shared__ long long s_woff;
@@ -224,12 +226,22 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
       for (int t = threadIdx.x; t < nwords; t += kSymWinThreads) bm[t] = 0u;
       __syncthreads();
       if (width <= kSymWinBits) {
-        // one window covers every column: no cursors, products handed out flattened
-        block_for_each_product<kSymWinThreads>(A, B, a0, na, s_excl, s_bs, s_scan, [&](int64_t j, int64_t) {
-          const int64_t rel = B.col[j] - w0;
-          if (rel >= 0 && rel < wend - w0) atomicOr(&bm[rel >> 5], 1u << (rel & 31));
-          else set_error(err, kErrWindowPlan);
-        });
+        // one window covers every column: no cursors; each warp marks a contiguous range of the
+        // row's products (four groups of 32 loaded before they are marked)
+        const int64_t span = wend - w0;
+        block_range_for_each_product<kSymWinThreads, 4>(
+            A, B, a0, na, s_excl, s_bs, s_scan64, s_ctl, [&](const int64_t (&j)[4]) {
+              int32_t c[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) c[u] = j[u] >= 0 ? B.col[j[u]] : 0;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if (j[u] < 0) continue;
+                const int64_t rel = c[u] - w0;
+                if (rel >= 0 && rel < span) atomicOr(&bm[rel >> 5], 1u << (rel & 31));
+                else set_error(err, kErrWindowPlan);
+              }
+            });
       } else {
         for (int64_t e = wid; e < na; e += kWarps) {
           const int32_t k = A.col[a0 + e];

@@ -106,33 +106,6 @@ __device__ __forceinline__ int32_t lower_bound_col(const int32_t* col, int32_t l
   return lo;
 }
 
-// Owner of each lane's partial product in a warp-contiguous range. The non-empty segments of a
-// chunk of A entries are numbered 0..nent-1 with exclusive prefix c_excl (c_excl[nent] = total).
-// For the 32 consecutive products p0..p0+31 whose first owner is `o`, lane t looks at the
-// boundary c_excl[o + 1 + t]; the boundaries inside the group form a bit mask, and lane l's owner
-// is o plus the number of boundaries at or before position l. Segments are non-empty, so at most
-// 31 boundaries fall inside a group of 32 products.
-__device__ __forceinline__ int group_owner(const int32_t* c_excl, int nent, int o, int32_t p0) {
-  const int lane = threadIdx.x & 31;
-  const int t = o + 1 + lane;
-  const int32_t rel = (t <= nent ? c_excl[t] : 0x7fffffff) - p0;
-  const unsigned bit = (rel >= 0 && rel < 32) ? (1u << rel) : 0u;
-  const unsigned q = __reduce_or_sync(0xffffffffu, bit);
-  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-  return o + __popc(q & upto);
-}
-
-// Largest o in [0, nent) with c_excl[o] <= p.
-__device__ __forceinline__ int search_owner(const int32_t* c_excl, int nent, int32_t p) {
-  int lo = 0, hi = nent - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (c_excl[mid] <= p) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 // Shared layout (dynamic): rank-indexed FP64 values [kRankCap] (also the staging buffer of
 // the window's columns during the write-out); window bitmap [kSpanWords]; in-group word prefix
 // (uint16) [kSpanWords]; group prefix (int32) [kSpanWords / 64]; per-entry state of the current
