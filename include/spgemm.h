@@ -102,7 +102,7 @@ typedef struct spgemm_opts {
   int32_t warp_max;           /* symbolic: rows with min(P_i, n) <= this use a warp table;
                                  numeric: rows with nnz(C_i) <= warp_max/2 (default 1024) */
   int32_t block_max;          /* rows up to this size use a block-wide hash table; larger
-                                 rows take the windowed path (default 4096) */
+                                 rows take the windowed path (default 2048, at most 4096) */
   int32_t window_hash_fill;   /* windowed rows: consecutive column blocks are merged into one
                                  window while it holds at most this many entries of C (default
                                  and maximum 4096; a single block is always one window) */

@@ -137,7 +137,7 @@ void spgemm_opts_default(spgemm_opts* o) {
   o->validate = 1;
   o->tiny_max = 32;
   o->warp_max = 1024;
-  o->block_max = 4096;
+  o->block_max = 2048;
   o->window_hash_fill = 4096;
   o->force_window = 0;
   o->rowptr32_limit = 0x7fffffffLL;

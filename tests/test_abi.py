@@ -76,7 +76,7 @@ def test_opts_default_without_gpu(lib):
     from paper_2004_13907_gb300 import _native
     o = _native.Opts()
     lib.spgemm_opts_default(ctypes.byref(o))
-    assert o.validate == 1 and o.tiny_max == 32 and o.block_max == 4096
+    assert o.validate == 1 and o.tiny_max == 32 and o.block_max == 2048
     assert o.rowptr32_limit == 2**31 - 1
 
 
