@@ -314,20 +314,21 @@ spgemm_status spgemm_multiply_noalloc(const spgemm_csr_in* A, const spgemm_csr_i
 
 /* ---- Serving: a long-lived server that takes products one at a time, from any host thread, and
  * runs them in fused batches (continuous batching). The paper has no counterpart; this is the
- * library's serving layer over the batched product above.
- * A scheduler thread gathers queued jobs in arrival order (up to max_batch_jobs, or until the
- * jobs' input entries reach max_batch_entries; it waits up to batch_window_us after the oldest
- * queued job arrived for more to come; small jobs may overtake a large one for up to
- * max_defer_ms), stacks them as spgemm_batch does and runs the plan and symbolic pass. That pass gives the EXACT device bytes of the batch (stacked inputs, plan
- * workspace, numeric tables and output); the numeric pass starts only when the bytes held by
- * the server plus that figure fit mem_cap_bytes, else it waits for running batches to finish or
- * for results to be released. A batch that does not fit the cap even alone is split in halves;
- * a single job that does not fit alone is REJECTED. A batch whose preparation fails is retried
- * job by job, so one bad job fails alone. Up to num_streams batches are in flight, each on a
- * stream of its own, so one batch's symbolic pass overlaps another's numeric pass. Completion
- * is signalled by a host callback on the batch's stream; a job's latency runs from its submit
- * call until it is marked done. Results stay in device memory, counted against the cap, until
- * spgemm_server_release. Every call is thread-safe. */
+ * library's serving layer over the batched product above. A scheduler thread gathers queued jobs
+ * in arrival order (up to max_batch_jobs, or until the jobs' input entries reach
+ * max_batch_entries; it waits up to batch_window_us after the oldest queued job arrived for more
+ * to come; small jobs may overtake a large one for up to max_defer_ms), stacks them as
+ * spgemm_batch does and runs the plan and symbolic pass. That pass gives the EXACT device bytes of
+ * the batch (stacked inputs, plan workspace, numeric tables and output); the numeric pass starts
+ * only when the bytes held by the server plus that figure fit mem_cap_bytes, else it waits for
+ * running batches to finish or for results to be released. A batch that does not fit the cap even
+ * alone is split in halves; a single job that does not fit alone runs as row panels into a pinned
+ * host result (host_panels), or is REJECTED when host_panels is 0 or a single row does not fit. A
+ * batch whose preparation fails is retried job by job, so one bad job fails alone. Up to
+ * num_streams batches are in flight, each on a stream of its own, so one batch's symbolic pass
+ * overlaps another's numeric pass. Completion is signalled by a host callback on the batch's
+ * stream; a job's latency runs from its submit call until it is marked done. Results stay in
+ * device memory, counted against the cap, until spgemm_server_release. Every call is thread-safe. */
 typedef struct spgemm_server_s spgemm_server_t;
 
 typedef struct {
@@ -351,6 +352,10 @@ typedef struct {
                                   order) */
   int32_t max_defer_ms;        /* longest a large job at the head of the queue is overtaken
                                   (default 250) */
+  int32_t host_panels;         /* 1 (default): a single job over the cap runs as row panels, each
+                                  under a quarter of the cap, into a result in pinned host memory;
+                                  0: such a job is REJECTED */
+  int32_t reserved_[3];
   spgemm_opts opts;            /* options of each batch's plan */
 } spgemm_server_cfg;
 
@@ -374,6 +379,8 @@ typedef struct {
   double queue_ms;             /* submit -> its batch started preparing */
   double run_ms;               /* batch start -> done */
   double latency_ms;           /* submit -> done */
+  int64_t panels;              /* row panels of a job run over the cap (0: none) */
+  int64_t result_on_host;      /* 1: spgemm_server_result gives host pointers (row panels) */
 } spgemm_job_info;
 
 typedef struct {
@@ -416,8 +423,9 @@ spgemm_status spgemm_server_poll(spgemm_server_t* server, int64_t job, spgemm_jo
 spgemm_status spgemm_server_wait(spgemm_server_t* server, int64_t job, double timeout_s,
                                  spgemm_job_info* info);
 
-/* A done job's result as a standalone CSR view (device pointers, int64 row_ptr from 0),
- * valid until spgemm_server_release of that job. NOT_READY before it is done. */
+/* A done job's result as a standalone CSR view (int64 row_ptr from 0), valid until
+ * spgemm_server_release of that job: device pointers, or pinned host pointers for a job that ran
+ * as row panels (spgemm_job_info.result_on_host). NOT_READY before it is done. */
 spgemm_status spgemm_server_result(spgemm_server_t* server, int64_t job, spgemm_csr_out* C);
 
 /* Forgets a finished job. Its result memory returns to the budget once every job of its batch

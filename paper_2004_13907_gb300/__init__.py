@@ -415,10 +415,23 @@ class Server:
         return _job_dict(info)
 
     def result(self, job: int) -> DeviceCSR:
-        """View of a done job's result (valid until ``release``)."""
+        """View of a done job's result (valid until ``release``): device tensors, or CPU tensors over
+        pinned host memory for a job the server ran as row panels (over its memory cap)."""
+        info = self.poll(job)
         c = _native.CsrOut()
         _native.check(lib().spgemm_server_result(self.handle, job, ctypes.byref(c)))
         vdt = _vdtype(self.prec)
+        if info["result_on_host"]:
+            import numpy as np
+
+            def host(ptr, n, ctype):
+                if n == 0:
+                    return torch.empty(0, dtype={ctypes.c_int64: torch.int64, ctypes.c_int32: torch.int32,
+                                                 ctypes.c_double: torch.float64, ctypes.c_float: torch.float32}[ctype])
+                return torch.from_numpy(np.ctypeslib.as_array((ctype * n).from_address(ptr)))
+            vct = ctypes.c_double if self.prec == F64 else ctypes.c_float
+            return DeviceCSR(int(c.rows), int(c.cols), host(c.row_ptr, c.rows + 1, ctypes.c_int64),
+                             host(c.col, c.nnz, ctypes.c_int32), host(c.val, c.nnz, vct))
         return DeviceCSR(int(c.rows), int(c.cols), _view(c.row_ptr, c.rows + 1, torch.int64, self.device),
                          _view(c.col, c.nnz, torch.int32, self.device), _view(c.val, c.nnz, vdt, self.device))
 

@@ -75,7 +75,8 @@ class Timings(ctypes.Structure):
 class ServerCfg(ctypes.Structure):
     _fields_ = [("mem_cap_bytes", c_i64), ("max_batch_entries", c_i64), ("max_batch_jobs", c_i32),
                 ("batch_window_us", c_i32), ("num_streams", c_i32), ("start_paused", c_i32), ("prec", c_i32),
-                ("reserve_sms", c_i32), ("small_products", c_i32), ("max_defer_ms", c_i32), ("opts", Opts)]
+                ("reserve_sms", c_i32), ("small_products", c_i32), ("max_defer_ms", c_i32), ("host_panels", c_i32),
+                ("reserved_", c_i32 * 3), ("opts", Opts)]
 
 
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "rejected"}
@@ -84,7 +85,8 @@ JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "rejected"}
 class JobInfo(ctypes.Structure):
     _fields_ = [("state", c_i32), ("status", c_i32), ("batch", c_i64), ("batch_jobs", c_i64), ("rows", c_i64),
                 ("cols", c_i64), ("nnz", c_i64), ("bytes", c_i64), ("needed_bytes", c_i64),
-                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("panels", c_i64), ("result_on_host", c_i64)]
 
 
 class ServerStats(ctypes.Structure):

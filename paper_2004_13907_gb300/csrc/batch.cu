@@ -341,6 +341,15 @@ void batch_set_release_stream(spgemm_batch_t* b, void* stream) {
 
 int64_t batch_products(const spgemm_batch_t* b) { return b->plan ? b->plan->total_products : 0; }
 
+spgemm_status batch_row_offsets(const spgemm_batch_t* b, int64_t* host_off, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(host_off, b->plan->c_off, sizeof(int64_t) * (b->rows + 1), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? SPGEMM_OK : cuda_status(e, "reading the batch row offsets");
+}
+
+int64_t batch_rows(const spgemm_batch_t* b) { return b->rows; }
+
 int64_t batch_jobs(const spgemm_batch_t* b) { return b->n_jobs; }
 
 spgemm_status batch_execute(spgemm_batch_t* b, void* stream) {

@@ -21,6 +21,9 @@ int64_t batch_output_bytes(const spgemm_batch_t* b);
 // numeric pass's own tables and the output.
 int64_t batch_needed_bytes(const spgemm_batch_t* b);
 int64_t batch_products(const spgemm_batch_t* b);
+int64_t batch_rows(const spgemm_batch_t* b);
+// Row offsets of the stacked C (rows + 1 int64) after the symbolic pass, read to the host.
+spgemm_status batch_row_offsets(const spgemm_batch_t* b, int64_t* host_off, void* stream);
 int64_t batch_nnz(const spgemm_batch_t* b);
 // Stream on which the batch's memory is handed back to the pool when it is destroyed.
 void batch_set_release_stream(spgemm_batch_t* b, void* stream);

@@ -14,6 +14,15 @@ namespace spg {
 
 namespace {
 
+// Row pointers of rows [r0, r0 + n1 - 1) of a CSR matrix, rebased to start at 0 (int64).
+__global__ void k_rowptr_rebase(const void* __restrict__ in, int idx64, int64_t r0, int64_t n1, int64_t base,
+                                int64_t* __restrict__ out) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n1; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t v = idx64 ? static_cast<const int64_t*>(in)[r0 + t] : static_cast<const int32_t*>(in)[r0 + t];
+    out[t] = v - base;
+  }
+}
+
 __global__ void k_rowptr_to64(const int32_t* __restrict__ in, int64_t* __restrict__ out, int64_t n1) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n1;
        i += int64_t(gridDim.x) * blockDim.x)
@@ -320,6 +329,13 @@ inline unsigned grid_for(int64_t n, int threads, int64_t cap = 65535LL * 16) {
 }
 
 }  // namespace
+
+int launch_rowptr_rebase(const void* in, int idx64, int64_t r0, int64_t n1, int64_t base, int64_t* out,
+                         cudaStream_t s) {
+  if (n1 <= 0) return 0;
+  k_rowptr_rebase<<<grid_for(n1, 256), 256, 0, s>>>(in, idx64, r0, n1, base, out);
+  return 1;
+}
 
 int launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t s) {
   k_rowptr_to64<<<grid_for(n1, 256), 256, 0, s>>>(in, out, n1);

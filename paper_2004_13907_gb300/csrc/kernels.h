@@ -30,6 +30,9 @@ struct Summary {
 
 // ---- setup / scan kernels (k_setup.cu)
 int launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t s);
+// out[t] = in[r0 + t] - base for t < n1 (in: int32 or int64 row pointers).
+int launch_rowptr_rebase(const void* in, int idx64, int64_t r0, int64_t n1, int64_t base, int64_t* out,
+                         cudaStream_t s);
 // starts: scratch of validate_words(M.nnz) words (the row-start bitmap).
 int64_t validate_words(int64_t nnz);
 int launch_validate(const DevCsr& M, uint32_t* starts, uint32_t* err, cudaStream_t s);

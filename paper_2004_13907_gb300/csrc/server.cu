@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <string>
@@ -51,7 +52,21 @@ struct Job {
   int64_t batch_jobs = 0;
   int64_t nnz = 0, bytes = 0, needed = 0;
   Clock::time_point t_submit, t_start, t_done;
+  // a job over the cap runs as row panels and its result lives in pinned host memory
+  int64_t panels = 0;
+  int64_t* host_rp = nullptr;
+  int32_t* host_col = nullptr;
+  void* host_val = nullptr;
 };
+
+void free_host_result(Job& j) {
+  if (j.host_rp) cudaFreeHost(j.host_rp);
+  if (j.host_col) cudaFreeHost(j.host_col);
+  if (j.host_val) cudaFreeHost(j.host_val);
+  j.host_rp = nullptr;
+  j.host_col = nullptr;
+  j.host_val = nullptr;
+}
 
 struct BatchRec {
   spgemm_batch_t* b = nullptr;
@@ -204,6 +219,166 @@ void destroy_batch(spgemm_server_s* S, spgemm_batch_t* b) {
   spgemm_batch_destroy(b);
 }
 
+// Device bytes of one panel: its plan's workspace and its output.
+int64_t charged_need(spgemm_plan_t* p, int64_t prow, int64_t pnnz, int vb) {
+  spgemm_plan_info info{};
+  spgemm_plan_get_info(p, &info);
+  return info.workspace_bytes + ws_rounded(8 * (prow + 1)) + ws_rounded(4 * pnnz) + ws_rounded(int64_t(vb) * pnnz);
+}
+
+// Runs a single job whose exact bytes exceed the cap as row panels: rows are cut where a panel's
+// output (known exactly from the job's symbolic pass, `off`) reaches a quarter of the cap; each
+// panel is its own product on A's rows [r0, r1) (row pointers rebased on the device) and B, charged
+// to the cap while it runs, and copied into a pinned host result. Called and returns with the
+// lock held; finishes the job.
+void run_panels(spgemm_server_s* S, int64_t id, const std::vector<int64_t>& off, cudaStream_t stream,
+                std::unique_lock<std::mutex>& lk) {
+  Job& j = S->jobs.at(id);
+  const spgemm_csr_in A = j.A, B = j.B;
+  const spgemm_prec prec = static_cast<spgemm_prec>(S->cfg.prec);
+  const spgemm_opts opts = S->cfg.opts;
+  const int64_t cap = S->cfg.mem_cap_bytes;
+  const int vb = prec == SPGEMM_F64 ? 8 : 4;
+  const int64_t rows = A.rows, nnz = off[rows];
+  lk.unlock();
+  spgemm_status st = SPGEMM_OK;
+  std::string msg;
+  auto fail = [&](spgemm_status code, const char* what) {
+    if (st == SPGEMM_OK) {
+      st = code;
+      msg = std::string(what) + ": " + spgemm_last_error();
+    }
+  };
+  int64_t* hrp = nullptr;
+  int32_t* hcol = nullptr;
+  void* hval = nullptr;
+  if (cudaMallocHost(&hrp, sizeof(int64_t) * (rows + 1)) != cudaSuccess ||
+      cudaMallocHost(&hcol, sizeof(int32_t) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
+      cudaMallocHost(&hval, size_t(vb) * (nnz > 0 ? nnz : 1)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error_msg(SPGEMM_ERR_OOM, "pinned host memory for the result (%lld entries)", (long long)nnz);
+    fail(SPGEMM_ERR_OOM, "row panels");
+  }
+  std::vector<int64_t> arp(static_cast<size_t>(rows) + 1);
+  if (st == SPGEMM_OK) {
+    std::memcpy(hrp, off.data(), sizeof(int64_t) * (rows + 1));
+    cudaError_t e;
+    if (A.idx64_rowptr) {
+      e = cudaMemcpyAsync(arp.data(), A.row_ptr, sizeof(int64_t) * (rows + 1), cudaMemcpyDeviceToHost, stream);
+    } else {
+      std::vector<int32_t> t(static_cast<size_t>(rows) + 1);
+      e = cudaMemcpyAsync(t.data(), A.row_ptr, sizeof(int32_t) * (rows + 1), cudaMemcpyDeviceToHost, stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      for (int64_t r = 0; r <= rows; ++r) arp[r] = t[r];
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) fail(cuda_status(e, "reading A's row pointers"), "row panels");
+  }
+  const int64_t budget = cap / 4;
+  int64_t npanels = 0;
+  for (int64_t r0 = 0; r0 < rows && st == SPGEMM_OK; ++npanels) {
+    int64_t r1 = r0 + 1;
+    while (r1 < rows && (off[r1 + 1] - off[r0]) * (4 + vb) + 8 * (r1 + 1 - r0) <= budget) ++r1;
+    const int64_t prow = r1 - r0, base = arp[r0], pnnz = off[r1] - off[r0];
+    int64_t* drp = nullptr;
+    int64_t* dout_rp = nullptr;
+    int32_t* dcol = nullptr;
+    void* dval = nullptr;
+    spgemm_plan_t* p = nullptr;
+    int64_t charged = 0;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&drp), sizeof(int64_t) * (prow + 1), stream);
+    if (e == cudaSuccess) {
+      launch_rowptr_rebase(A.row_ptr, A.idx64_rowptr, r0, prow + 1, base, drp, stream);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) fail(cuda_status(e, "rebasing a panel's row pointers"), "row panels");
+    spgemm_csr_in Ap{prow, A.cols, arp[r1] - base, 1, 0, drp, A.col + base,
+                     static_cast<const unsigned char*>(A.val) + size_t(vb) * base};
+    if (st == SPGEMM_OK && spgemm_plan(&Ap, &B, prec, &opts, nullptr, stream, &p) != SPGEMM_OK)
+      fail(SPGEMM_ERR_INVALID_CSR, "panel plan");
+    int64_t got = 0;
+    if (st == SPGEMM_OK && spgemm_symbolic(p, stream, &got, nullptr) != SPGEMM_OK)
+      fail(SPGEMM_ERR_INTERNAL, "panel symbolic");
+    if (st == SPGEMM_OK && got != pnnz) {
+      set_error_msg(SPGEMM_ERR_INTERNAL, "panel rows [%lld, %lld) have %lld entries, expected %lld", (long long)r0,
+                    (long long)r1, (long long)got, (long long)pnnz);
+      fail(SPGEMM_ERR_INTERNAL, "row panels");
+    }
+    if (st == SPGEMM_OK && charged_need(p, prow, pnnz, vb) > cap) {
+      {   // a panel (a single row, since panels stop at a quarter of the cap) does not fit the cap
+        const int64_t need = charged_need(p, prow, pnnz, vb);
+        set_error_msg(SPGEMM_ERR_REJECTED, "rows [%lld, %lld) need %lld device bytes, over the server's cap of %lld",
+                      (long long)r0, (long long)r1, (long long)need, (long long)cap);
+        fail(SPGEMM_ERR_REJECTED, "row panels");
+      }
+    }
+    if (st == SPGEMM_OK) {
+      const int64_t need = charged_need(p, prow, pnnz, vb);
+      lk.lock();
+      S->cv_sched.wait(lk, [&] { return S->stop || S->in_use == 0 || S->in_use + need <= cap; });
+      const bool stopped = S->stop;
+      if (!stopped) {
+        S->charge(need);
+        charged = need;
+      }
+      lk.unlock();
+      if (stopped) {
+        set_error_msg(SPGEMM_ERR_INVALID_ARG, "server stopped");
+        fail(SPGEMM_ERR_INVALID_ARG, "row panels");
+      }
+    }
+    if (st == SPGEMM_OK) {
+      e = cudaMallocAsync(reinterpret_cast<void**>(&dout_rp), sizeof(int64_t) * (prow + 1), stream);
+      if (e == cudaSuccess)
+        e = cudaMallocAsync(reinterpret_cast<void**>(&dcol), sizeof(int32_t) * (pnnz > 0 ? pnnz : 1), stream);
+      if (e == cudaSuccess) e = cudaMallocAsync(&dval, size_t(vb) * (pnnz > 0 ? pnnz : 1), stream);
+      if (e != cudaSuccess) fail(cuda_status(e, "allocating a panel's output"), "row panels");
+    }
+    if (st == SPGEMM_OK) {
+      spgemm_csr_out Cp{prow, B.cols, pnnz, 1, 0, dout_rp, dcol, dval};
+      if (spgemm_numeric(p, &Cp, stream) != SPGEMM_OK || spgemm_plan_check(p, stream) != SPGEMM_OK)
+        fail(SPGEMM_ERR_INTERNAL, "panel numeric");
+    }
+    if (st == SPGEMM_OK && pnnz > 0) {
+      e = cudaMemcpyAsync(hcol + off[r0], dcol, sizeof(int32_t) * pnnz, cudaMemcpyDeviceToHost, stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<unsigned char*>(hval) + size_t(vb) * off[r0], dval, size_t(vb) * pnnz,
+                            cudaMemcpyDeviceToHost, stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) fail(cuda_status(e, "copying a panel to the host"), "row panels");
+    }
+    cudaStreamSynchronize(stream);
+    if (p) spgemm_plan_destroy(p);
+    if (dval) cudaFreeAsync(dval, stream);
+    if (dcol) cudaFreeAsync(dcol, stream);
+    if (dout_rp) cudaFreeAsync(dout_rp, stream);
+    if (drp) cudaFreeAsync(drp, stream);
+    cudaStreamSynchronize(stream);
+    if (charged) {
+      lk.lock();
+      S->in_use -= charged;
+      lk.unlock();
+      S->cv_sched.notify_all();
+    }
+    r0 = r1;
+  }
+  lk.lock();
+  if (st != SPGEMM_OK) {
+    if (hrp) cudaFreeHost(hrp);
+    if (hcol) cudaFreeHost(hcol);
+    if (hval) cudaFreeHost(hval);
+    S->finish_job(id, st == SPGEMM_ERR_REJECTED ? SPGEMM_JOB_REJECTED : SPGEMM_JOB_FAILED, st, msg, Clock::now());
+    return;
+  }
+  j.host_rp = hrp;
+  j.host_col = hcol;
+  j.host_val = hval;
+  j.panels = npanels;
+  j.nnz = nnz;
+  j.bytes = 0;   // the result holds no device memory
+  S->finish_job(id, SPGEMM_JOB_DONE, SPGEMM_OK, "", Clock::now());
+}
+
 void scheduler_main(spgemm_server_s* S) {
   cudaSetDevice(S->device);
   const spgemm_prec prec = static_cast<spgemm_prec>(S->cfg.prec);
@@ -323,15 +498,29 @@ void scheduler_main(spgemm_server_s* S) {
     S->charge(dev);
     for (int64_t id : group) S->jobs.at(id).needed = need;
     if (need > S->cfg.mem_cap_bytes) {
-      // does not fit even alone: split, or reject a single job
+      // does not fit even alone: split, run a single job as row panels, or reject it
+      const bool paneled = n == 1 && S->cfg.host_panels != 0;
+      std::vector<int64_t> off;
+      spgemm_status ost = SPGEMM_OK;
+      if (paneled) {
+        off.resize(static_cast<size_t>(batch_rows(b)) + 1);
+        lk.unlock();
+        ost = batch_row_offsets(b, off.data(), stream);
+        lk.lock();
+      }
       S->in_use -= dev;
-      give_up_slot();
+      if (!paneled) give_up_slot();
       lk.unlock();
       destroy_batch(S, b);
       lk.lock();
       if (n > 1) {
         S->requeue_front(group, n / 2);
         ++S->n_splits;
+      } else if (paneled) {
+        if (ost == SPGEMM_OK) run_panels(S, group[0], off, stream, lk);
+        else S->finish_job(group[0], SPGEMM_JOB_FAILED, ost, spgemm_last_error(), Clock::now());
+        give_up_slot();
+        S->cv_wait.notify_all();
       } else {
         char buf[160];
         std::snprintf(buf, sizeof(buf), "the job needs %lld device bytes, over the server's cap of %lld",
@@ -462,6 +651,8 @@ void fill_info(const spgemm_server_s* S, const Job& j, spgemm_job_info* info) {
   info->queue_ms = ms_between(j.t_submit, started ? j.t_start : now);
   info->run_ms = started ? ms_between(j.t_start, is_final(j.state) ? j.t_done : now) : 0.0;
   info->latency_ms = ms_between(j.t_submit, is_final(j.state) ? j.t_done : now);
+  info->panels = j.panels;
+  info->result_on_host = j.host_rp != nullptr;
   (void)S;
 }
 
@@ -499,6 +690,7 @@ extern "C" spgemm_status spgemm_server_cfg_default(spgemm_server_cfg* cfg) {
   cfg->reserve_sms = 0;
   cfg->small_products = 1 << 26;
   cfg->max_defer_ms = 250;
+  cfg->host_panels = 1;
   spgemm_opts_default(&cfg->opts);
   return SPGEMM_OK;
 }
@@ -619,6 +811,10 @@ extern "C" spgemm_status spgemm_server_result(spgemm_server_t* S, int64_t job, s
   if (it == S->jobs.end()) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "unknown job %lld", (long long)job);
   const Job& j = it->second;
   if (j.state != SPGEMM_JOB_DONE) return final_status(j);
+  if (j.host_rp) {   // row-paneled job: the result is in pinned host memory
+    *C = spgemm_csr_out{j.A.rows, j.B.cols, j.nnz, 1, 0, j.host_rp, j.host_col, j.host_val};
+    return SPGEMM_OK;
+  }
   return spgemm_batch_result(S->batches.at(j.batch).b, j.index, C);
 }
 
@@ -632,6 +828,7 @@ extern "C" spgemm_status spgemm_server_release(spgemm_server_t* S, int64_t job) 
     if (it == S->jobs.end()) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "unknown job %lld", (long long)job);
     if (!is_final(it->second.state)) return set_error_msg(SPGEMM_ERR_NOT_READY, "job %lld has not finished", (long long)job);
     const int64_t bid = it->second.batch;
+    free_host_result(it->second);
     S->jobs.erase(it);
     if (bid >= 0) {
       BatchRec& rec = S->batches.at(bid);
@@ -745,6 +942,7 @@ extern "C" spgemm_status spgemm_server_destroy(spgemm_server_t* S) {
     std::lock_guard<std::mutex> g(S->mu);
     for (auto& kv : S->batches) destroy_batch(S, kv.second.b);
     S->batches.clear();
+    for (auto& kv : S->jobs) free_host_result(kv.second);
     S->jobs.clear();
     S->pending.clear();
   }

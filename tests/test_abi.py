@@ -109,7 +109,7 @@ def test_server_config_checks_on_host(lib):
     assert cfg.mem_cap_bytes == 32 << 30 and cfg.num_streams == 2 and cfg.prec == 0
     assert cfg.opts.validate == 1 and cfg.opts.window_hash_fill == 4096
     assert cfg.reserve_sms == 0 and cfg.opts.max_sms == 0
-    assert cfg.small_products == 1 << 26 and cfg.max_defer_ms == 250
+    assert cfg.small_products == 1 << 26 and cfg.max_defer_ms == 250 and cfg.host_panels == 1
     h = ctypes.c_void_p()
     for field, bad in [("num_streams", 0), ("num_streams", 9), ("mem_cap_bytes", 0), ("max_batch_jobs", 0),
                        ("prec", 7), ("batch_window_us", -1), ("reserve_sms", -1), ("small_products", -1), ("max_defer_ms", -1)]:

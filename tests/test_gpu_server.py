@@ -124,7 +124,7 @@ def test_admission_splits_batches_and_rejects_oversized_jobs():
     dbigB = sp.DeviceCSR.from_host(synth.uniform_random(16, 1500, 0.9, seed=72), "cuda")
     # inputs alone over the cap: rejected from its sizes, before any device work
     dhuge = sp.DeviceCSR.from_host(synth.uniform_random(20_000, 20_000, 1e-3, seed=73), "cuda")
-    with sp.Server(mem_cap_bytes=cap, start_paused=1, batch_window_us=50_000) as srv:
+    with sp.Server(mem_cap_bytes=cap, start_paused=1, batch_window_us=50_000, host_panels=0) as srv:
         ids = [srv.submit(dA, dB) for dA, dB in dev]
         jbig = srv.submit(dbig, dbigB)
         jhuge = srv.submit(dhuge, dhuge)
@@ -236,3 +236,33 @@ def test_small_jobs_overtake_a_large_one_for_a_bounded_time():
                 assert all(x["batch"] > ib["batch"] for x in iss)
             for (A, B), (a, b), j in zip(smalls, dsm, js):
                 _same_as_alone(A, B, srv.result(j), sp.multiply(a, b))
+
+
+def test_job_over_the_cap_runs_as_row_panels():
+    """A job whose exact size exceeds the cap runs as row panels, each under a quarter of the cap,
+    into a pinned host result equal to the oracle's product; device memory never exceeds the cap."""
+    import paper_2004_13907_gb300 as sp
+    A = synth.uniform_random(1500, 16, 0.9, seed=120)
+    B = synth.uniform_random(16, 1500, 0.9, seed=121)
+    dA, dB = sp.DeviceCSR.from_host(A, "cuda"), sp.DeviceCSR.from_host(B, "cuda")
+    cap = 6 << 20          # the product's output alone is about 27 MB
+    small = synth.batch_job(0, seed=122, n_lo=300, n_hi=400)
+    ds = (sp.DeviceCSR.from_host(small[0], "cuda"), sp.DeviceCSR.from_host(small[1], "cuda"))
+    with sp.Server(mem_cap_bytes=cap) as srv:
+        j = srv.submit(dA, dB)
+        js = srv.submit(*ds)
+        inf = srv.wait(j, timeout=300)
+        assert inf["state"] == "done" and inf["result_on_host"] == 1 and inf["panels"] > 4
+        C = srv.result(j)
+        assert C.col.device.type == "cpu"
+        ref = oracle.spgemm(A, B)
+        assert np.array_equal(C.row_ptr.numpy(), ref.row_ptr)
+        assert np.array_equal(C.col.numpy(), ref.col)
+        assert np.all(np.abs(C.val.numpy() - ref.val) <= 1e-12 * ref.mag)
+        srv.wait(js, timeout=60)
+        _same_as_alone(*small, srv.result(js), sp.multiply(*ds))
+        st = srv.stats()
+        assert st["bytes_peak"] <= cap and st["completed"] == 2
+        srv.release(j)
+        srv.release(js)
+        assert srv.stats()["bytes_in_use"] == 0
