@@ -154,9 +154,10 @@ def _dist():
 
 
 def _window_bytes(info: dict) -> tuple:
-    """Algorithmic bytes of the windowed numeric kernel's launch: per row 8 (its A row
-    pointers), per A entry 12 (column, value) + 8 (start and end of the named B row), per
-    partial product 12 (the gathered B column and value), per entry of C 12 (column, value)."""
+    """Algorithmic bytes of the windowed numeric pass (k_num_window, and k_expand_cols for the
+    columns of rows whose bitmap the symbolic pass stored): per row 8 (its A row pointers), per
+    A entry 12 (column, value) + 8 (start and end of the named B row), per partial product 12
+    (the gathered B column and value), per entry of C 12 (column, value)."""
     rows = sum(info["num_class_rows"][0:4])
     annz = sum(info["num_class_annz"][0:4])
     prods = sum(info["num_class_products"][0:4])
@@ -247,18 +248,21 @@ def run_ours(args):
     ms = _max_over_ranks(ms_local, dist, "cuda")
     value = _job_gflops(products_step, ws, ms)
 
-    # dominant kernel: the stage with the largest device time across the step
+    # dominant kernel: the stage with the largest device time across the step (the windowed
+    # numeric pass counts with the column expansion that completes its output)
     stage_tot = {}
     for name, d in per.items():
         for k, v in d["stages"].items():
-            stage_tot[(name, k)] = float(np.mean(v))
+            key = "num_window" if k == "num_expand" else k
+            stage_tot[(name, key)] = stage_tot.get((name, key), 0.0) + float(np.mean(v))
     (dom_mat, dom_stage), dom_ms = max(stage_tot.items(), key=lambda kv: kv[1])
     peak, peak_kind = _peaks()
     roof = None
     if dom_stage == "num_window":
         bytes_, _ = _window_bytes(per[dom_mat]["info"])
         achieved = bytes_ / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": f"k_num_window ({dom_mat})", "achieved": round(achieved, 1),
+        roof = {"bound": "hbm", "kernel": f"k_num_window + k_expand_cols ({dom_mat})",
+                "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": bytes_,
                 "launch_ms": round(dom_ms, 4), "traffic": _traffic("k_window.cu", args.workload)}
@@ -271,7 +275,8 @@ def run_ours(args):
             "stage_ms": {k: round(float(np.mean(v)), 4) for k, v in d["stages"].items() if np.mean(v) > 0},
             "kernel_ms_sum": round(tot, 4),
             "numeric_ms": round(sum(float(np.mean(d["stages"][k])) for k in
-                                    ("num_rowptr", "num_window", "num_block", "num_warp", "num_tiny")), 4),
+                                    ("num_rowptr", "num_window", "num_expand", "num_block", "num_warp",
+                                     "num_tiny")), 4),
             "numeric_alg_bytes": _numeric_bytes(info, d["rows"]),
             "num_class_rows": {sp._native.NUM_CLASSES[c]: info["num_class_rows"][c]
                                for c in range(len(sp._native.NUM_CLASSES)) if info["num_class_rows"][c]},

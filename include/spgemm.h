@@ -170,7 +170,8 @@ typedef enum spgemm_stage {
   SPGEMM_STAGE_NUM_WARP = 10,
   SPGEMM_STAGE_NUM_TINY = 11,
   SPGEMM_STAGE_NUM_RERUN = 12,   /* FP64 recomputation of flagged FP32 rows */
-  SPGEMM_NUM_STAGES = 13
+  SPGEMM_STAGE_NUM_EXPAND = 13,  /* columns of the windowed rows whose bitmap the symbolic pass stored */
+  SPGEMM_NUM_STAGES = 14
 } spgemm_stage;
 
 typedef struct spgemm_timings {

@@ -61,7 +61,7 @@ class PlanInfo(ctypes.Structure):
 
 
 STAGES = ["validate", "count", "sym_window", "sym_block", "sym_warp", "sym_tiny", "sym_scan",
-          "num_rowptr", "num_window", "num_block", "num_warp", "num_tiny", "num_rerun"]
+          "num_rowptr", "num_window", "num_block", "num_warp", "num_tiny", "num_rerun", "num_expand"]
 SYM_CLASSES = ["win0", "win1", "win2", "win3", "block8192", "warp2048", "warp512", "warp128", "tiny", "micro",
                "empty"]
 NUM_CLASSES = ["win0", "win1", "win2", "win3", "block8192", "block2048", "warp1024", "warp256", "warp64",

@@ -88,6 +88,13 @@ int launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t*
                       const int32_t* abase, uint32_t* err, int num_sms, cudaStream_t s);
 
 // ---- windowed numeric pass and the column-block split table of B (k_window.cu)
+// Columns of C for the windowed rows with a stored bitmap (k_window.cu); rows without one get
+// theirs from the windowed numeric kernel.
+int launch_expand_cols(const int32_t* perm, int64_t count, const int32_t* win_slot, const int64_t* woff,
+                       const uint32_t* wbits, const uint16_t* blockcnt, int64_t nblocks, const int64_t* c_off,
+                       const int32_t* awidth, int64_t width, int32_t* ccol, int num_sms, uint32_t* err,
+                       cudaStream_t s);
+
 // ---- FP64 recomputation of flagged windowed FP32 rows (k_rerun.cu): groups of group_rows rows
 // share `dense` (group_rows * width FP64), every partial product added with a global atomic.
 int64_t rerun_group_rows(int64_t width, int64_t budget_bytes);

@@ -312,6 +312,10 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
                             p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
                             p->rerun_flag, p->abase, p->awidth, p->width, p->wbits, p->woff, p->num_sms, err, s);
     stage_end(p, SPGEMM_STAGE_NUM_WINDOW, nl, s);
+    stage_begin(p, SPGEMM_STAGE_NUM_EXPAND, s);
+    nl = launch_expand_cols(seg(kNumWin0), nwin, p->win_slot, p->woff, p->wbits, p->blockcnt, p->nblocks, p->c_off,
+                            p->awidth, p->width, C->col, p->num_sms, err, s);
+    stage_end(p, SPGEMM_STAGE_NUM_EXPAND, nl, s);
     if (!f32c) {
       double* cval = static_cast<double*>(C->val);
       stage_begin(p, SPGEMM_STAGE_NUM_BLOCK, s);
