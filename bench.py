@@ -17,6 +17,7 @@ import argparse
 import csv
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -110,19 +111,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _traffic(kernel_file: str, workload: str):
+def _traffic(kernel_file: str, workload: str, root: str = ROOT):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, when it was
     taken on this workload with the kernel source as it is now (else None)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"k_num_window_{workload}.md")
-    src = os.path.join(ROOT, "paper_2004_13907_gb300", "csrc", kernel_file)
+    path = os.path.join(root, "profiles", f"k_num_window_{workload}.md")
+    src = os.path.join(root, "paper_2004_13907_gb300", "csrc", kernel_file)
     try:
         want = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         fields = {}
         for line in open(path):
-            if ":" in line and line.lstrip().startswith("- "):
-                k, v = line.lstrip()[2:].split(":", 1)
-                fields[k.strip()] = v.strip().strip("`")
+            # "- key: value" (the key may itself hold a colon, as in "sha256[:16]")
+            m = re.match(r"\s*- (.+?): (.*)$", line)
+            if m:
+                fields[m.group(1).strip()] = m.group(2).strip().strip("`")
         if fields.get("kernel source sha256[:16]") != want:
             return None
         return int(fields["dram bytes per launch"].replace(",", ""))
