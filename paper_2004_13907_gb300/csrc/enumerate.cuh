@@ -116,6 +116,58 @@ __device__ __forceinline__ int group_owner(const int32_t* c_excl, int nent, int 
   return o + __popc(q & upto);
 }
 
+// Hands out a warp's contiguous range of product numbers 32 at a time (lane l takes g0 + l). The
+// segment owning the current group stays in registers: its start in B, its first product number,
+// the next boundary, and a value the caller attaches to it (load(segment), e.g. its a_ik). A group
+// that lies inside that segment (the next boundary 32 or more products on; o and g0 are the same on
+// every lane, so the test is warp-uniform) touches no shared memory; a group across boundaries
+// takes group_owner, and the segment of its last lane becomes the cached one. Segments past the
+// last (the last lane beyond the range's end) are never asked for, so the cache is clamped.
+template <typename T, typename Load>
+struct GroupWalker {
+  const int32_t* c_excl;
+  const int64_t* c_bs;
+  int nent;
+  Load load;
+  int o;
+  int32_t oex, onext;
+  int64_t obs;
+  T oval;
+
+  __device__ __forceinline__ GroupWalker(const int32_t* ce, const int64_t* cb, int n, int o0, Load ld)
+      : c_excl(ce), c_bs(cb), nent(n), load(ld) {
+    set(o0);
+  }
+  __device__ __forceinline__ void set(int o0) {
+    o = o0 < nent ? o0 : nent - 1;
+    oex = c_excl[o];
+    onext = c_excl[o + 1];
+    obs = c_bs[o];
+    oval = load(o);
+  }
+  // Group g0 (< hi, same on every lane): the lane's index into B (-1 at or past hi) and the
+  // value of its segment (T(0) at or past hi). A product below hi has its owner below nent.
+  __device__ __forceinline__ void step(int32_t g0, int32_t hi, int64_t& j, T& val) {
+    const int32_t p = g0 + static_cast<int32_t>(threadIdx.x & 31);
+    if (onext - g0 >= 32) {
+      j = p < hi ? obs + (p - oex) : -1;
+      val = oval;
+    } else {
+      // a lane past the range's end may be past the last segment (my == nent): no load for it
+      const int my = group_owner(c_excl, nent, o, g0);
+      j = p < hi ? c_bs[my] + (p - c_excl[my]) : -1;
+      val = p < hi ? load(my) : T(0);
+      set(__shfl_sync(0xffffffffu, my, 31));
+    }
+  }
+};
+
+template <typename T, typename Load>
+__device__ __forceinline__ GroupWalker<T, Load> make_walker(const int32_t* c_excl, const int64_t* c_bs, int nent,
+                                                            int o0, Load ld) {
+  return GroupWalker<T, Load>(c_excl, c_bs, nent, o0, ld);
+}
+
 // Largest o in [0, nent) with c_excl[o] <= p.
 __device__ __forceinline__ int search_owner(const int32_t* c_excl, int nent, int32_t p) {
   int lo = 0, hi = nent - 1;
@@ -138,7 +190,7 @@ template <int NT, int U, typename F>
 __device__ __forceinline__ void block_range_for_each_product(const DevCsr& A, const DevCsr& B, int64_t a0,
                                                              int64_t na, int32_t* s_excl, int64_t* s_bs,
                                                              long long* s_scan64, int32_t* s_ctl, F&& f) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int wid = threadIdx.x >> 5;
   constexpr int kWarps = NT / 32;
   for (int64_t base = 0; base < na; base += NT) {
     const int64_t e = base + threadIdx.x;
@@ -171,18 +223,15 @@ __device__ __forceinline__ void block_range_for_each_product(const DevCsr& A, co
     const int32_t lo = wid * per;
     const int32_t hi = total < lo + per ? total : lo + per;
     if (lo < hi) {
-      int o = search_owner(s_excl, nent, lo);
+      auto walk = make_walker<int>(s_excl, s_bs, nent, search_owner(s_excl, nent, lo), [](int) { return 0; });
       for (int32_t p0 = lo; p0 < hi; p0 += 32 * U) {
         int64_t j[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int32_t g0 = p0 + 32 * u;
           j[u] = -1;
-          if (g0 < hi) {
-            const int my = group_owner(s_excl, nent, o, g0);
-            if (g0 + lane < hi) j[u] = s_bs[my] + (g0 + lane - s_excl[my]);
-            o = __shfl_sync(0xffffffffu, my, 31);
-          }
+          int unused;
+          if (g0 < hi) walk.step(g0, hi, j[u], unused);
         }
         f(j);
       }

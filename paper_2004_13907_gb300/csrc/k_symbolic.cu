@@ -193,7 +193,6 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
   extern __shared__ uint32_t bm[];  // kSymWinBits / 32 words
   __shared__ int32_t s_excl[kSymWinThreads + 1];
   __shared__ int64_t s_bs[kSymWinThreads];
-  __shared__ int32_t s_scan[33];
   __shared__ long long s_scan64[33];
   __shared__ int32_t s_ctl[2];
   __shared__ int32_t s_idx;
@@ -228,20 +227,25 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
       if (width <= kSymWinBits) {
         // one window covers every column: no cursors; each warp marks a contiguous range of the
         // row's products (four groups of 32 loaded before they are marked)
-        const int64_t span = wend - w0;
+        // columns and the window start are below 2^31, so the offset fits 32 bits; a negative one
+        // wraps above span
+        const uint32_t span = static_cast<uint32_t>(wend - w0);
+        const int32_t w0i = static_cast<int32_t>(w0);
+        bool outside = false;
         block_range_for_each_product<kSymWinThreads, 4>(
             A, B, a0, na, s_excl, s_bs, s_scan64, s_ctl, [&](const int64_t (&j)[4]) {
               int32_t c[4];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) c[u] = j[u] >= 0 ? B.col[j[u]] : 0;
+              for (int u = 0; u < 4; ++u) c[u] = j[u] >= 0 ? B.col[j[u]] : w0i;
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 if (j[u] < 0) continue;
-                const int64_t rel = c[u] - w0;
-                if (rel >= 0 && rel < span) atomicOr(&bm[rel >> 5], 1u << (rel & 31));
-                else set_error(err, kErrWindowPlan);
+                const uint32_t rel = static_cast<uint32_t>(c[u] - w0i);
+                if (rel < span) atomicOr(&bm[rel >> 5], 1u << (rel & 31));
+                else outside = true;
               }
             });
+        if (outside) set_error(err, kErrWindowPlan);
       } else {
         for (int64_t e = wid; e < na; e += kWarps) {
           const int32_t k = A.col[a0 + e];

@@ -322,18 +322,15 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
           const int32_t lo = wid * per;
           const int32_t hi = total < lo + per ? total : lo + per;
           if (lo < hi) {
-            int o = search_owner(c_excl, nent, lo);
+            auto walk = make_walker<int>(c_excl, c_bs, nent, search_owner(c_excl, nent, lo), [](int) { return 0; });
             for (int32_t p0 = lo; p0 < hi; p0 += 32 * kUnroll) {
               int64_t j[kUnroll];
 #pragma unroll
               for (int u = 0; u < kUnroll; ++u) {
                 const int32_t g0 = p0 + 32 * u;
                 j[u] = -1;
-                if (g0 < hi) {
-                  const int my = group_owner(c_excl, nent, o, g0);
-                  if (g0 + lane < hi) j[u] = c_bs[my] + (g0 + lane - c_excl[my]);
-                  o = __shfl_sync(0xffffffffu, my, 31);
-                }
+                int unused;
+                if (g0 < hi) walk.step(g0, hi, j[u], unused);
               }
               int32_t c[kUnroll];
 #pragma unroll
@@ -388,21 +385,18 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
           const int32_t lo = wid * per;
           const int32_t hi = total < lo + per ? total : lo + per;
           if (lo < hi) {
-            int o = search_owner(c_excl, nent, lo);
+            // each segment carries its a_ik, so a group inside one segment reads no shared memory
+            auto walk = make_walker<double>(c_excl, c_bs, nent, search_owner(c_excl, nent, lo),
+                                            [&](int sgm) { return e_av[c_ent[sgm]]; });
             for (int32_t p0 = lo; p0 < hi; p0 += 32 * kUnroll) {
               int64_t j[kUnroll];
-              int ow[kUnroll];
+              double av[kUnroll];
 #pragma unroll
               for (int u = 0; u < kUnroll; ++u) {
                 const int32_t g0 = p0 + 32 * u;
                 j[u] = -1;
-                ow[u] = 0;
-                if (g0 < hi) {
-                  const int my = group_owner(c_excl, nent, o, g0);
-                  ow[u] = my;
-                  if (g0 + lane < hi) j[u] = c_bs[my] + (g0 + lane - c_excl[my]);
-                  o = __shfl_sync(0xffffffffu, my, 31);
-                }
+                av[u] = 0.0;
+                if (g0 < hi) walk.step(g0, hi, j[u], av[u]);
               }
               int32_t c[kUnroll];
               double bv[kUnroll];
@@ -428,7 +422,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
                   // error-free product a*b = ph + pl (TwoProduct with fmaf); the sum's own rounding
                   // error is rebuilt from the value atomicAdd returns (TwoSum) and, with pl, goes
                   // to the compensation term (Ogita, Rump and Oishi's Dot2, accumulated concurrently)
-                  const float a = static_cast<float>(e_av[c_ent[ow[u]]]);
+                  const float a = static_cast<float>(av[u]);
                   const float b = static_cast<float>(bv[u]);
                   const float ph = a * b;
                   const float pl = fmaf(a, b, -ph);
@@ -440,7 +434,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
                   atomicAdd(&f_m[r], fabsf(ph));
                   atomicAdd(&f_t[r], 1);
                 } else {
-                  atomicAdd(&vals[r], e_av[c_ent[ow[u]]] * bv[u]);
+                  atomicAdd(&vals[r], av[u] * bv[u]);
                 }
               }
             }
