@@ -145,6 +145,14 @@ struct GroupWalker {
     obs = c_bs[o];
     oval = load(o);
   }
+  // The n products from p0 (same on every lane) all lie in the cached segment and below hi: the
+  // lane's product p0 + l + 32 u then has index first(p0) + 32 u into B.
+  __device__ __forceinline__ bool whole(int32_t p0, int32_t n, int32_t hi) const {
+    return onext - p0 >= n && hi - p0 >= n;
+  }
+  __device__ __forceinline__ int64_t first(int32_t p0) const {
+    return obs + (p0 + static_cast<int32_t>(threadIdx.x & 31) - oex);
+  }
   // Group g0 (< hi, same on every lane): the lane's index into B (-1 at or past hi) and the
   // value of its segment (T(0) at or past hi). A product below hi has its owner below nent.
   __device__ __forceinline__ void step(int32_t g0, int32_t hi, int64_t& j, T& val) {
@@ -226,12 +234,18 @@ __device__ __forceinline__ void block_range_for_each_product(const DevCsr& A, co
       auto walk = make_walker<int>(s_excl, s_bs, nent, search_owner(s_excl, nent, lo), [](int) { return 0; });
       for (int32_t p0 = lo; p0 < hi; p0 += 32 * U) {
         int64_t j[U];
+        if (walk.whole(p0, 32 * U, hi)) {
+          const int64_t j0 = walk.first(p0);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int32_t g0 = p0 + 32 * u;
-          j[u] = -1;
-          int unused;
-          if (g0 < hi) walk.step(g0, hi, j[u], unused);
+          for (int u = 0; u < U; ++u) j[u] = j0 + 32 * u;
+        } else {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int32_t g0 = p0 + 32 * u;
+            j[u] = -1;
+            int unused;
+            if (g0 < hi) walk.step(g0, hi, j[u], unused);
+          }
         }
         f(j);
       }

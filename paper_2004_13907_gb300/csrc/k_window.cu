@@ -325,12 +325,18 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
             auto walk = make_walker<int>(c_excl, c_bs, nent, search_owner(c_excl, nent, lo), [](int) { return 0; });
             for (int32_t p0 = lo; p0 < hi; p0 += 32 * kUnroll) {
               int64_t j[kUnroll];
+              if (walk.whole(p0, 32 * kUnroll, hi)) {
+                const int64_t j0 = walk.first(p0);
 #pragma unroll
-              for (int u = 0; u < kUnroll; ++u) {
-                const int32_t g0 = p0 + 32 * u;
-                j[u] = -1;
-                int unused;
-                if (g0 < hi) walk.step(g0, hi, j[u], unused);
+                for (int u = 0; u < kUnroll; ++u) j[u] = j0 + 32 * u;
+              } else {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                  const int32_t g0 = p0 + 32 * u;
+                  j[u] = -1;
+                  int unused;
+                  if (g0 < hi) walk.step(g0, hi, j[u], unused);
+                }
               }
               int32_t c[kUnroll];
 #pragma unroll
@@ -391,12 +397,21 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
             for (int32_t p0 = lo; p0 < hi; p0 += 32 * kUnroll) {
               int64_t j[kUnroll];
               double av[kUnroll];
+              if (walk.whole(p0, 32 * kUnroll, hi)) {
+                const int64_t j0 = walk.first(p0);
 #pragma unroll
-              for (int u = 0; u < kUnroll; ++u) {
-                const int32_t g0 = p0 + 32 * u;
-                j[u] = -1;
-                av[u] = 0.0;
-                if (g0 < hi) walk.step(g0, hi, j[u], av[u]);
+                for (int u = 0; u < kUnroll; ++u) {
+                  j[u] = j0 + 32 * u;
+                  av[u] = walk.oval;
+                }
+              } else {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                  const int32_t g0 = p0 + 32 * u;
+                  j[u] = -1;
+                  av[u] = 0.0;
+                  if (g0 < hi) walk.step(g0, hi, j[u], av[u]);
+                }
               }
               int32_t c[kUnroll];
               double bv[kUnroll];
