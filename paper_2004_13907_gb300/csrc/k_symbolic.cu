@@ -200,6 +200,8 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
   __shared__ long long s_woff;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int kWarps = kSymWinThreads / 32;
+  // the bitmap is cleared once here; every window's counting pass leaves it clear again
+  for (int t = threadIdx.x; t < kSymWinBits / 32; t += kSymWinThreads) bm[t] = 0u;
   for (;;) {
     if (threadIdx.x == 0) {
       s_idx = atomicAdd(counter, 1);
@@ -215,15 +217,24 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
     const int64_t cb = abase ? abase[i] : 0;   // the row's columns are [cb, cb + width)
     const int64_t width = awidth ? awidth[i] : width_all;
     uint16_t* cnts = blockcnt + idx * nblocks;
-    // a row inside one window stores its bitmap (for the numeric pass) when wbits has room
+    // a row inside one window stores its bitmap (its blocks, 128 words each) for the numeric
+    // pass when wbits has room
     const bool store = wbits != nullptr && width <= kSymWinBits;
-    if (threadIdx.x == 0 && woff) woff[idx] = -1;
+    if (threadIdx.x == 0) {
+      long long wo = -1;
+      if (store) {
+        const int64_t words = (width + kBlockCols - 1) / kBlockCols * kBlockWords;
+        const unsigned long long off = atomicAdd(wcur, static_cast<unsigned long long>(words));
+        if (off + words <= static_cast<unsigned long long>(wcap)) wo = static_cast<long long>(off);
+      }
+      s_woff = wo;
+      if (woff) woff[idx] = wo;
+    }
+    __syncthreads();
+    const long long wo = s_woff;
     for (int64_t r0 = 0; r0 < width; r0 += kSymWinBits) {
       const int64_t w0 = cb + r0;
       const int64_t wend = cb + ((r0 + kSymWinBits < width) ? r0 + kSymWinBits : width);
-      const int nwords = static_cast<int>((wend - w0 + 31) >> 5);
-      for (int t = threadIdx.x; t < nwords; t += kSymWinThreads) bm[t] = 0u;
-      __syncthreads();
       if (width <= kSymWinBits) {
         // one window covers every column: no cursors; each warp marks a contiguous range of the
         // row's products (four groups of 32 loaded before they are marked)
@@ -264,51 +275,30 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
         }
         __syncthreads();
       }
-      // per-block counts of this window (warp per block of kBlockWords words); blocks are
-      // counted from the row's first column cb
+      // per-block counts of this window, the stored copy and the clearing of the bitmap in one
+      // pass: a warp per block of kBlockWords words (lane: 4), blocks counted from the row's first
+      // column cb. A window ends on a block boundary (kSymWinBits is a multiple of kBlockCols), so
+      // every block's words lie inside the bitmap; words past the row's width were never marked.
       const int64_t b0 = r0 / kBlockCols;
       const int64_t b1 = (wend - cb + kBlockCols - 1) / kBlockCols;
       for (int64_t b = b0 + wid; b < b1; b += kWarps) {
-        const int wlo = static_cast<int>(b * kBlockWords - (r0 >> 5));
-        const int whi = wlo + kBlockWords < nwords ? wlo + kBlockWords : nwords;
-        int c = 0;
-        for (int t = wlo + lane; t < whi; t += 32) c += __popc(bm[t]);
+        uint4* p = reinterpret_cast<uint4*>(bm + (b * kBlockWords - (r0 >> 5))) + lane;
+        const uint4 v = *p;
+        int c = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
         c = warp_sum(c);
         if (lane == 0) {
           cnts[b] = static_cast<uint16_t>(c);
           if (c) atomicAdd(&s_total, static_cast<unsigned long long>(c));
         }
+        // a stored row has one window, starting at block 0
+        if (wo >= 0) reinterpret_cast<uint4*>(wbits + wo)[b * (kBlockWords / 4) + lane] = v;
+        if (v.x | v.y | v.z | v.w) *p = make_uint4(0u, 0u, 0u, 0u);
       }
       __syncthreads();
-      if (store) {
-        // the row's bitmap (its blocks, 128 words each) goes to wbits for the numeric pass
-        const int nb = static_cast<int>(b1);   // a stored row has one window, starting at block 0
-        const int64_t words = int64_t(nb) * kBlockWords;
-        if (threadIdx.x == 0) {
-          const unsigned long long off = atomicAdd(wcur, static_cast<unsigned long long>(words));
-          s_woff = off + words <= static_cast<unsigned long long>(wcap) ? static_cast<long long>(off) : -1ll;
-          woff[idx] = s_woff;
-        }
-        __syncthreads();
-        const long long wo = s_woff;
-        if (wo >= 0) {
-          // words past the row's width (the tail of its last block) are stored as zero
-          uint4* dst = reinterpret_cast<uint4*>(wbits + wo);
-          for (int64_t q = threadIdx.x; q < words / 4; q += kSymWinThreads) {
-            const int w = static_cast<int>(q * 4);
-            uint4 v;
-            v.x = w + 0 < nwords ? bm[w + 0] : 0u;
-            v.y = w + 1 < nwords ? bm[w + 1] : 0u;
-            v.z = w + 2 < nwords ? bm[w + 2] : 0u;
-            v.w = w + 3 < nwords ? bm[w + 3] : 0u;
-            dst[q] = v;
-          }
-        }
-        __syncthreads();
-      }
     }
+    // s_total is final (the counting pass ended with a barrier); thread 0 itself resets it for
+    // the next row, after this read
     if (threadIdx.x == 0) nnz_row[i] = static_cast<int32_t>(s_total);
-    __syncthreads();
   }
 }
 
