@@ -59,6 +59,7 @@ struct WinGeom {
   static constexpr int kBlocksPerSm = 2;
   static_assert(kWordsPerThread * kNumThreads == kSpanWords, "words per thread");
   static_assert(kGroupWords % kWordsPerThread == 0, "a thread's words lie in one group");
+  static_assert(kWordsPerThread % 4 == 0, "a thread's words are copied as 16-byte vectors");
   static_assert(kSmemVals % 16 == 0, "vector clearing of the values");
   static_assert(2 * (kSmemBytes + 1024 + 512) <= 228 * 1024, "two blocks per SM");
 };
@@ -307,12 +308,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
         const int32_t expect = w_cnt[wi];
         const int nwords = (span + 31) >> 5;
 
-        // pass 1: mark the window's columns (copy the stored bitmap when the row has one)
-        if (stored) {
-          const uint32_t* src = wbits + toff + b0 * kBlockWords;
-          for (int w = threadIdx.x; w < nwords; w += kNumThreads) bm[w] = src[w];
-          __syncthreads();
-        }
+        // pass 1: mark the window's columns (a row with a stored bitmap copies it in the rank
+        // prefix below instead)
         for (int64_t base = 0; base < (stored ? 0 : na); base += kNumThreads) {
           build_chunk(a0, na, base, resident, b0, b1, w0, w1);
           const int nent = s_ctl[6];
@@ -353,15 +350,32 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
           __syncthreads();
         }
         // rank prefix over the window's words: each thread owns kWordsPerThread consecutive
-        // words of one group
+        // words of one group. A stored bitmap is read here straight into the thread's registers
+        // and copied to shared memory; its window's whole blocks are stored (zero past the row's
+        // width), so every word up to (b1 - b0) * kBlockWords can be read.
         {
           const int wlo = threadIdx.x * kWordsPerThread;
-          const bool mine = wlo < nwords;
-          int c = 0;
-          if (mine) {
+          const int wmine = stored ? static_cast<int>((b1 - b0) * kBlockWords) : nwords;
+          const bool mine = wlo < wmine;
+          uint32_t wv[kWordsPerThread];
+          if (mine && stored) {
+            const uint4* src = reinterpret_cast<const uint4*>(wbits + toff + b0 * kBlockWords + wlo);
 #pragma unroll
-            for (int t = 0; t < kWordsPerThread; ++t) c += __popc(bm[wlo + t]);
+            for (int q = 0; q < kWordsPerThread / 4; ++q) {
+              const uint4 v = src[q];
+              reinterpret_cast<uint4*>(bm + wlo)[q] = v;
+              wv[4 * q] = v.x;
+              wv[4 * q + 1] = v.y;
+              wv[4 * q + 2] = v.z;
+              wv[4 * q + 3] = v.w;
+            }
+          } else {
+#pragma unroll
+            for (int t = 0; t < kWordsPerThread; ++t) wv[t] = mine ? bm[wlo + t] : 0u;
           }
+          int c = 0;
+#pragma unroll
+          for (int t = 0; t < kWordsPerThread; ++t) c += __popc(wv[t]);
           int32_t tot;
           const int32_t tpre = block_excl_scan<int32_t>(c, s_scan32, &tot);
           constexpr int kThreadsPerGroup = kGroupWords / kWordsPerThread;
@@ -373,7 +387,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
 #pragma unroll
             for (int t = 0; t < kWordsPerThread; ++t) {
               pre[wlo + t] = static_cast<uint16_t>(run);
-              run += __popc(bm[wlo + t]);
+              run += __popc(wv[t]);
             }
           }
           if (threadIdx.x == 0) s_ctl[5] = tot;
