@@ -458,30 +458,25 @@ def run_serve(args):
     cap = 32 << 30
 
     def server(**kw):
-        return sp.Server(mem_cap_bytes=cap, batch_window_us=args.serve_window_us, num_streams=2, **kw)
+        if args.serve_small_products >= 0:
+            kw["small_products"] = args.serve_small_products
+        if args.serve_batch_entries > 0:
+            kw["max_batch_entries"] = args.serve_batch_entries
+        return sp.Server(mem_cap_bytes=cap, batch_window_us=args.serve_window_us, num_streams=args.serve_streams,
+                         **kw)
 
-    def release_done(srv, pending, states, block_first=False):
-        """Releases every finished job of `pending` (a dict id -> request index), in whatever order
-        they finish, as a client consuming results would; with block_first, waits for the oldest."""
-        if block_first and pending:
-            first = next(iter(pending))
-            try:
-                srv.wait(first, timeout=600)
-            except sp.SpgemmError as e:
-                if e.name not in ("REJECTED", "OOM"):
-                    raise
-        for i in list(pending):
-            st = srv.poll(i)["state"]
-            if st in ("done", "failed", "rejected"):
-                states[pending.pop(i)] = st
-                srv.release(i)
-
-    def drain(srv, ids):
-        """Consumes every result, releasing each as soon as it is done."""
+    def drain(srv, ids, stall_s=600.0):
+        """Consumes every result as it finishes (the server's completion queue), releasing each at
+        once, as a client would; fails when no job has finished for stall_s seconds."""
         states = [None] * len(ids)
         pending = {i: k for k, i in enumerate(ids)}
         while pending:
-            release_done(srv, pending, states, block_first=True)
+            j = srv.wait_any(timeout=stall_s)
+            if j is None:
+                raise RuntimeError(f"serve: no job finished for {stall_s:.0f} s ({len(pending)} pending)")
+            if j in pending:
+                states[pending.pop(j)] = srv.poll(j)["state"]
+                srv.release(j)
         return states
 
     # warm-up: the plain path and the server on the first requests
@@ -556,13 +551,11 @@ def run_serve(args):
         th = threading.Thread(target=submitter)
         th.start()
         ready.wait()
-        pending, states, seen = {}, [None] * R, 0
-        while seen < R or pending:
-            while seen < R and ids[seen] is not None:
-                pending[ids[seen]] = seen
-                seen += 1
-            release_done(srv, pending, states)
-            time.sleep(2e-4)
+        for _ in range(R):   # every request finishes once; each result is released as it comes out
+            j = srv.wait_any(timeout=600.0)
+            if j is None:
+                raise RuntimeError("serve: no job finished for 600 s")
+            srv.release(j)
         th.join()
         live = srv.stats()
     clocks = sampler.stop()
@@ -578,7 +571,8 @@ def run_serve(args):
                                   f"[1e-4, 1e-2]), {n_lap} A*A for 3D 7-point Laplacians with g in 64..128; "
                                   f"FP64; 32 GB admission cap; inputs resident on the device",
                    "requests": R, "input_bytes": in_bytes, "products_per_step": products,
-                   "l2": "inputs larger than L2", "parallelism": "one GPU, continuous batching, 2 streams",
+                   "l2": "inputs larger than L2",
+                   "parallelism": f"one GPU, continuous batching, {args.serve_streams} streams",
                    "batch_window_us": args.serve_window_us, "input_generation_s": round(t_gen, 1)},
         "saturated": {"server_ms": round(ms_srv, 3), "plain_ms": round(ms_plain, 3),
                       "plain_value": gf(products, ms_plain), "speedup": round(ms_plain / ms_srv, 3),
@@ -757,6 +751,9 @@ def main():
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-window-us", type=int, default=300)
+    ap.add_argument("--serve-streams", type=int, default=2)
+    ap.add_argument("--serve-small-products", type=int, default=-1, help="server default when negative")
+    ap.add_argument("--serve-batch-entries", type=int, default=0, help="server default when 0")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         sys.stderr.write("note: fewer than 3 warm-up steps\n")

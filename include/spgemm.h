@@ -424,6 +424,13 @@ spgemm_status spgemm_server_poll(spgemm_server_t* server, int64_t job, spgemm_jo
 spgemm_status spgemm_server_wait(spgemm_server_t* server, int64_t job, double timeout_s,
                                  spgemm_job_info* info);
 
+/* Completion queue: waits up to timeout_s seconds (< 0: no limit, 0: no wait) for a job that
+ * reached a final state (done, failed or rejected) and that this call has not returned yet, and
+ * writes its id to *job. Jobs come out in the order they finished, each once; a job released
+ * before it comes out is skipped. TIMEOUT when none finished in time (or the server is being
+ * destroyed). Lets a client consume results as they finish without polling every job. */
+spgemm_status spgemm_server_wait_any(spgemm_server_t* server, double timeout_s, int64_t* job);
+
 /* A done job's result as a standalone CSR view (int64 row_ptr from 0), valid until
  * spgemm_server_release of that job: device pointers, or pinned host pointers for a job that ran
  * as row panels (spgemm_job_info.result_on_host). NOT_READY before it is done. */

@@ -14,6 +14,7 @@ product.
 from __future__ import annotations
 
 import ctypes
+import threading
 from dataclasses import dataclass
 
 import torch
@@ -387,6 +388,8 @@ class Server:
         _native.check(lib().spgemm_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h.value
         self._inputs = {}
+        # a job may finish, and another thread release it, before submit has recorded its inputs
+        self._inputs_lock = threading.Lock()
 
     def submit(self, A: DeviceCSR, B: DeviceCSR, sync: bool = True) -> int:
         """Queues C = A*B. The server reads A and B on its own streams, so they must be written
@@ -395,8 +398,10 @@ class Server:
             torch.cuda.current_stream().synchronize()
         a, b = A.as_in(), B.as_in()
         job = ctypes.c_int64()
-        _native.check(lib().spgemm_server_submit(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(job)))
-        self._inputs[job.value] = (A, B)
+        with self._inputs_lock:
+            _native.check(lib().spgemm_server_submit(self.handle, ctypes.byref(a), ctypes.byref(b),
+                                                     ctypes.byref(job)))
+            self._inputs[job.value] = (A, B)
         return int(job.value)
 
     def poll(self, job: int) -> dict:
@@ -413,6 +418,17 @@ class Server:
         _native.check(lib().spgemm_server_wait(self.handle, job, -1.0 if timeout is None else float(timeout),
                                                ctypes.byref(info)))
         return _job_dict(info)
+
+    def wait_any(self, timeout: float | None = None) -> int | None:
+        """Id of a job that reached a final state and was not returned by this call before (in the
+        order they finished), waiting up to ``timeout`` seconds (None: no limit); None on timeout."""
+        job = ctypes.c_int64()
+        st = lib().spgemm_server_wait_any(self.handle, -1.0 if timeout is None else float(timeout),
+                                          ctypes.byref(job))
+        if st == _native.STATUS_CODES["TIMEOUT"]:
+            return None
+        _native.check(st)
+        return int(job.value)
 
     def result(self, job: int) -> DeviceCSR:
         """View of a done job's result (valid until ``release``): device tensors, or CPU tensors over
@@ -436,8 +452,9 @@ class Server:
                          _view(c.col, c.nnz, torch.int32, self.device), _view(c.val, c.nnz, vdt, self.device))
 
     def release(self, job: int) -> None:
-        _native.check(lib().spgemm_server_release(self.handle, job))
-        self._inputs.pop(job, None)
+        with self._inputs_lock:
+            _native.check(lib().spgemm_server_release(self.handle, job))
+            self._inputs.pop(job, None)
 
     def pause(self) -> None:
         _native.check(lib().spgemm_server_pause(self.handle))

@@ -15,6 +15,7 @@ STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "INVALID_CSR", 3: "OOM", 4: "INDEX_OVERFLOW", 5: "CUDA",
     6: "TIMEOUT", 7: "REJECTED", 8: "NOT_READY", 9: "UNSUPPORTED", 10: "INTERNAL",
 }
+STATUS_CODES = {name: code for code, name in STATUS_NAMES.items()}
 F64, F32_COMPENSATED = 0, 1
 
 
@@ -137,6 +138,7 @@ SIGNATURES = {
     "spgemm_server_submit": (c_i32, [c_vp, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(c_i64)]),
     "spgemm_server_poll": (c_i32, [c_vp, c_i64, ctypes.POINTER(JobInfo)]),
     "spgemm_server_wait": (c_i32, [c_vp, c_i64, ctypes.c_double, ctypes.POINTER(JobInfo)]),
+    "spgemm_server_wait_any": (c_i32, [c_vp, ctypes.c_double, ctypes.POINTER(c_i64)]),
     "spgemm_server_result": (c_i32, [c_vp, c_i64, ctypes.POINTER(CsrOut)]),
     "spgemm_server_release": (c_i32, [c_vp, c_i64]),
     "spgemm_server_pause": (c_i32, [c_vp]),

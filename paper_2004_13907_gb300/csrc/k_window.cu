@@ -173,8 +173,19 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
 
   // Compacts the non-empty window segments of chunk [base, base + kNumThreads) of the row's A
   // entries into c_bs / c_excl / c_ent; returns (segments, products) through s_ctl[6..7].
+  // The split offsets of a resident row's entry for window [b0, b1), loaded early (with the
+  // window's stored bitmap) so that their latency overlaps the bitmap's.
+  auto split_of = [&](int64_t na, bool resident, int64_t b0, int64_t b1, int32_t& s0, int32_t& s1) {
+    s0 = -1;
+    s1 = -1;
+    if (resident && split && threadIdx.x < na) {
+      const int32_t* sp = split + int64_t(e_k[threadIdx.x]) * (nblocks + 1);
+      s0 = sp[b0];
+      s1 = sp[b1];
+    }
+  };
   auto build_chunk = [&](int64_t a0, int64_t na, int64_t base, bool resident, int64_t b0, int64_t b1,
-                         int64_t w0, int64_t w1) {
+                         int64_t w0, int64_t w1, int32_t ps0 = -1, int32_t ps1 = -1) {
     const int64_t e = base + threadIdx.x;
     int64_t bs = 0;
     int32_t len = 0;
@@ -190,7 +201,10 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
         e_av[threadIdx.x] = a_at(a0 + e);
       }
       int32_t s0, s1;
-      if (split) {
+      if (ps0 >= 0) {
+        s0 = ps0;
+        s1 = ps1;
+      } else if (split) {
         const int32_t* sp = split + int64_t(k) * (nblocks + 1);
         s0 = sp[b0];
         s1 = sp[b1];
@@ -349,6 +363,10 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
           }
           __syncthreads();
         }
+        // a resident row with a stored bitmap skips pass 1: its pass 2 chunk's split offsets are
+        // loaded now, beside the bitmap
+        int32_t ps0 = -1, ps1 = -1;
+        if (stored) split_of(na, resident, b0, b1, ps0, ps1);
         // rank prefix over the window's words: each thread owns kWordsPerThread consecutive
         // words of one group. A stored bitmap is read here straight into the thread's registers
         // and copied to shared memory; its window's whole blocks are stored (zero past the row's
@@ -397,7 +415,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
         if (threadIdx.x == 0 && cnt != expect) set_error(err, kErrCount);
         // pass 2: accumulate a_ik * b_kj by rank
         for (int64_t base = 0; base < na; base += kNumThreads) {
-          if (na > kNumThreads || stored) build_chunk(a0, na, base, resident, b0, b1, w0, w1);
+          if (na > kNumThreads || stored) build_chunk(a0, na, base, resident, b0, b1, w0, w1, ps0, ps1);
           const int nent = s_ctl[6];    // the single chunk of a resident row is kept from pass 1
           const int32_t total = s_ctl[7];
           int32_t per = (total + kWarps - 1) / kWarps;

@@ -96,6 +96,7 @@ struct spgemm_server_s {
   std::unordered_map<int64_t, Job> jobs;
   std::unordered_map<int64_t, BatchRec> batches;
   std::deque<int64_t> finished;
+  std::deque<int64_t> final_q;        // jobs in a final state, not yet returned by wait_any
   int64_t next_job = 1, next_batch = 1;
   int num_streams = 1;
   int sm_count = 0;
@@ -171,6 +172,7 @@ struct spgemm_server_s {
     j.status = st;
     j.msg = msg;
     j.t_done = now;
+    final_q.push_back(id);
     if (state == SPGEMM_JOB_DONE) {
       ++n_completed;
       latencies.push_back(ms_between(j.t_submit, now));
@@ -801,6 +803,27 @@ extern "C" spgemm_status spgemm_server_wait(spgemm_server_t* S, int64_t job, dou
     return set_error_msg(SPGEMM_ERR_TIMEOUT, "job %lld still %s after %g s", (long long)job,
                          it->second.state == SPGEMM_JOB_QUEUED ? "queued" : "running", timeout_s);
   return final_status(it->second);
+}
+
+extern "C" spgemm_status spgemm_server_wait_any(spgemm_server_t* S, double timeout_s, int64_t* job) {
+  clear_error_msg();
+  if (!S || !job) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "NULL argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto ready = [&] {
+    while (!S->final_q.empty() && S->jobs.find(S->final_q.front()) == S->jobs.end()) S->final_q.pop_front();
+    return S->stop || !S->final_q.empty();
+  };
+  bool ok = true;
+  if (timeout_s < 0 || !std::isfinite(timeout_s)) {
+    S->cv_wait.wait(lk, ready);
+  } else {
+    ok = S->cv_wait.wait_for(lk, std::chrono::duration<double>(timeout_s), ready);
+  }
+  if (!ok || S->final_q.empty())
+    return set_error_msg(SPGEMM_ERR_TIMEOUT, "no job finished within %g s", timeout_s);
+  *job = S->final_q.front();
+  S->final_q.pop_front();
+  return SPGEMM_OK;
 }
 
 extern "C" spgemm_status spgemm_server_result(spgemm_server_t* S, int64_t job, spgemm_csr_out* C) {

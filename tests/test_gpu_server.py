@@ -4,7 +4,7 @@ Each job's result from the server, where it ran inside a batch with other jobs, 
 same as the job run alone: structure bit-exact, FP64 values within 1e-12 * sum|a*b| of the
 oracle on both sides. Also: admission against the memory cap (a batch too big for the cap is
 split, a job too big alone is rejected, memory returns to zero once results are released), a
-paused server's bounded wait returning TIMEOUT, an invalid job failing alone, submissions from
+paused server's bounded wait returning TIMEOUT, the completion queue, an invalid job failing alone, submissions from
 several host threads, FP32-compensated serving, and the statistics.
 """
 
@@ -106,6 +106,37 @@ def test_paused_server_wait_times_out_then_runs():
         srv.release(j)
         with pytest.raises(sp.SpgemmError):
             srv.poll(j)
+
+
+def test_completion_queue_returns_every_job_once_in_finish_order():
+    """wait_any hands out each finished job exactly once (a rejected one too), times out while
+    nothing has finished, and skips a job released before it came out."""
+    import paper_2004_13907_gb300 as sp
+    jobs = [synth.batch_job(i, seed=71, n_hi=2000) for i in range(24)]
+    dev = _to_dev(sp, jobs)
+    big = synth.uniform_random(3000, 3000, 0.05, seed=72)
+    dbig = sp.DeviceCSR.from_host(big, "cuda")
+    with sp.Server(start_paused=1, mem_cap_bytes=8 << 20, host_panels=0) as srv:
+        ids = [srv.submit(dA, dB) for dA, dB in dev]
+        rej = srv.submit(dbig, dbig)          # inputs over the 8 MB cap on their own: rejected
+        assert srv.wait_any(timeout=0.2) is None
+        srv.resume()
+        first = srv.wait(ids[0], timeout=60)
+        assert first["state"] == "done"
+        srv.release(ids[0])                    # released before wait_any returned it: skipped
+        seen = []
+        while len(seen) < len(ids):
+            j = srv.wait_any(timeout=60)
+            assert j is not None
+            seen.append(j)
+            if j != rej:
+                A, B = jobs[ids.index(j)]
+                dA, dB = dev[ids.index(j)]
+                _same_as_alone(A, B, srv.result(j), sp.multiply(dA, dB))
+            srv.release(j)
+        assert sorted(seen) == sorted(ids[1:] + [rej])
+        assert srv.wait_any(timeout=0.05) is None
+        assert srv.wait_any(timeout=0) is None
 
 
 def test_admission_splits_batches_and_rejects_oversized_jobs():
