@@ -202,11 +202,11 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
   constexpr int kWarps = kSymWinThreads / 32;
   // the bitmap is cleared once here; every window's counting pass leaves it clear again
   for (int t = threadIdx.x; t < kSymWinBits / 32; t += kSymWinThreads) bm[t] = 0u;
+  if (threadIdx.x == 0) {
+    s_idx = atomicAdd(counter, 1);
+    s_total = 0;
+  }
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_idx = atomicAdd(counter, 1);
-      s_total = 0;
-    }
     __syncthreads();
     const int64_t idx = s_idx;
     if (idx >= count) break;
@@ -220,18 +220,15 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
     // a row inside one window stores its bitmap (its blocks, 128 words each) for the numeric
     // pass when wbits has room
     const bool store = wbits != nullptr && width <= kSymWinBits;
+    // thread 0 claims the next row and this row's stored-bitmap space now; both results are used
+    // only after the marking, so the atomics' latency hides behind it
+    int64_t next_idx = 0;
+    const int64_t words = store ? (width + kBlockCols - 1) / kBlockCols * kBlockWords : 0;
+    unsigned long long woff_at = 0;
     if (threadIdx.x == 0) {
-      long long wo = -1;
-      if (store) {
-        const int64_t words = (width + kBlockCols - 1) / kBlockCols * kBlockWords;
-        const unsigned long long off = atomicAdd(wcur, static_cast<unsigned long long>(words));
-        if (off + words <= static_cast<unsigned long long>(wcap)) wo = static_cast<long long>(off);
-      }
-      s_woff = wo;
-      if (woff) woff[idx] = wo;
+      next_idx = atomicAdd(counter, 1);
+      if (store) woff_at = atomicAdd(wcur, static_cast<unsigned long long>(words));
     }
-    __syncthreads();
-    const long long wo = s_woff;
     for (int64_t r0 = 0; r0 < width; r0 += kSymWinBits) {
       const int64_t w0 = cb + r0;
       const int64_t wend = cb + ((r0 + kSymWinBits < width) ? r0 + kSymWinBits : width);
@@ -275,6 +272,17 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
         }
         __syncthreads();
       }
+      if (r0 == 0) {
+        // the stored copy's place (a stored row has this one window), published for the pass below
+        if (threadIdx.x == 0) {
+          long long o = -1;
+          if (store && woff_at + words <= static_cast<unsigned long long>(wcap)) o = static_cast<long long>(woff_at);
+          s_woff = o;
+          if (woff) woff[idx] = o;
+        }
+        __syncthreads();
+      }
+      const long long wo = s_woff;
       // per-block counts of this window, the stored copy and the clearing of the bitmap in one
       // pass: a warp per block of kBlockWords words (lane: 4), blocks counted from the row's first
       // column cb. A window ends on a block boundary (kSymWinBits is a multiple of kBlockCols), so
@@ -296,9 +304,13 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
       }
       __syncthreads();
     }
-    // s_total is final (the counting pass ended with a barrier); thread 0 itself resets it for
-    // the next row, after this read
-    if (threadIdx.x == 0) nnz_row[i] = static_cast<int32_t>(s_total);
+    // s_total is final (the counting pass ended with a barrier); thread 0 resets it and hands out
+    // the next row, which every thread reads after the barrier at the top
+    if (threadIdx.x == 0) {
+      nnz_row[i] = static_cast<int32_t>(s_total);
+      s_total = 0;
+      s_idx = next_idx;
+    }
   }
 }
 
