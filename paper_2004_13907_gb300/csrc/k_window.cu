@@ -539,14 +539,18 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
 }
 
 // Columns of the windowed rows with a stored bitmap, straight from that bitmap: a warp per row
-// walks the row's blocks 32 at a time (their entry counts scanned across the lanes). A non-empty
-// block's 128 words (lane: 4 of them) are compacted into a per-warp list of its nonzero words with
-// their running bit counts; its set bits are then cut into 32 equal runs of consecutive ranks, so
-// that every lane extracts the same number of columns however the bits are spread over the block.
-// Each lane finds its first rank by binary search over the list, writes its run into a staging
-// buffer in rank order, and the warp stores the buffer out contiguously, kExpandStage at a time.
+// walks the row's blocks 32 at a time (their entry counts scanned across the lanes), in groups of
+// kExpandGroup consecutive blocks (lane: kExpandWords consecutive words of a group). A non-empty
+// group's nonzero words are listed in shared memory with their running bit counts; its set bits
+// are then cut into 32 equal runs of consecutive ranks, so that every lane extracts the same
+// number of columns however the bits are spread. Each lane finds its first rank by binary search
+// over the list, writes its run into a staging buffer in rank order, and the warp stores the
+// buffer out contiguously, kExpandStage at a time.
 constexpr int kExpandStage = 512;
 constexpr int kExpandWarps = 8;
+constexpr int kExpandGroup = 4;                                    // blocks per group
+constexpr int kExpandGroupWords = kExpandGroup * kBlockWords;      // 512
+constexpr int kExpandWords = kExpandGroupWords / 32;               // words per lane, 16
 
 // Position of the set bit of rank r (0-based, r < popc(m)) in m: a binary search on popcounts of
 // the low halves.
@@ -563,21 +567,21 @@ __device__ __forceinline__ int select_bit(uint32_t m, int r) {
 struct ExpandWarpSmem {
   alignas(16) int32_t stage[kExpandStage + 4];   // columns of the current run of ranks, shifted so
                                                  // that stage[p] goes to a 16-byte aligned slot p
-  uint2 list[kBlockWords];          // nonzero words of the block in column order, with the column
+  uint2 list[kExpandGroupWords];    // nonzero words of the group in column order, with the column
                                     // of their bit 0
-  uint16_t pre[kBlockWords];        // set bits before each listed word
+  uint16_t pre[kExpandGroupWords];  // set bits before each listed word
 };
 
-__global__ void __launch_bounds__(kExpandWarps * 32, 4) k_expand_cols(const int32_t* __restrict__ perm, int64_t count,
+__global__ void __launch_bounds__(kExpandWarps * 32, 3) k_expand_cols(const int32_t* __restrict__ perm, int64_t count,
                                                      const int32_t* __restrict__ win_slot,
                                                      const int64_t* __restrict__ woff, const uint32_t* __restrict__ wbits,
                                                      const uint16_t* __restrict__ blockcnt, int64_t nblocks,
                                                      const int64_t* __restrict__ c_off,
                                                      const int32_t* __restrict__ awidth, int64_t width_all,
                                                      int32_t* __restrict__ ccol, uint32_t* err) {
-  __shared__ ExpandWarpSmem s_warp[kExpandWarps];
+  extern __shared__ __align__(16) unsigned char s_expand[];
   const int lane = threadIdx.x & 31;
-  ExpandWarpSmem& sw = s_warp[threadIdx.x >> 5];
+  ExpandWarpSmem& sw = reinterpret_cast<ExpandWarpSmem*>(s_expand)[threadIdx.x >> 5];
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < count; r += nw) {
     const int32_t i = perm[r];
@@ -595,93 +599,93 @@ __global__ void __launch_bounds__(kExpandWarps * 32, 4) k_expand_cols(const int3
       const int c = b < nb ? cnts[b] : 0;
       const int incl = warp_incl_scan(c);
       const int tot = __shfl_sync(0xffffffffu, incl, 31);
-      unsigned nz = __ballot_sync(0xffffffffu, c != 0);
-      while (nz) {
-        // up to four non-empty blocks at a time: their words are loaded before any is expanded
-        constexpr int kAhead = 4;
-        int srcs[kAhead];
-        uint4 qs[kAhead];
+      const unsigned nzb = __ballot_sync(0xffffffffu, c != 0);
+      for (int g = 0; g < 32 / kExpandGroup; ++g) {
+        if (((nzb >> (g * kExpandGroup)) & ((1u << kExpandGroup) - 1u)) == 0u) continue;
+        const int first = g * kExpandGroup, last = first + kExpandGroup - 1;
+        const int64_t base = out + __shfl_sync(0xffffffffu, incl - c, first);
+        const int gcnt = __shfl_sync(0xffffffffu, incl, last) - __shfl_sync(0xffffffffu, incl - c, first);
+        const int64_t gb = b0 + first;                     // the group's first block
+        const int32_t col0 = static_cast<int32_t>(gb * kBlockCols);
+        // the lane's words: blocks past the row's last are not the row's (read as zero)
+        uint32_t wv[kExpandWords];
+        if (gb + (lane * kExpandWords) / kBlockWords < nb) {
+          const uint4* src = reinterpret_cast<const uint4*>(wbits + toff + gb * kBlockWords + lane * kExpandWords);
 #pragma unroll
-        for (int u = 0; u < kAhead; ++u) {
-          srcs[u] = -1;
-          qs[u] = make_uint4(0u, 0u, 0u, 0u);
-          if (nz) {
-            srcs[u] = __ffs(nz) - 1;
-            nz &= nz - 1;
-            qs[u] = reinterpret_cast<const uint4*>(wbits + toff + (b0 + srcs[u]) * kBlockWords)[lane];
+          for (int q = 0; q < kExpandWords / 4; ++q) {
+            const uint4 v = src[q];
+            wv[4 * q] = v.x;
+            wv[4 * q + 1] = v.y;
+            wv[4 * q + 2] = v.z;
+            wv[4 * q + 3] = v.w;
           }
+        } else {
+#pragma unroll
+          for (int t = 0; t < kExpandWords; ++t) wv[t] = 0u;
         }
+        // one scan gives each lane its first bit rank (low 16 bits) and list slot (high bits)
+        int pc = 0, nzw = 0;
 #pragma unroll
-        for (int u = 0; u < kAhead; ++u) {
-          if (srcs[u] < 0) break;
-          const int src = srcs[u];
-          const int64_t base = out + __shfl_sync(0xffffffffu, incl - c, src);
-          const int bcnt = __shfl_sync(0xffffffffu, c, src);
-          const int32_t col0 = static_cast<int32_t>((b0 + src) * kBlockCols);
-          const uint32_t wv[4] = {qs[u].x, qs[u].y, qs[u].z, qs[u].w};
-          // one scan gives each lane its first bit rank (low 16 bits) and list slot (high bits)
-          int pc = 0, nzw = 0;
+        for (int t = 0; t < kExpandWords; ++t) { pc += __popc(wv[t]); nzw += wv[t] != 0u; }
+        const int packed = (nzw << 16) | pc;
+        const int pincl = warp_incl_scan(packed);
+        const int ptot = __shfl_sync(0xffffffffu, pincl, 31);
+        const int nbits = ptot & 0xffff, nlist = ptot >> 16;
+        int rk = (pincl - packed) & 0xffff, pos = (pincl - packed) >> 16;
 #pragma unroll
-          for (int t = 0; t < 4; ++t) { pc += __popc(wv[t]); nzw += wv[t] != 0u; }
-          const int packed = (nzw << 16) | pc;
-          const int pincl = warp_incl_scan(packed);
-          const int ptot = __shfl_sync(0xffffffffu, pincl, 31);
-          const int nbits = ptot & 0xffff, nlist = ptot >> 16;
-          int rk = (pincl - packed) & 0xffff, pos = (pincl - packed) >> 16;
+        for (int t = 0; t < kExpandWords; ++t)
+          if (wv[t]) {
+            sw.list[pos] = make_uint2(wv[t], static_cast<uint32_t>(col0 + (lane * kExpandWords + t) * 32));
+            sw.pre[pos] = static_cast<uint16_t>(rk);
+            ++pos;
+            rk += __popc(wv[t]);
+          }
+        if (nbits != gcnt) bad = true;
+        __syncwarp();
+        for (int lo = 0; lo < nbits; lo += kExpandStage) {
+          const int n = nbits - lo < kExpandStage ? nbits - lo : kExpandStage;
+          const int64_t g0 = base + lo;
+          const int sh = static_cast<int>((reinterpret_cast<uintptr_t>(ccol + g0) >> 2) & 3u);
+          // an odd run length keeps the lanes' staging writes on distinct banks
+          const int q = ((n + 31) >> 5) | 1;
+          const int s = lo + q * lane;
+          const int e = s + q < lo + n ? s + q : lo + n;
+          if (s < e) {
+            int j = 0;
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
-            if (wv[t]) {
-              sw.list[pos] = make_uint2(wv[t], static_cast<uint32_t>(col0 + (lane * 4 + t) * 32));
-              sw.pre[pos] = static_cast<uint16_t>(rk);
-              ++pos;
-              rk += __popc(wv[t]);
+            for (int h = kExpandGroupWords / 2; h >= 1; h >>= 1)
+              if (j + h < nlist && sw.pre[j + h] <= s) j += h;
+            uint2 wj = sw.list[j];
+            uint32_t m = wj.x & (0xffffffffu << select_bit(wj.x, s - sw.pre[j]));
+            int32_t cb = static_cast<int32_t>(wj.y);
+            for (int k = s - lo + sh; k < e - lo + sh; ++k) {
+              if (m == 0u) {
+                ++j;
+                wj = sw.list[j];
+                m = wj.x;
+                cb = static_cast<int32_t>(wj.y);
+              }
+              sw.stage[k] = cb + __ffs(m) - 1;
+              m &= m - 1;
             }
-          if (nbits != bcnt) bad = true;
+          }
           __syncwarp();
-          for (int lo = 0; lo < nbits; lo += kExpandStage) {
-            const int n = nbits - lo < kExpandStage ? nbits - lo : kExpandStage;
-            const int64_t g0 = base + lo;
-            const int sh = static_cast<int>((reinterpret_cast<uintptr_t>(ccol + g0) >> 2) & 3u);
-            // an odd run length keeps the lanes' staging writes on distinct banks
-            const int q = ((n + 31) >> 5) | 1;
-            const int s = lo + q * lane;
-            const int e = s + q < lo + n ? s + q : lo + n;
-            if (s < e) {
-              int j = 0;
-#pragma unroll
-              for (int h = 64; h >= 1; h >>= 1)
-                if (j + h < nlist && sw.pre[j + h] <= s) j += h;
-              uint2 wj = sw.list[j];
-              uint32_t m = wj.x & (0xffffffffu << select_bit(wj.x, s - sw.pre[j]));
-              int32_t cb = static_cast<int32_t>(wj.y);
-              for (int k = s - lo + sh; k < e - lo + sh; ++k) {
-                if (m == 0u) {
-                  ++j;
-                  wj = sw.list[j];
-                  m = wj.x;
-                  cb = static_cast<int32_t>(wj.y);
-                }
-                sw.stage[k] = cb + __ffs(m) - 1;
-                m &= m - 1;
-              }
+          // stage[p] -> dst[p] for p in [sh, pend): whole 16-byte slots as one vector store
+          int lim = n;
+          if (out_end - g0 < lim) lim = out_end - g0 < 0 ? 0 : static_cast<int>(out_end - g0);
+          const int pend = sh + lim;
+          int32_t* dst = ccol + (g0 - sh);
+          for (int v = lane; v * 4 < pend; v += 32) {
+            const int p0 = v * 4;
+            if (p0 >= sh && p0 + 4 <= pend) {
+              reinterpret_cast<int4*>(dst)[v] = reinterpret_cast<const int4*>(sw.stage)[v];
+            } else {
+              for (int p = p0 > sh ? p0 : sh; p < p0 + 4 && p < pend; ++p) dst[p] = sw.stage[p];
             }
-            __syncwarp();
-            // stage[p] -> dst[p] for p in [sh, pend): whole 16-byte slots as one vector store
-            int lim = n;
-            if (out_end - g0 < lim) lim = out_end - g0 < 0 ? 0 : static_cast<int>(out_end - g0);
-            const int pend = sh + lim;
-            int32_t* dst = ccol + (g0 - sh);
-            for (int v = lane; v * 4 < pend; v += 32) {
-              const int p0 = v * 4;
-              if (p0 >= sh && p0 + 4 <= pend) {
-                reinterpret_cast<int4*>(dst)[v] = reinterpret_cast<const int4*>(sw.stage)[v];
-              } else {
-                for (int p = p0 > sh ? p0 : sh; p < p0 + 4 && p < pend; ++p) dst[p] = sw.stage[p];
-              }
-            }
-            __syncwarp();
           }
+          __syncwarp();
         }
+        __syncwarp();
       }
       out += tot;
     }
@@ -696,9 +700,11 @@ int launch_expand_cols(const int32_t* perm, int64_t count, const int32_t* win_sl
                        const int32_t* awidth, int64_t width, int32_t* ccol, int num_sms, uint32_t* err,
                        cudaStream_t s) {
   if (count <= 0 || !wbits) return 0;
+  constexpr int smem = kExpandWarps * static_cast<int>(sizeof(ExpandWarpSmem));
+  cudaFuncSetAttribute(k_expand_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int64_t g = (count + kExpandWarps - 1) / kExpandWarps;
   if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
-  k_expand_cols<<<static_cast<unsigned>(g), kExpandWarps * 32, 0, s>>>(perm, count, win_slot, woff, wbits, blockcnt, nblocks, c_off,
+  k_expand_cols<<<static_cast<unsigned>(g), kExpandWarps * 32, smem, s>>>(perm, count, win_slot, woff, wbits, blockcnt, nblocks, c_off,
                                                        awidth, width, ccol, err);
   return 1;
 }
