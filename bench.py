@@ -625,15 +625,21 @@ def run_e2e(args, mats, nnz_c, products_step, sp, torch, dist):
         d2h = (M.rows + 1) * orp.element_size() + nnz * 12    # C copied out
         hosts.append((name, hA, out, idx64, h2d, d2h))
 
+    per_matrix = {name: [] for name, *_ in hosts}
+
     def step():
         for name, hA, out, idx64, _, _ in hosts:
+            t = time.perf_counter()
             sp.spgemm_multiply_host(hA, hA, out=out, idx64=idx64)
+            per_matrix[name].append(time.perf_counter() - t)
 
     for _ in range(max(1, min(args.warmup, 2))):
         step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    for v in per_matrix.values():
+        v.clear()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
@@ -646,6 +652,7 @@ def run_e2e(args, mats, nnz_c, products_step, sp, torch, dist):
             "h2d_bytes_per_step": int(sum(h[4] for h in hosts)),
             "d2h_bytes_per_step": int(sum(h[5] for h in hosts)),
             "ms_per_step": round(t * 1e3, 3), "host_buffers": "pinned" if pinned_ok else "pageable (pinning failed)",
+            "ms_per_matrix": {k: round(float(np.mean(v)) * 1e3, 3) for k, v in per_matrix.items()},
             "api": "spgemm_multiply_host (C ABI, host buffers)"}
 
 
