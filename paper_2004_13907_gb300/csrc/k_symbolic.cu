@@ -234,19 +234,19 @@ __global__ void __launch_bounds__(kSymWinThreads, 1) k_sym_window(DevCsr A, DevC
       const int64_t wend = cb + ((r0 + kSymWinBits < width) ? r0 + kSymWinBits : width);
       if (width <= kSymWinBits) {
         // one window covers every column: no cursors; each warp marks a contiguous range of the
-        // row's products (four groups of 32 loaded before they are marked)
+        // row's products (eight groups of 32 loaded before they are marked)
         // columns and the window start are below 2^31, so the offset fits 32 bits; a negative one
         // wraps above span
         const uint32_t span = static_cast<uint32_t>(wend - w0);
         const int32_t w0i = static_cast<int32_t>(w0);
         bool outside = false;
-        block_range_for_each_product<kSymWinThreads, 4>(
-            A, B, a0, na, s_excl, s_bs, s_scan64, s_ctl, [&](const int64_t (&j)[4]) {
-              int32_t c[4];
+        block_range_for_each_product<kSymWinThreads, 8>(
+            A, B, a0, na, s_excl, s_bs, s_scan64, s_ctl, [&](const int64_t (&j)[8]) {
+              int32_t c[8];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) c[u] = j[u] >= 0 ? B.col[j[u]] : w0i;
+              for (int u = 0; u < 8; ++u) c[u] = j[u] >= 0 ? B.col[j[u]] : w0i;
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
+              for (int u = 0; u < 8; ++u) {
                 if (j[u] < 0) continue;
                 const uint32_t rel = static_cast<uint32_t>(c[u] - w0i);
                 if (rel < span) atomicOr(&bm[rel >> 5], 1u << (rel & 31));
