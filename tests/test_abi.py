@@ -121,4 +121,6 @@ def test_server_config_checks_on_host(lib):
     job = ctypes.c_int64()
     a = _native.CsrIn(4, 5, 0, 0, 0, 1, 0, 0)
     assert lib.spgemm_server_submit(None, ctypes.byref(a), ctypes.byref(a), ctypes.byref(job)) == 1
+    lib.spgemm_server_wait_any.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]
+    assert lib.spgemm_server_wait_any(None, 0.0, ctypes.byref(job)) == 1
     assert lib.spgemm_server_destroy(None) == 0
