@@ -535,7 +535,6 @@ def run_serve(args):
         del C
     # server at rate lam: a submitter thread follows the arrival times, this thread consumes
     with server() as srv:
-        ids = [None] * R
         lag = [0.0]
         ready = threading.Event()
 
@@ -547,7 +546,7 @@ def run_serve(args):
                 if wait > 0:
                     time.sleep(wait)
                 lag[0] = max(lag[0], time.perf_counter() - t0s - arrival[k])
-                ids[k] = srv.submit(*dev[k], sync=False)
+                srv.submit(*dev[k], sync=False)
         th = threading.Thread(target=submitter)
         th.start()
         ready.wait()
