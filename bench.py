@@ -63,6 +63,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _fp64_pipe(products: int, ms: float, sm_count: int, sm_mhz) -> dict:
+    """The windowed numeric pass against GB300's FP64 pipe: every partial product costs two FP64
+    operations there (the product a_ik * b_kj and the add inside the shared atomic), and the pipe
+    executes 2 lanes per clock per SM (1.25 TFLOP/s counted as FMA), at the sampled SM clock."""
+    mhz = float(sm_mhz) if sm_mhz else 2070.0
+    peak = 2.0 * sm_count * mhz * 1e6
+    achieved = 2.0 * products / (ms * 1e-3)
+    return {"fp64_ops_per_s": round(achieved, 1), "fp64_peak_ops_per_s": round(peak, 1),
+            "fp64_frac": round(achieved / peak, 4), "fp64_floor_ms": round(2.0 * products / peak * 1e3, 2)}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -261,13 +272,17 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     roof = None
     if dom_stage == "num_window":
-        bytes_, _ = _window_bytes(per[dom_mat]["info"])
+        bytes_, wprods = _window_bytes(per[dom_mat]["info"])
         achieved = bytes_ / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": f"k_num_window + k_expand_cols ({dom_mat})",
                 "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": bytes_,
                 "launch_ms": round(dom_ms, 4), "traffic": _traffic("k_window.cu", args.workload)}
+        if all(p == "f64" for p in precs.values()):
+            roof.update(_fp64_pipe(wprods, dom_ms,
+                                   torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count,
+                                   clocks.get("sm_mhz")))
     breakdown = {}
     for name, d in per.items():
         info = d["info"]

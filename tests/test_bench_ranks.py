@@ -86,3 +86,15 @@ def test_committed_window_profile_parses():
     text = open(os.path.join(ROOT, "profiles", "k_num_window_lap2d1024+rmat20.md")).read()
     assert re.search(r"- kernel source sha256\[:16\]: `[0-9a-f]{16}`", text)
     assert re.search(r"- dram bytes per launch: [0-9,]+", text)
+
+
+def test_fp64_pipe_fraction():
+    """Two FP64 operations per partial product against 2 lanes per clock per SM."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench._fp64_pipe(20_919_618_292, 241.0, 152, 2070.0)
+    assert r["fp64_peak_ops_per_s"] == 2.0 * 152 * 2070e6
+    assert abs(r["fp64_ops_per_s"] - 2 * 20_919_618_292 / 0.241) < 1.0
+    assert abs(r["fp64_frac"] - 0.2757) < 1e-3
+    assert abs(r["fp64_floor_ms"] - 66.49) < 0.01
+    assert bench._fp64_pipe(1, 1.0, 1, None)["fp64_peak_ops_per_s"] == 2.0 * 2070e6
