@@ -294,14 +294,17 @@ spgemm_status spgemm_autotune_batch(int64_t n_jobs, const spgemm_csr_in* A, cons
                                     void* stream, spgemm_opts* best, spgemm_tune_report* report);
 
 /* C = A*B without allocating any device memory, for callers that cannot allocate while they
- * call (for example code being captured into a CUDA graph, services that reserve the whole
- * device up front, or real-time loops that must not wait on an allocator). The paper has no
- * counterpart; it is an interface convenience of this library.
+ * call: services that reserve the whole device up front and hand out fixed buffers (an
+ * allocation would fail or take memory promised to someone else), and real-time loops that
+ * must not block in an allocator or risk its failure. The paper has no counterpart; it is an
+ * interface convenience of this library.
  * A and B: device CSR (int32 or int64 row_ptr), FP64 values, canonical. C: caller-allocated
  * device arrays, row_ptr[A.rows + 1] (C->idx64_rowptr selects its type) and col/val with room
  * for nnz_capacity entries. *nnz_c receives nnz(C). Limits: A.rows <= 65536 and every row of C
  * has at most 4096 entries (else SPGEMM_ERR_UNSUPPORTED); nnz(C) > nnz_capacity returns
- * SPGEMM_ERR_INVALID_ARG with *nnz_c set and nothing written to C.
+ * SPGEMM_ERR_INVALID_ARG with *nnz_c set and nothing written to C. A column of A outside
+ * [0, B.rows) or of B outside [0, B.cols) returns SPGEMM_ERR_INVALID_CSR (other CSR invariants
+ * are not checked here).
  * Scratch: one fixed device array of about 770 KB inside the library, which every GPU that
  * loads the library holds until the process exits. The first call on a device looks up that
  * array's address (cudaGetSymbolAddress, with the device current), so make the first call

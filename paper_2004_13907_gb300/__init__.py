@@ -314,7 +314,8 @@ def spgemm_multiply_noalloc(A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, stream=Non
     is too small."""
     a, b, c = A.as_in(), B.as_in(), C.as_out()
     nnz = ctypes.c_int64()
-    st = lib().spgemm_multiply_noalloc(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), C.col.numel(),
+    cap = min(C.col.numel(), C.val.numel())   # the kernels write both arrays up to the capacity
+    st = lib().spgemm_multiply_noalloc(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), cap,
                                        ctypes.byref(nnz), _stream_handle(stream))
     if st != 0:
         msg = lib().spgemm_last_error()

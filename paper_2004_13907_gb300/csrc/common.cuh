@@ -15,7 +15,6 @@ enum : uint32_t {
   kErrInvalidCsr = 1u,
   kErrHashFull = 2u,       // a hash table ran out of slots (cannot happen with exact sizing)
   kErrWindowPlan = 4u,     // a window held more entries than its table
-  kErrTimeout = 8u,
   kErrCount = 16u,         // a row wrote a different number of entries than counted
 };
 

@@ -1,10 +1,9 @@
 // spgemm_multiply_noalloc: C = A*B for small products without any device allocation.
 //
-// Some callers cannot allocate device memory while they call into this library: code that
-// is being captured into a CUDA graph on a stream where an allocation would break the
-// capture, services that reserve the whole device up front and hand out fixed buffers, and
-// real-time loops that must never block in an allocator or risk its failure. This entry
-// point serves them. The caller passes A, B and C's arrays (with a capacity); the scratch the
+// Some callers cannot allocate device memory while they call into this library: services
+// that reserve the whole device up front and hand out fixed buffers (an allocation would
+// fail or steal memory another tenant was promised), and real-time loops that must never
+// block in an allocator or risk its failure. This entry point serves them. The caller passes A, B and C's arrays (with a capacity); the scratch the
 // kernels need (row counts of C, row offsets, an error word and the total) lives in one
 // file-scope device array of fixed size, kScratchBytes, which every GPU that loads the library
 // keeps until the process exits.
@@ -93,7 +92,10 @@ __device__ __forceinline__ void na_for_each_product(const InCsr& A, const InCsr&
     int owner = 0;
     for (int32_t p = threadIdx.x; p < total; p += kThreads) {
       owner = find_owner(s_excl, nvalid, p, owner);
-      f(s_bs[owner] + (p - s_excl[owner]), base + owner);
+      const int64_t j = s_bs[owner] + (p - s_excl[owner]);
+      const int32_t c = B.col[j];
+      if (c < 0 || c >= B.cols) atomicOr(err, kNaInvalid);   // B is not canonical: no product for it
+      else f(j, base + owner);
     }
     __syncthreads();
   }
@@ -281,15 +283,18 @@ extern "C" spgemm_status spgemm_multiply_noalloc(const spgemm_csr_in* A, const s
   const unsigned grid = static_cast<unsigned>(A->rows < 4 * 152 ? (A->rows > 0 ? A->rows : 1) : 4 * 152);
   if (A->rows > 0) {
     k_na_symbolic<<<grid, kThreads, kSlots * 4, s>>>(a, b, sc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "launching the no-allocation symbolic pass");
   }
   k_na_scan<<<1, 1024, 0, s>>>(A->rows, sc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "launching the no-allocation row scan");
   uint32_t herr = 0;
   int64_t htotal = 0;
   e = cudaMemcpyAsync(&herr, sc.err, sizeof(herr), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&htotal, sc.total, sizeof(htotal), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e, "symbolic pass of the no-allocation product");
-  if (herr & kNaInvalid) return set_error_msg(SPGEMM_ERR_INVALID_CSR, "a column index of A is outside B's rows");
+  if (herr & kNaInvalid)
+    return set_error_msg(SPGEMM_ERR_INVALID_CSR, "a column index of A is outside B's rows, or of B outside B's columns");
   if (herr & (kNaTooLarge | kNaHashFull))
     return set_error_msg(SPGEMM_ERR_UNSUPPORTED, "a row of C has more than %d entries", kMaxRowEntries);
   *nnz_c = htotal;
@@ -301,9 +306,12 @@ extern "C" spgemm_status spgemm_multiply_noalloc(const spgemm_csr_in* A, const s
   if (htotal > 0 && (!C->col || !C->val)) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "C arrays are NULL");
   k_na_rowptr<<<static_cast<unsigned>((A->rows + 256) / 256), 256, 0, s>>>(A->rows + 1, sc, C->row_ptr,
                                                                             C->idx64_rowptr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "launching the no-allocation row pointers");
   if (A->rows > 0 && htotal > 0) {
-    cudaFuncSetAttribute(k_na_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlots * 12);
+    e = cudaFuncSetAttribute(k_na_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlots * 12);
+    if (e != cudaSuccess) return cuda_status(e, "raising the numeric kernel's shared memory limit");
     k_na_numeric<<<grid, kThreads, kSlots * 12, s>>>(a, b, sc, C->col, static_cast<double*>(C->val));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "launching the no-allocation numeric pass");
   }
   e = cudaMemcpyAsync(&herr, sc.err, sizeof(herr), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

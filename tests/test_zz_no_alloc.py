@@ -1,7 +1,8 @@
 """spgemm_multiply_noalloc, the entry point for callers that cannot allocate device memory
-(graph capture, fixed device reservations, real-time loops): its output must match the
-regular plan/symbolic/numeric path, called through the C ABI, on two calls in a row that
-reuse its fixed scratch array. This file is collected last on purpose."""
+(services holding a fixed device reservation, real-time loops that must not block in an
+allocator): its output must match the regular plan/symbolic/numeric path, called through the
+C ABI, on two calls in a row that reuse its fixed scratch array. This file is collected last
+on purpose."""
 
 import numpy as np
 import pytest
@@ -68,3 +69,47 @@ def test_noalloc_capacity_and_limits():
     with pytest.raises(sp.SpgemmError) as ei:
         _noalloc(sp, dbig, dB, 10)
     assert ei.value.name == "UNSUPPORTED"
+
+
+def _csr(rows, cols, row_ptr, col, val):
+    return synth.CSR(rows, cols, np.asarray(row_ptr, np.int64), np.asarray(col, np.int32),
+                     np.asarray(val, np.float64))
+
+
+def test_noalloc_row_entry_limit_4096_and_4097():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2004_13907_gb300 as sp
+    A = _csr(1, 1, [0, 1], [0], [2.0])
+    for n, ok in ((4096, True), (4097, False)):
+        B = _csr(1, n, [0, n], np.arange(n), np.linspace(-1.0, 1.0, n))
+        dA, dB = sp.DeviceCSR.from_host(A, "cuda"), sp.DeviceCSR.from_host(B, "cuda")
+        if ok:
+            got = _noalloc(sp, dA, dB, n)
+            assert int(got.col.numel()) == n
+            assert np.array_equal(got.col.cpu().numpy(), np.arange(n))
+            assert np.array_equal(got.val.cpu().numpy(), 2.0 * B.val)   # one exact product per entry
+        else:
+            with pytest.raises(sp.SpgemmError) as ei:
+                _noalloc(sp, dA, dB, n)
+            assert ei.value.name == "UNSUPPORTED"
+
+
+def test_noalloc_rejects_out_of_range_columns():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2004_13907_gb300 as sp
+    B = _csr(2, 3, [0, 2, 3], [0, 2, 1], [1.0, 2.0, 3.0])
+    bad_a = _csr(1, 2, [0, 1], [5], [1.0])            # column of A >= B.rows
+    good_a = _csr(1, 2, [0, 2], [0, 1], [1.0, 1.0])
+    bad_b = _csr(2, 3, [0, 2, 3], [0, 7, 1], [1.0, 2.0, 3.0])   # column of B >= B.cols
+    for A_, B_ in ((bad_a, B), (good_a, bad_b)):
+        dA, dB = sp.DeviceCSR.from_host(A_, "cuda"), sp.DeviceCSR.from_host(B_, "cuda")
+        with pytest.raises(sp.SpgemmError) as ei:
+            _noalloc(sp, dA, dB, 16)
+        assert ei.value.name == "INVALID_CSR"
+    # the scratch array is usable again after a refused call
+    dA, dB = sp.DeviceCSR.from_host(good_a, "cuda"), sp.DeviceCSR.from_host(B, "cuda")
+    got = _noalloc(sp, dA, dB, 16)
+    assert np.array_equal(got.col.cpu().numpy(), [0, 1, 2])
+    assert np.array_equal(got.val.cpu().numpy(), [1.0, 3.0, 2.0])
