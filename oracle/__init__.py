@@ -4,7 +4,10 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench
 import this package. The CUDA library never calls it and shares no code with it.
 
 ``spgemm`` is the paper's row-by-row formulation (Algorithm 1, Sec. III-A) as a plain
-ordered-map Gustavson product in FP64 (``gustavson.cpp``), threaded over rows.
+ordered-map Gustavson product in FP64 (``gustavson.cpp``), threaded over rows. With
+``exact_sum=True`` every value is instead the sum of the entry's rounded partial products
+rounded once (correctly rounded, ties to even), kept exactly as Shewchuk's non-overlapping
+partial sums until the end.
 ``products_per_row`` is the definition of the per-row intermediate-product count used by
 the method's flop metric: P_i = sum over stored (i, k) of A of nnz(row k of B), the number
 of partial products Algorithm 1 forms for row i (its B rows "streamed" for row i, Sec. III-A).
@@ -52,6 +55,9 @@ def _load():
             lib.oracle_spgemm.restype = P
             lib.oracle_spgemm.argtypes = [ctypes.c_int64, P, P, P, P, P, P, P, ctypes.c_int64,
                                           ctypes.c_int]
+            lib.oracle_spgemm_ex.restype = P
+            lib.oracle_spgemm_ex.argtypes = [ctypes.c_int64, P, P, P, P, P, P, P, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_int]
             lib.oracle_nnz.restype = ctypes.c_int64
             lib.oracle_nnz.argtypes = [P]
             lib.oracle_threads.restype = ctypes.c_int
@@ -84,12 +90,13 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
 
 
-def spgemm(A, B, rows=None, threads: int = 0, values: bool = True) -> OracleOut:
+def spgemm(A, B, rows=None, threads: int = 0, values: bool = True, exact_sum: bool = False) -> OracleOut:
     """C = A*B for the given rows of A (all rows when ``rows`` is None).
 
     A and B are ``synth.CSR``-like objects (rows, cols, row_ptr, col, val). Values are
     taken in FP64 (FP32 inputs are widened exactly). ``values=False`` multiplies the
-    patterns (every stored value taken as 1).
+    patterns (every stored value taken as 1). ``exact_sum=True`` rounds each entry's sum of
+    rounded products once instead of summing in stored order.
     """
     if A.cols != B.rows:
         raise ValueError("inner dimensions differ")
@@ -102,8 +109,8 @@ def spgemm(A, B, rows=None, threads: int = 0, values: bool = True) -> OracleOut:
     b_val = np.ascontiguousarray(B.val, dtype=np.float64) if values else None
     r = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
     nrows = A.rows if r is None else r.shape[0]
-    h = lib.oracle_spgemm(A.rows, _ptr(a_rp), _ptr(a_col), _ptr(a_val), _ptr(b_rp), _ptr(b_col),
-                          _ptr(b_val), _ptr(r), nrows, threads)
+    h = lib.oracle_spgemm_ex(A.rows, _ptr(a_rp), _ptr(a_col), _ptr(a_val), _ptr(b_rp), _ptr(b_col),
+                             _ptr(b_val), _ptr(r), nrows, threads, 1 if exact_sum else 0)
     try:
         nnz = lib.oracle_nnz(h)
         rp = np.empty(nrows + 1, dtype=np.int64)

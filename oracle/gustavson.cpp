@@ -16,7 +16,14 @@
 // column, which holds the partial products of one row already merged.
 //
 // Arithmetic: FP64, each product rounded once (the build passes -ffp-contract=off so no
-// multiply-add is fused), summed in stored order. Beside each value it returns
+// multiply-add is fused), summed in stored order. A second variant (exact_sum) returns for each
+// entry the sum of its rounded products rounded once to FP64 (round to nearest, ties to even):
+// the exact sum of the same partial products, with no rounding in between. It keeps each
+// entry's running sum as a list of non-overlapping partial sums (Shewchuk, "Adaptive precision
+// floating-point arithmetic and fast robust geometric predicates", 1997: TwoSum growth of an
+// expansion) and rounds it once at the end, from the largest partial down, with the half-way
+// correction that makes the result correctly rounded. An entry with a non-finite product takes
+// the stored-order sum. Beside each value it returns
 // mag = sum of |a_ik*b_kj| (the scale of the entry's rounding error) and the number of
 // terms that entry received. Inputs in FP32 are widened to FP64 by the caller; that is
 // exact, and so is every FP32*FP32 product in FP64.
@@ -51,6 +58,79 @@ struct OracleResult {
   int threads = 0;
 };
 
+// Exact sum of one entry: partials[] hold non-overlapping FP64 values whose exact sum is the
+// exact sum of the terms added so far (each TwoSum below is error-free).
+struct ExactEntry {
+  std::vector<double> partials;
+  double plain = 0.0;   // stored-order sum (for non-finite terms)
+  double mag = 0.0;
+  int32_t terms = 0;
+  bool finite = true;
+
+  void add(double x) {
+    plain = plain + x;
+    if (!std::isfinite(x)) finite = false;
+    if (!finite) return;
+    size_t n = 0;
+    for (size_t q = 0; q < partials.size(); ++q) {
+      double y = partials[q];
+      if (std::fabs(x) < std::fabs(y)) std::swap(x, y);
+      const double hi = x + y;          // |x| >= |y|: hi + lo == x + y exactly
+      const double lo = y - (hi - x);
+      if (lo != 0.0) partials[n++] = lo;
+      x = hi;
+    }
+    partials.resize(n);
+    partials.push_back(x);
+  }
+
+  // The exact sum of the partials rounded once to FP64 (nearest, ties to even).
+  double rounded() const {
+    if (!finite) return plain;
+    size_t n = partials.size();
+    if (n == 0) return 0.0;
+    double hi = partials[--n];
+    double lo = 0.0;
+    while (n > 0) {   // add partials from the top while the sum stays exact
+      const double x = hi;
+      const double y = partials[--n];
+      hi = x + y;
+      lo = y - (hi - x);
+      if (lo != 0.0) break;
+    }
+    // hi is the sum rounded to nearest unless lo is exactly half an ulp of hi and the partials
+    // below push the true sum past the half-way point (same sign as lo): then round away
+    if (n > 0 && ((lo < 0.0 && partials[n - 1] < 0.0) || (lo > 0.0 && partials[n - 1] > 0.0))) {
+      const double y = lo * 2.0;
+      const double x = hi + y;
+      if (y == x - hi) hi = x;
+    }
+    return hi;
+  }
+};
+
+static void oracle_row_exact(int64_t i, const int64_t* a_rp, const int32_t* a_col, const double* a_val,
+                             const int64_t* b_rp, const int32_t* b_col, const double* b_val, RowOut& out) {
+  std::map<int32_t, ExactEntry> acc;
+  for (int64_t p = a_rp[i]; p < a_rp[i + 1]; ++p) {
+    const int32_t k = a_col[p];
+    const double a = a_val ? a_val[p] : 1.0;
+    for (int64_t q = b_rp[k]; q < b_rp[k + 1]; ++q) {
+      const double prod = a * (b_val ? b_val[q] : 1.0);
+      ExactEntry& e = acc[b_col[q]];
+      e.add(prod);
+      e.mag = e.mag + std::fabs(prod);
+      e.terms += 1;
+    }
+  }
+  for (const auto& kv : acc) {
+    out.col.push_back(kv.first);
+    out.val.push_back(kv.second.rounded());
+    out.mag.push_back(kv.second.mag);
+    out.terms.push_back(kv.second.terms);
+  }
+}
+
 static void oracle_row(int64_t i, const int64_t* a_rp, const int32_t* a_col, const double* a_val,
                        const int64_t* b_rp, const int32_t* b_col, const double* b_val,
                        RowOut& out) {
@@ -83,10 +163,11 @@ extern "C" {
 // Computes rows `rows[0..nrows)` of C = A*B (all m rows when rows == NULL).
 // a_val / b_val may be NULL (pattern only: every stored value taken as 1).
 // threads <= 0 uses std::thread::hardware_concurrency().
-OracleResult* oracle_spgemm(int64_t m, const int64_t* a_rp, const int32_t* a_col,
-                            const double* a_val, const int64_t* b_rp, const int32_t* b_col,
-                            const double* b_val, const int64_t* rows, int64_t nrows,
-                            int threads) {
+// exact_sum != 0: every value is the correctly rounded sum of the entry's partial products.
+OracleResult* oracle_spgemm_ex(int64_t m, const int64_t* a_rp, const int32_t* a_col,
+                               const double* a_val, const int64_t* b_rp, const int32_t* b_col,
+                               const double* b_val, const int64_t* rows, int64_t nrows,
+                               int threads, int exact_sum) {
   OracleResult* r = new OracleResult();
   const int64_t count = rows ? nrows : m;
   r->rows.resize(static_cast<size_t>(count));
@@ -103,7 +184,8 @@ OracleResult* oracle_spgemm(int64_t m, const int64_t* a_rp, const int32_t* a_col
       const int64_t e = s + chunk < count ? s + chunk : count;
       for (int64_t t = s; t < e; ++t) {
         const int64_t i = rows ? rows[t] : t;
-        oracle_row(i, a_rp, a_col, a_val, b_rp, b_col, b_val, r->rows[t]);
+        if (exact_sum) oracle_row_exact(i, a_rp, a_col, a_val, b_rp, b_col, b_val, r->rows[t]);
+        else oracle_row(i, a_rp, a_col, a_val, b_rp, b_col, b_val, r->rows[t]);
       }
     }
   };
@@ -118,6 +200,13 @@ OracleResult* oracle_spgemm(int64_t m, const int64_t* a_rp, const int32_t* a_col
   for (const auto& ro : r->rows) nnz += static_cast<int64_t>(ro.col.size());
   r->nnz = nnz;
   return r;
+}
+
+OracleResult* oracle_spgemm(int64_t m, const int64_t* a_rp, const int32_t* a_col,
+                            const double* a_val, const int64_t* b_rp, const int32_t* b_col,
+                            const double* b_val, const int64_t* rows, int64_t nrows,
+                            int threads) {
+  return oracle_spgemm_ex(m, a_rp, a_col, a_val, b_rp, b_col, b_val, rows, nrows, threads, 0);
 }
 
 int64_t oracle_nnz(const OracleResult* r) { return r->nnz; }

@@ -279,3 +279,66 @@ def test_fp32_inputs_widen_exactly():
     Ad = A.to_dense()
     ref = Ad @ Ad
     assert np.all(np.abs(d - ref) <= 1e-12 * (np.abs(Ad) @ np.abs(Ad)) + 1e-300)
+
+
+# ---- exact_sum: every value the correctly rounded sum of the entry's rounded products ----
+
+def _one_row(products):
+    """A 1 x t row of ones times a t x 1 column holding the given products: one entry whose
+    partial products are exactly `products`, in this order."""
+    t = len(products)
+    A = synth.CSR(1, t, np.array([0, t], np.int64), np.arange(t, dtype=np.int32), np.ones(t))
+    B = synth.CSR(t, 1, np.arange(t + 1, dtype=np.int64), np.zeros(t, np.int32), np.array(products, np.float64))
+    return A, B
+
+
+def test_exact_sum_closed_forms():
+    # 1e16 + 1 - 1e16: stored order loses the 1, the exact sum is 1
+    A, B = _one_row([1e16, 1.0, -1e16])
+    assert oracle.spgemm(A, B).val[0] == 0.0
+    assert oracle.spgemm(A, B, exact_sum=True).val[0] == 1.0
+    # a tie rounds to even; anything past the tie rounds away
+    A, B = _one_row([1.0, 2.0 ** -53])
+    assert oracle.spgemm(A, B, exact_sum=True).val[0] == 1.0
+    A, B = _one_row([1.0, 2.0 ** -53, 2.0 ** -80])
+    assert oracle.spgemm(A, B, exact_sum=True).val[0] == 1.0 + 2.0 ** -52
+    A, B = _one_row([1.0 + 2.0 ** -52, 2.0 ** -53])   # odd last bit: the tie goes up
+    assert oracle.spgemm(A, B, exact_sum=True).val[0] == 1.0 + 2.0 ** -51
+    A, B = _one_row([-(1.0 + 2.0 ** -52), -(2.0 ** -53)])
+    assert oracle.spgemm(A, B, exact_sum=True).val[0] == -(1.0 + 2.0 ** -51)
+    # full cancellation of many terms stays a stored zero
+    A, B = _one_row([0.1, 0.2, 0.3, -0.1, -0.2, -0.3])
+    out = oracle.spgemm(A, B, exact_sum=True)
+    assert out.nnz == 1 and out.val[0] == 0.0
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5])
+def test_exact_sum_equals_math_fsum(seed):
+    """Against Python's math.fsum (an exactly rounded summation in the standard library) over
+    the products of each entry, on values spread over 16 decades with signs mixed."""
+    import math
+    rng = np.random.default_rng(seed)
+    A = synth.random_small(30, 40, 0.4, seed)
+    B = synth.random_small(40, 25, 0.4, seed + 100)
+    A = synth.CSR(A.rows, A.cols, A.row_ptr, A.col, A.val * 10.0 ** rng.uniform(-8, 8, A.nnz))
+    B = synth.CSR(B.rows, B.cols, B.row_ptr, B.col, B.val * 10.0 ** rng.uniform(-8, 8, B.nnz))
+    out = oracle.spgemm(A, B, exact_sum=True)
+    for i in range(A.rows):
+        acc = {}
+        for q in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            k = A.col[q]
+            for t in range(B.row_ptr[k], B.row_ptr[k + 1]):
+                acc.setdefault(int(B.col[t]), []).append(float(A.val[q]) * float(B.val[t]))
+        s = slice(out.row_ptr[i], out.row_ptr[i + 1])
+        assert list(out.col[s]) == sorted(acc)
+        want = np.array([math.fsum(acc[int(j)]) for j in out.col[s]])
+        assert np.array_equal(out.val[s], want)
+
+
+def test_exact_sum_equals_stored_order_on_integers():
+    A = synth.rmat(9, 8, seed=7)
+    A = synth.CSR(A.rows, A.cols, A.row_ptr, A.col, np.floor(A.val * 8.0) - 3.0)
+    a = oracle.spgemm(A, A)
+    b = oracle.spgemm(A, A, exact_sum=True)
+    assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col)
+    assert np.array_equal(a.val, b.val) and np.array_equal(a.mag, b.mag) and np.array_equal(a.terms, b.terms)
