@@ -201,7 +201,7 @@ def run_ours(args):
     precs = {name: prec for name, _, prec in specs}
     dev = [(name, M, sp.DeviceCSR.from_host(M, "cuda")) for name, M in mats]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    opts = sp.spgemm_opts_default(record_timings=1)
+    opts = sp.spgemm_opts_default(record_timings=1, fp64_accumulate=args.fp64_accumulate)
     stream = torch.cuda.current_stream()
 
     def step(collect=None):
@@ -291,6 +291,7 @@ def run_ours(args):
             "rows": d["rows"], "products": info["products"], "nnz_c": info["nnz_c"],
             "stage_ms": {k: round(float(np.mean(v)), 4) for k, v in d["stages"].items() if np.mean(v) > 0},
             "kernel_ms_sum": round(tot, 4),
+            "rows_redone_fp64": info["f32c_rerun_rows"],
             "numeric_ms": round(sum(float(np.mean(d["stages"][k])) for k in
                                     ("num_rowptr", "num_window", "num_expand", "num_block", "num_warp",
                                      "num_tiny")), 4),
@@ -766,6 +767,9 @@ def main():
     ap.add_argument("--workload", default="lap2d1024+rmat20",
                     choices=sorted(WORKLOADS) + ["batch_small", "batch_mid", "serve"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-accumulate", type=int, default=0, choices=[0, 1, 2],
+                    help="FP64 sums: 0 shared atomics (default), 1 exact fixed point on the windowed rows, "
+                         "2 deterministic (every row windowed, exact)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-products-per-step", type=float, default=2e8)

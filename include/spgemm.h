@@ -125,7 +125,19 @@ typedef struct spgemm_opts {
                                  bytes per 4096 columns of the row), so the numeric pass copies
                                  them instead of marking every partial product again; rows beyond
                                  the budget are marked again (default 49152; 0: never store) */
-  int32_t reserved[11];
+  int32_t fp64_accumulate;    /* how FP64 sums are formed (F64 plans):
+                                 0 (default): FP64 shared-memory atomics (fastest; the order of
+                                   the additions, so the last bits, may vary from run to run);
+                                 1: rows of the windowed path (more entries of C than a block
+                                   table) sum every entry exactly in integer fixed point and round
+                                   it once: the correctly rounded sum of the entry's products;
+                                 2: deterministic: every non-empty row takes the windowed path
+                                   with that exact sum, so every value of C is the correctly
+                                   rounded sum of its FP64 partial products and repeats bit for
+                                   bit. In 1 and 2 a row whose products span more than about 2^40
+                                   in magnitude, or hold subnormal or non-finite values, is redone
+                                   with FP64 atomics (counted in f32c_rerun_rows) */
+  int32_t reserved[10];
 } spgemm_opts;
 
 /* Opaque plan: the work description of one product (row counts, row classes, row
@@ -149,7 +161,9 @@ typedef struct spgemm_plan_info {
   int64_t num_class_annz[16];      /* sum of nnz(A_i) over each numeric class */
   int64_t num_class_cnnz[16];      /* sum of nnz(C_i) over each numeric class */
   int64_t workspace_bytes;     /* device workspace held by the plan */
-  int64_t f32c_rerun_rows;     /* rows recomputed in FP64 by the last F32 numeric pass */
+  int64_t f32c_rerun_rows;     /* rows recomputed in FP64 by the last numeric pass: F32 rows over
+                                  the compensated bound; FP64 windowed rows outside the exact
+                                  fixed-point range (read by spgemm_plan_check) */
   int64_t kernel_launches;     /* CUDA kernels this plan has launched so far */
   int32_t needs_rowptr64;
   int32_t state;               /* 0 planned, 1 symbolic done, 2 numeric done */

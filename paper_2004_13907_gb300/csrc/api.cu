@@ -248,7 +248,16 @@ spgemm_status spgemm_plan_get_info(const spgemm_plan_t* plan, spgemm_plan_info* 
 spgemm_status spgemm_plan_check(spgemm_plan_t* plan, void* stream) {
   clear_error_msg();
   if (!plan) return set_error_msg(SPGEMM_ERR_INVALID_ARG, "plan is NULL");
-  return read_device_error(plan, static_cast<cudaStream_t>(stream));
+  const spgemm_status st = read_device_error(plan, static_cast<cudaStream_t>(stream));
+  if (st == SPGEMM_OK && plan->fx_rerun_pending) {
+    int32_t n = 0;
+    cudaError_t e = cudaMemcpyAsync(&n, plan->counters + 6, sizeof(n), cudaMemcpyDeviceToHost,
+                                    static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_status(e, "reading the FP64 rerun count");
+    plan->f32c_rerun_rows = n;
+  }
+  return st;
 }
 
 spgemm_status spgemm_plan_get_timings(spgemm_plan_t* plan, spgemm_timings* t) {

@@ -129,9 +129,130 @@ __device__ __forceinline__ bool f32c_within_bound(float res, float mag, int t) {
   return g * g * mag_ub <= u * fabsf(res) * (1.0f - 8.0f * u);
 }
 
-// Modes of the accumulating kernels: FP64 values; FP32 values with compensated FP32
-// accumulation; FP32 values recomputed in FP64 and rounded once to FP32.
-enum : int { kModeF64 = 0, kModeF32C = 1, kModeF32R = 2 };
+// Modes of the accumulating kernels: FP64 values summed with FP64 shared atomics; FP32 values
+// with compensated FP32 accumulation; FP32 values recomputed in FP64 and rounded once to FP32;
+// FP64 values summed exactly in integer fixed point (below).
+enum : int { kModeF64 = 0, kModeF32C = 1, kModeF32R = 2, kModeF64X = 3 };
+
+// Exact fixed-point accumulation of FP64 partial products (kModeF64X).
+//
+// GB300 runs FP64 arithmetic at 2 lanes per clock per SM and a shared-memory FP64 atomic add at
+// about one per clock per SM, while a 32-bit shared integer atomic add runs at about 12-15 per
+// clock per SM. So an entry of C is accumulated as an integer: every partial product p = a*b
+// (rounded once, as any FP64 product) is written as q * 2^lsb with q an integer, and q is split
+// into four 32-bit limbs (three unsigned 22-bit chunks and a signed top part) that are added
+// with integer atomics. Integer addition is exact and associative, so the sum of an entry does
+// not depend on the order of its terms; it is rounded once to FP64 at the end.
+//
+// lsb is chosen per row from bounds of the operands: |p| < 2^(eA + eB - 2044) for biased
+// exponents eA, eB of a and b, and the row's bound E is the largest eA + eB' over its A entries
+// (eB' the largest exponent in the named B row). With H = ceil(log2(nnz(A_i) + 1)) (an entry has
+// at most nnz(A_i) terms) and Q = kFxTopBits - H, lsb = E - 2044 - Q keeps |q| < 2^(Q+1), and the
+// signed top limb below 2^31 for any number of terms up to 2^H. Products whose q would keep fewer
+// than 45 significant bits, subnormal products and non-finite ones make the row fall back to the
+// FP64 path; every other product is exact (q >= 2^44 * 2^lsb when it is truncated at all), so an
+// entry's error is at most 2^-44 * sum|p| plus the final rounding, 2^-53 |c|.
+// The lower limbs take at most 2^9 products between normalisations (512 A entries per chunk),
+// so they never wrap: 513 * (2^22 - 1) < 2^32.
+constexpr int kFxLimbBits = 22;
+constexpr uint32_t kFxLimbMask = (1u << kFxLimbBits) - 1u;
+constexpr int kFxTopBits = 95;
+constexpr int kFxMinShift = -8;   // q keeps 53 + shift significant bits
+
+// Biased exponent field of x.
+__device__ __forceinline__ int fx_exponent(double x) {
+  return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7ffu);
+}
+
+// Limbs of p / 2^lsb, with sh0 = 1075 + lsb. Returns false when p cannot be taken exactly
+// enough (non-finite, subnormal, or fewer than 45 significant bits left); ±0 gives zero limbs.
+__device__ __forceinline__ bool fx_split(double p, int sh0, uint32_t& c0, uint32_t& c1, uint32_t& c2,
+                                         int32_t& ct) {
+  const unsigned long long pb = static_cast<unsigned long long>(__double_as_longlong(p));
+  const int e = static_cast<int>((pb >> 52) & 0x7ffu);
+  const unsigned long long f = pb & ((1ull << 52) - 1ull);
+  c0 = c1 = c2 = 0u;
+  ct = 0;
+  if (e == 0) return f == 0ull;
+  if (e == 0x7ff) return false;
+  const int sh = e - sh0;   // q = (f + 2^52) * 2^sh, sh <= kFxTopBits - 52 < 64 by the choice of lsb
+  if (sh < kFxMinShift) return false;
+  const unsigned long long m = f | (1ull << 52);
+  unsigned long long lo, hi;
+  if (sh >= 0) {
+    lo = m << sh;
+    hi = sh > 0 ? (m >> (64 - sh)) : 0ull;
+  } else {
+    lo = m >> (-sh);
+    hi = 0ull;
+  }
+  if (pb >> 63) {   // two's complement of the 128-bit hi:lo
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    lo = 0ull - lo;
+  }
+  c0 = static_cast<uint32_t>(lo) & kFxLimbMask;
+  c1 = static_cast<uint32_t>(lo >> kFxLimbBits) & kFxLimbMask;
+  c2 = static_cast<uint32_t>((lo >> (2 * kFxLimbBits)) | (hi << (64 - 2 * kFxLimbBits))) & kFxLimbMask;
+  ct = static_cast<int32_t>(static_cast<long long>(hi) >> (3 * kFxLimbBits - 64));
+  return true;
+}
+
+// Carries the low limbs of one accumulator into the next, leaving each below 2^22.
+__device__ __forceinline__ void fx_normalise(uint32_t& l0, uint32_t& l1, uint32_t& l2, int32_t& lt) {
+  l1 += l0 >> kFxLimbBits;
+  l0 &= kFxLimbMask;
+  l2 += l1 >> kFxLimbBits;
+  l1 &= kFxLimbMask;
+  lt += static_cast<int32_t>(l2 >> kFxLimbBits);
+  l2 &= kFxLimbMask;
+}
+
+// The accumulated value (lt * 2^66 + l2 * 2^44 + l1 * 2^22 + l0) * 2^lsb rounded to the nearest
+// FP64 (ties to even). Sets *bad when the result overflows or is subnormal (the row then takes
+// the FP64 path). An exact zero gives +0. The low limbs may hold up to 32 bits each.
+__device__ __forceinline__ double fx_to_double(uint32_t l0, uint32_t l1, uint32_t l2, int32_t lt, int lsb,
+                                               bool* bad) {
+  // the value as a signed 128-bit hi:lo (hi two's complement)
+  const unsigned long long lo1 = static_cast<unsigned long long>(l0) + (static_cast<unsigned long long>(l1) << 22);
+  const unsigned long long t2 = static_cast<unsigned long long>(l2) << 44;   // low 64 bits of l2 * 2^44
+  unsigned long long lo = lo1 + t2;
+  long long hi = static_cast<long long>(lt) * 4 + static_cast<long long>(l2 >> 20) + (lo < lo1 ? 1 : 0);
+  if (hi == 0 && lo == 0ull) return 0.0;
+  const bool neg = hi < 0;
+  unsigned long long uh = static_cast<unsigned long long>(hi);
+  if (neg) {
+    uh = ~uh + (lo == 0ull ? 1ull : 0ull);
+    lo = 0ull - lo;
+  }
+  // normalise so that the leading one is bit 127 of uh:lo
+  const int lz = uh ? __clzll(static_cast<long long>(uh)) : 64 + __clzll(static_cast<long long>(lo));
+  if (lz >= 64) {
+    uh = lo << (lz - 64);
+    lo = 0ull;
+  } else if (lz > 0) {
+    uh = (uh << lz) | (lo >> (64 - lz));
+    lo <<= lz;
+  }
+  int b = 127 - lz;   // position of the leading one in the unnormalised value
+  unsigned long long mant = uh >> 11;
+  const bool rbit = (uh >> 10) & 1ull;
+  const bool sticky = (uh & 0x3ffull) != 0ull || lo != 0ull;
+  if (rbit && (sticky || (mant & 1ull))) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++b;
+    }
+  }
+  const int biased = b + lsb + 1023;
+  if (biased <= 0 || biased >= 2047) {
+    *bad = true;
+    return 0.0;
+  }
+  const unsigned long long bits = (static_cast<unsigned long long>(neg) << 63) |
+                                  (static_cast<unsigned long long>(biased) << 52) | (mant & ((1ull << 52) - 1ull));
+  return __longlong_as_double(static_cast<long long>(bits));
+}
 
 // Knuth's multiplicative hash: the top log2S bits of key * floor(2^32 / phi).
 __device__ __forceinline__ uint32_t hash_slot(int32_t key, int log2S) {

@@ -153,6 +153,45 @@ struct GroupWalker {
   __device__ __forceinline__ int64_t first(int32_t p0) const {
     return obs + (p0 + static_cast<int32_t>(threadIdx.x & 31) - oex);
   }
+  // U consecutive groups from p0 (< hi, same on every lane) at once: lane l of group u gets the
+  // index into B of product p0 + 32u + l (-1 at or past hi) and its segment's value. When at most
+  // 32 segment boundaries fall among the 32U products, one load of the next 32 boundaries gives U
+  // masks (one per group) and every group's owners follow from them without waiting on the
+  // previous group; otherwise the groups are stepped one after the other.
+  template <int U>
+  __device__ __forceinline__ void step_many(int32_t p0, int32_t hi, int64_t (&j)[U], T (&val)[U]) {
+    static_assert(U >= 1 && U <= 8, "groups per step");
+    const int lane = static_cast<int>(threadIdx.x & 31);
+    const int t = o + 1 + lane;
+    const int32_t rel = (t <= nent ? c_excl[t] : 0x7fffffff) - p0;   // >= 0: o owns p0 or p0 - 1
+    const bool more = __shfl_sync(0xffffffffu, rel, 31) < 32 * U;  // a 33rd boundary may lie inside
+    if (more) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t g0 = p0 + 32 * u;
+        j[u] = -1;
+        val[u] = T(0);
+        if (g0 < hi) step(g0, hi, j[u], val[u]);
+      }
+      return;
+    }
+    int before = 0;   // boundaries in the earlier groups
+    int last = o;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const unsigned bit = (rel >= 32 * u && rel < 32 * (u + 1)) ? (1u << (rel - 32 * u)) : 0u;
+      const unsigned q = __reduce_or_sync(0xffffffffu, bit);
+      const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+      const int my = o + before + __popc(q & upto);
+      const int32_t p = p0 + 32 * u + lane;
+      j[u] = p < hi ? c_bs[my] + (p - c_excl[my]) : -1;
+      val[u] = p < hi ? load(my) : T(0);
+      before += __popc(q);
+      last = o + before;
+    }
+    // the owner of the last product of the last group becomes the cached segment
+    set(last);
+  }
   // Group g0 (< hi, same on every lane): the lane's index into B (-1 at or past hi) and the
   // value of its segment (T(0) at or past hi). A product below hi has its owner below nent.
   __device__ __forceinline__ void step(int32_t g0, int32_t hi, int64_t& j, T& val) {
@@ -239,13 +278,8 @@ __device__ __forceinline__ void block_range_for_each_product(const DevCsr& A, co
 #pragma unroll
           for (int u = 0; u < U; ++u) j[u] = j0 + 32 * u;
         } else {
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int32_t g0 = p0 + 32 * u;
-            j[u] = -1;
-            int unused;
-            if (g0 < hi) walk.step(g0, hi, j[u], unused);
-          }
+          int unused[U];
+          walk.step_many<U>(p0, hi, j, unused);
         }
         f(j);
       }

@@ -24,8 +24,10 @@
 // counterpart of REAP's CPU-side regularisation of B into bundles (Sec. II): it turns "find
 // the B entries of this row in this column range" into a table lookup.
 //
-// Sums are accumulated with shared-memory FP64 atomics, so their order may differ from run to
-// run; the pattern is always exact.
+// FP64 sums are accumulated with FP64 shared-memory atomics (kModeF64, the order of the additions
+// may vary from run to run) or, on request, exactly in integer fixed point (kModeF64X, see
+// common.cuh): a value then does not depend on the order of its terms and repeats bit for bit; a
+// row whose products span too wide a range takes kModeF64 afterwards. The pattern is always exact.
 #include "enumerate.cuh"
 
 namespace spg {
@@ -40,19 +42,20 @@ constexpr int kMaxWin = 256;                       // windows planned per batch
 constexpr int kUnroll = 4;                         // partial products in flight per thread
 // per entry: B row start, a_ik, B row number; per non-empty segment: start, prefix, entry
 constexpr int kSmemEnt = kNumThreads * (8 + 8 + 4) + kNumThreads * (8 + 4 + 4) + 16;
-// Per rank the windowed kernel keeps an FP64 sum (kModeF64, kModeF32R) or, in kModeF32C, an FP32
-// sum, its compensation, sum|p| and the term count. A window spans at most kSpanBlocks blocks:
-// 64 (256K columns) in FP64, 32 with the larger FP32 state, so that two blocks fit on an SM in
-// every mode.
+// Per rank the windowed kernel keeps an FP64 sum (kModeF64, kModeF32R), in kModeF32C an FP32
+// sum, its compensation, sum|p| and the term count, and in kModeF64X four 32-bit fixed-point
+// limbs. A window spans at most kSpanBlocks blocks: 64 (256K columns) with 8 bytes per rank, 32
+// with 16, so that two blocks fit on an SM in every mode.
 template <int Mode>
 struct WinGeom {
-  static constexpr int kSpanBlocks = Mode == kModeF32C ? 32 : 64;
+  static constexpr bool kWide = Mode == kModeF32C || Mode == kModeF64X;
+  static constexpr int kSpanBlocks = kWide ? 32 : 64;
   static constexpr int kSpanWords = kSpanBlocks * kBlockWords;   // bitmap words
   static constexpr int kWordsPerThread = kSpanWords / kNumThreads;
   static constexpr int kSmemBits = kSpanWords * 4;
   static constexpr int kSmemPre = kSpanWords * 2;
   static constexpr int kSmemGrp = (kSpanWords / kGroupWords) * 4;
-  static constexpr int kValBytes = Mode == kModeF32C ? 16 : 8;
+  static constexpr int kValBytes = kWide ? 16 : 8;
   static constexpr int kSmemVals = kRankCap * kValBytes;
   static constexpr int kSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemGrp + kSmemEnt + kCntCache * 2 +
                                     kMaxWin * 12;
@@ -126,7 +129,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     const int32_t* __restrict__ split, int32_t merge_cap, int32_t* __restrict__ ccol,
     void* __restrict__ cval_, int32_t* __restrict__ row_flag, const int32_t* __restrict__ abase,
     const int32_t* __restrict__ awidth, int64_t width_all, const uint32_t* __restrict__ wbits,
-    const int64_t* __restrict__ woff, uint32_t* err) {
+    const int64_t* __restrict__ woff, const uint16_t* __restrict__ bexp, const int32_t* __restrict__ dev_count,
+    uint32_t* err) {
   using G = WinGeom<Mode>;
   constexpr int kSmemBits = G::kSmemBits;
   constexpr int kSmemPre = G::kSmemPre;
@@ -140,6 +144,10 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
   float* f_c = f_s + kRankCap;                                //   compensation,
   float* f_m = f_c + kRankCap;                                //   sum |p|,
   int32_t* f_t = reinterpret_cast<int32_t*>(f_m + kRankCap);  //   term count
+  uint32_t* x_l0 = reinterpret_cast<uint32_t*>(win_smem);     // kModeF64X: low limbs,
+  uint32_t* x_l1 = x_l0 + kRankCap;
+  uint32_t* x_l2 = x_l1 + kRankCap;
+  int32_t* x_lt = reinterpret_cast<int32_t*>(x_l2 + kRankCap); //   signed top limb
   int32_t* colbuf = reinterpret_cast<int32_t*>(win_smem);
   uint32_t* bm = reinterpret_cast<uint32_t*>(win_smem + kSmemVals);
   uint16_t* pre = reinterpret_cast<uint16_t*>(win_smem + kSmemVals + kSmemBits);
@@ -164,8 +172,14 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
   const double* bv64 = static_cast<const double*>(B.val);
   const float* av32 = static_cast<const float*>(A.val);
   const float* bv32 = static_cast<const float*>(B.val);
-  auto a_at = [&](int64_t q) -> double { return Mode == kModeF64 ? av64[q] : static_cast<double>(av32[q]); };
+  auto a_at = [&](int64_t q) -> double {
+    return (Mode == kModeF64 || Mode == kModeF64X) ? av64[q] : static_cast<double>(av32[q]);
+  };
   const bool cnt_cached = nblocks <= kCntCache;
+  if (dev_count) {   // the rows to redo are listed on the device
+    const int64_t dc = *dev_count;
+    count = dc < count ? dc : count;
+  }
 
   for (int t = threadIdx.x; t < (kSmemVals + kSmemBits) / 16; t += kNumThreads)
     reinterpret_cast<uint4*>(win_smem)[t] = make_uint4(0u, 0u, 0u, 0u);
@@ -173,17 +187,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
 
   // Compacts the non-empty window segments of chunk [base, base + kNumThreads) of the row's A
   // entries into c_bs / c_excl / c_ent; returns (segments, products) through s_ctl[6..7].
-  // The split offsets of a resident row's entry for window [b0, b1), loaded early (with the
-  // window's stored bitmap) so that their latency overlaps the bitmap's.
-  auto split_of = [&](int64_t na, bool resident, int64_t b0, int64_t b1, int32_t& s0, int32_t& s1) {
-    s0 = -1;
-    s1 = -1;
-    if (resident && split && threadIdx.x < na) {
-      const int32_t* sp = split + int64_t(e_k[threadIdx.x]) * (nblocks + 1);
-      s0 = sp[b0];
-      s1 = sp[b1];
-    }
-  };
+  // ps0/ps1 (when >= 0): the entry's split offsets for the window, already in registers.
   auto build_chunk = [&](int64_t a0, int64_t na, int64_t base, bool resident, int64_t b0, int64_t b1,
                          int64_t w0, int64_t w1, int32_t ps0 = -1, int32_t ps1 = -1) {
     const int64_t e = base + threadIdx.x;
@@ -262,12 +266,37 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
       e_av[threadIdx.x] = a_at(a0 + threadIdx.x);
     }
     const uint16_t* cnts = cnt_cached ? s_cnt : gcnt;
+    // kModeF64X: the row's fixed-point scale from its largest possible product exponent
+    int fx_sh0 = 0, fx_lsb = 0;
+    bool row_bad = false;   // kModeF64X: the row needs the FP64 path
+    if constexpr (Mode == kModeF64X) {
+      int emax = 0;
+      for (int64_t q = threadIdx.x; q < na; q += kNumThreads)
+        emax = max(emax, fx_exponent(av64[a0 + q]) + static_cast<int>(bexp[A.col[a0 + q]]));
+      emax = __reduce_max_sync(0xffffffffu, emax);
+      if (lane == 0) s_scan32[wid] = emax;
+      __syncthreads();
+      emax = s_scan32[0];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) emax = max(emax, s_scan32[w]);
+      const int hbits = 32 - __clz(static_cast<int>(na < (int64_t(1) << 30) ? na : (int64_t(1) << 30)));
+      fx_lsb = emax - 2044 - (kFxTopBits - hbits);
+      fx_sh0 = 1075 + fx_lsb;
+    }
     int64_t out = c_off[i];
     const int64_t out_end = c_off[i + 1];
     // the symbolic pass stored this row's column bitmap: windows copy it instead of marking
     const int64_t toff = woff ? woff[slot] : -1;
     const bool stored = toff >= 0;
     int64_t next_b = 0;   // meaningful in warp 0 only
+    // Split offsets of a resident row's entry (thread t < na holds entry t): a window [b0, b1)
+    // needs the entry's offsets at b0 and b1. The blocks between two windows of the row hold none
+    // of its entries, so no B row it names has entries there either: the offset at the next
+    // window's b0 equals this window's at b1 (sp_prev1). The offset at the next window's b1 is
+    // loaded one window ahead (sp_pref), so its latency hides behind the current window.
+    const int32_t* sp_row = nullptr;
+    int32_t sp_prev1 = -1, sp_pref = -1;
+    if (resident && split && threadIdx.x < na) sp_row = split + int64_t(e_k[threadIdx.x]) * (nblocks + 1);
     __syncthreads();
     for (;;) {
       // plan a batch of windows: runs of consecutive blocks holding <= merge_cap entries of C
@@ -321,11 +350,18 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
         const int32_t span = static_cast<int32_t>(w1 - w0);
         const int32_t expect = w_cnt[wi];
         const int nwords = (span + 31) >> 5;
+        int32_t ps0 = -1, ps1 = -1;
+        if (sp_row) {
+          ps0 = sp_prev1 >= 0 ? sp_prev1 : sp_row[b0];
+          ps1 = sp_pref >= 0 ? sp_pref : sp_row[b1];
+          sp_prev1 = ps1;
+          sp_pref = wi + 1 < nwin ? sp_row[w_b1[wi + 1]] : -1;
+        }
 
         // pass 1: mark the window's columns (a row with a stored bitmap copies it in the rank
         // prefix below instead)
         for (int64_t base = 0; base < (stored ? 0 : na); base += kNumThreads) {
-          build_chunk(a0, na, base, resident, b0, b1, w0, w1);
+          build_chunk(a0, na, base, resident, b0, b1, w0, w1, ps0, ps1);
           const int nent = s_ctl[6];
           const int32_t total = s_ctl[7];
           int32_t per = (total + kWarps - 1) / kWarps;
@@ -341,13 +377,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) j[u] = j0 + 32 * u;
               } else {
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                  const int32_t g0 = p0 + 32 * u;
-                  j[u] = -1;
-                  int unused;
-                  if (g0 < hi) walk.step(g0, hi, j[u], unused);
-                }
+                int unused[kUnroll];
+                walk.step_many<kUnroll>(p0, hi, j, unused);
               }
               int32_t c[kUnroll];
 #pragma unroll
@@ -363,10 +394,6 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
           }
           __syncthreads();
         }
-        // a resident row with a stored bitmap skips pass 1: its pass 2 chunk's split offsets are
-        // loaded now, beside the bitmap
-        int32_t ps0 = -1, ps1 = -1;
-        if (stored) split_of(na, resident, b0, b1, ps0, ps1);
         // rank prefix over the window's words: each thread owns kWordsPerThread consecutive
         // words of one group. A stored bitmap is read here straight into the thread's registers
         // and copied to shared memory; its window's whole blocks are stored (zero past the row's
@@ -413,6 +440,14 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
         __syncthreads();
         const int32_t cnt = s_ctl[5];
         if (threadIdx.x == 0 && cnt != expect) set_error(err, kErrCount);
+        constexpr int kLineThreads = kWordsPerThread >= 32 ? 1 : 32 / kWordsPerThread;   // threads per 128 B
+        if (stored && wi + 1 < nwin && (threadIdx.x & (kLineThreads - 1)) == 0) {
+          // the next window's stored words (one request per 128-byte line) into L2
+          const int64_t nb0 = w_b0[wi + 1], nb1 = w_b1[wi + 1];
+          const int wlo = threadIdx.x * kWordsPerThread;
+          if (wlo < (nb1 - nb0) * kBlockWords)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(wbits + toff + nb0 * kBlockWords + wlo));
+        }
         // pass 2: accumulate a_ik * b_kj by rank
         for (int64_t base = 0; base < na; base += kNumThreads) {
           if (na > kNumThreads || stored) build_chunk(a0, na, base, resident, b0, b1, w0, w1, ps0, ps1);
@@ -437,20 +472,16 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
                   av[u] = walk.oval;
                 }
               } else {
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                  const int32_t g0 = p0 + 32 * u;
-                  j[u] = -1;
-                  av[u] = 0.0;
-                  if (g0 < hi) walk.step(g0, hi, j[u], av[u]);
-                }
+                walk.step_many<kUnroll>(p0, hi, j, av);
               }
               int32_t c[kUnroll];
               double bv[kUnroll];
 #pragma unroll
               for (int u = 0; u < kUnroll; ++u) {
                 c[u] = j[u] >= 0 ? B.col[j[u]] : -1;
-                bv[u] = j[u] >= 0 ? (Mode == kModeF64 ? bv64[j[u]] : static_cast<double>(bv32[j[u]])) : 0.0;
+                bv[u] = j[u] >= 0 ? ((Mode == kModeF64 || Mode == kModeF64X) ? bv64[j[u]]
+                                                                             : static_cast<double>(bv32[j[u]]))
+                                  : 0.0;
               }
 #pragma unroll
               for (int u = 0; u < kUnroll; ++u) {
@@ -480,6 +511,14 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
                   atomicAdd(&f_c[r], q + pl);
                   atomicAdd(&f_m[r], fabsf(ph));
                   atomicAdd(&f_t[r], 1);
+                } else if constexpr (Mode == kModeF64X) {
+                  uint32_t c0, c1, c2;
+                  int32_t ct;
+                  if (!fx_split(av[u] * bv[u], fx_sh0, c0, c1, c2, ct)) row_bad = true;
+                  atomicAdd(&x_l0[r], c0);
+                  atomicAdd(&x_l1[r], c1);
+                  atomicAdd(&x_l2[r], c2);
+                  atomicAdd(&x_lt[r], ct);
                 } else {
                   atomicAdd(&vals[r], av[u] * bv[u]);
                 }
@@ -487,6 +526,22 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
             }
           }
           __syncthreads();
+          if constexpr (Mode == kModeF64X) {
+            // a row with more than one chunk of A entries: carry the low limbs before the next chunk
+            if (na > kNumThreads && base + kNumThreads < na) {
+              const int nr = cnt < kRankCap ? cnt : kRankCap;
+              for (int r = threadIdx.x; r < nr; r += kNumThreads) {
+                uint32_t l0 = x_l0[r], l1 = x_l1[r], l2 = x_l2[r];
+                int32_t lt = x_lt[r];
+                fx_normalise(l0, l1, l2, lt);
+                x_l0[r] = l0;
+                x_l1[r] = l1;
+                x_l2[r] = l2;
+                x_lt[r] = lt;
+              }
+              __syncthreads();
+            }
+          }
         }
         // write-out: values by rank (coalesced); then the columns, staged by rank in the value
         // array's memory (words interleaved across threads for balance), copied out coalesced
@@ -500,6 +555,12 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
             f_s[r] = 0.f; f_c[r] = 0.f; f_m[r] = 0.f; f_t[r] = 0;
           }
           if (missed) row_flag[i] = 1;
+        } else if constexpr (Mode == kModeF64X) {
+          for (int r = threadIdx.x; r < ncnt; r += kNumThreads) {
+            const double res = fx_to_double(x_l0[r], x_l1[r], x_l2[r], x_lt[r], fx_lsb, &row_bad);
+            if (out + r < out_end) static_cast<double*>(cval_)[out + r] = res;
+            x_l0[r] = 0u; x_l1[r] = 0u; x_l2[r] = 0u; x_lt[r] = 0;
+          }
         } else {
           for (int r = threadIdx.x; r < ncnt; r += kNumThreads) {
             if (out + r < out_end) {
@@ -535,6 +596,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
       }
     }
     if (threadIdx.x == 0 && out != out_end) set_error(err, kErrCount);
+    if (Mode == kModeF64X && row_bad) row_flag[i] = 1;
   }
 }
 
@@ -724,7 +786,8 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
                       int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag,
                       const int32_t* abase, const int32_t* awidth, int64_t width, const uint32_t* wbits,
-                      const int64_t* woff, int num_sms, uint32_t* err, cudaStream_t s) {
+                      const int64_t* woff, const uint16_t* bexp, const int32_t* dev_count, int num_sms,
+                      uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   auto go = [&](auto kernel, int smem, int per_sm) {
@@ -733,11 +796,34 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
     kernel<<<static_cast<unsigned>(g), kNumThreads, smem, s>>>(A, B, perm, count, counter, c_off, win_slot,
                                                                blockcnt, nblocks, nslots, split, merge_cap,
                                                                ccol, cval, row_flag, abase, awidth, width, wbits,
-                                                               woff, err);
+                                                               woff, bexp, dev_count, err);
   };
   if (mode == kModeF32C) go(k_num_window<kModeF32C>, WinGeom<kModeF32C>::kSmemBytes, 2);
   else if (mode == kModeF32R) go(k_num_window<kModeF32R>, WinGeom<kModeF32R>::kSmemBytes, 2);
+  else if (mode == kModeF64X) go(k_num_window<kModeF64X>, WinGeom<kModeF64X>::kSmemBytes, 2);
   else go(k_num_window<kModeF64>, WinGeom<kModeF64>::kSmemBytes, 2);
+  return 1;
+}
+
+// Largest biased exponent of the values of every row of B (0 for an empty row): a warp per row.
+__global__ void __launch_bounds__(256) k_brow_exponent(DevCsr B, uint16_t* __restrict__ bexp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const double* bv = static_cast<const double*>(B.val);
+  for (int64_t k = gw; k < B.rows; k += nw) {
+    int e = 0;
+    for (int64_t q = B.rp[k] + lane; q < B.rp[k + 1]; q += 32) e = max(e, fx_exponent(bv[q]));
+    e = __reduce_max_sync(0xffffffffu, e);
+    if (lane == 0) bexp[k] = static_cast<uint16_t>(e);
+  }
+}
+
+int launch_brow_exponent(const DevCsr& B, uint16_t* bexp, int num_sms, cudaStream_t s) {
+  if (B.rows <= 0) return 0;
+  int64_t g = (B.rows * 32 + 255) / 256;
+  if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
+  k_brow_exponent<<<static_cast<unsigned>(g), 256, 0, s>>>(B, bexp);
   return 1;
 }
 

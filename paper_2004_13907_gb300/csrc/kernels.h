@@ -109,7 +109,10 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
                       int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag,
                       const int32_t* abase, const int32_t* awidth, int64_t width, const uint32_t* wbits,
-                      const int64_t* woff, int num_sms, uint32_t* err, cudaStream_t s);
+                      const int64_t* woff, const uint16_t* bexp, const int32_t* dev_count, int num_sms,
+                      uint32_t* err, cudaStream_t s);
+// Largest biased exponent of the values of every row of B (FP64), for the exact accumulation mode
+int launch_brow_exponent(const DevCsr& B, uint16_t* bexp, int num_sms, cudaStream_t s);
 // F32-compensated rerun lists: the rows of perm[0, count) whose flag is set (all rows when
 // `all`), appended to list at list_count (a device counter)
 int launch_collect_flagged(const int32_t* perm, int64_t count, const int32_t* row_flag, int all,

@@ -108,7 +108,8 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   p->cp.tiny_max = clampi(o.tiny_max, 0, 32);
   p->cp.warp_max = clampi(o.warp_max, 0, 1024);
   p->cp.block_max = clampi(o.block_max, p->cp.warp_max > 32 ? p->cp.warp_max : 32, 4096);
-  p->cp.force_window = o.force_window ? 1 : 0;
+  // deterministic FP64 (fp64_accumulate 2): every non-empty row takes the exact windowed path
+  p->cp.force_window = (o.force_window || (p->prec == SPGEMM_F64 && o.fp64_accumulate == 2)) ? 1 : 0;
   p->cp.window_all = p->prec == SPGEMM_F32_COMPENSATED ? 1 : 0;
   if (o.window_hash_fill < 1 || o.window_hash_fill > 4096) p->opts.window_hash_fill = 4096;
 
@@ -259,6 +260,10 @@ int64_t numeric_extra_bytes(const spgemm_plan_s* p) {
     extra += 2 * ws_rounded(4 * m);
     if (nwin > 0) extra += ws_rounded(8 * rerun_group_rows(p->width, kRerunScratchBytes) * p->width);
   }
+  if (p->prec == SPGEMM_F64 && p->opts.fp64_accumulate != 0 && nwin > 0) {
+    if (!p->rerun_flag) extra += 2 * ws_rounded(4 * m);   // flags and list of FP64 reruns
+    if (!p->bexp) extra += ws_rounded(2 * p->B.rows);     // exponent bound per row of B
+  }
   if (nwin > 0 && !p->split_tried) {
     const int64_t bytes = split_table_bytes(p->B.rows, p->nblocks);
     if (bytes <= (int64_t(p->opts.window_split_max_mb) << 20)) extra += ws_rounded(bytes);
@@ -271,6 +276,8 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
   const int64_t m = p->A.rows;
   const bool f32c = p->prec == SPGEMM_F32_COMPENSATED;
   const int mode = f32c ? kModeF32C : kModeF64;
+  // FP64 windowed rows: exact fixed-point accumulation when the caller asks for it
+  const bool fx = !f32c && p->opts.fp64_accumulate != 0;
   stage_begin(p, SPGEMM_STAGE_NUM_ROWPTR, s);
   int nl = launch_write_rowptr(p->c_off, m + 1, C->row_ptr, C->idx64_rowptr, s);
   stage_end(p, SPGEMM_STAGE_NUM_ROWPTR, nl, s);
@@ -296,8 +303,19 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       }
       cudaMemsetAsync(p->rerun_flag, 0, sizeof(int32_t) * m, s);
     }
+    if (fx && nwin > 0) {
+      if (!p->rerun_flag) {
+        p->rerun_flag = ws_get<int32_t>(p, m, &st);
+        p->rerun_list = ws_get<int32_t>(p, m, &st);
+      }
+      if (!p->bexp) p->bexp = ws_get<uint16_t>(p, p->B.rows, &st);
+      if (st) return st;
+      cudaMemsetAsync(p->rerun_flag, 0, sizeof(int32_t) * m, s);
+      cudaMemsetAsync(p->counters + 6, 0, sizeof(int32_t), s);
+    }
     stage_begin(p, SPGEMM_STAGE_NUM_WINDOW, s);
     nl = 0;
+    if (fx && nwin > 0) nl += launch_brow_exponent(p->B, p->bexp, p->num_sms, s);
     if (nwin > 0 && !p->split_tried) {
       // split table of B, once per plan, when it fits the budget (else the kernel searches)
       p->split_tried = true;
@@ -307,9 +325,20 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
         if (p->split) nl += launch_bsplit(p->B, p->nblocks, p->bbase, p->split, s);
       }
     }
-    nl += launch_num_window(mode, p->A, p->B, seg(kNumWin0), nwin, p->counters + 1, p->c_off, p->win_slot,
-                            p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
-                            p->rerun_flag, p->abase, p->awidth, p->width, p->wbits, p->woff, p->num_sms, err, s);
+    nl += launch_num_window(fx ? kModeF64X : mode, p->A, p->B, seg(kNumWin0), nwin, p->counters + 1, p->c_off,
+                            p->win_slot, p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col,
+                            C->val, p->rerun_flag, p->abase, p->awidth, p->width, p->wbits, p->woff, p->bexp,
+                            nullptr, p->num_sms, err, s);
+    if (fx && nwin > 0) {
+      // rows outside the fixed-point range (a very wide spread of product magnitudes, subnormal or
+      // non-finite values) are redone with FP64 shared atomics; the list stays on the device
+      nl += launch_collect_flagged(seg(kNumWin0), nwin, p->rerun_flag, 0, p->rerun_list, p->counters + 6, s);
+      nl += launch_num_window(kModeF64, p->A, p->B, p->rerun_list, nwin, p->counters + 7, p->c_off, p->win_slot,
+                              p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
+                              nullptr, p->abase, p->awidth, p->width, p->wbits, p->woff, nullptr, p->counters + 6,
+                              p->num_sms, err, s);
+      p->fx_rerun_pending = true;
+    }
     stage_end(p, SPGEMM_STAGE_NUM_WINDOW, nl, s);
     stage_begin(p, SPGEMM_STAGE_NUM_EXPAND, s);
     nl = launch_expand_cols(seg(kNumWin0), nwin, p->win_slot, p->woff, p->wbits, p->blockcnt, p->nblocks, p->c_off,

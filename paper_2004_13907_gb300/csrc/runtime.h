@@ -71,6 +71,8 @@ struct spgemm_plan_s {
   bool split_tried = false;
   // FP32-compensated path
   int32_t* rerun_flag = nullptr;     // per row: 1 = recompute in FP64
+  uint16_t* bexp = nullptr;          // largest biased exponent per row of B (exact FP64 accumulation)
+  bool fx_rerun_pending = false;     // the last numeric pass listed FP64 reruns in counters[6]
   int32_t* rerun_list = nullptr;
   int64_t sym_off[spg::kMaxClasses + 1] = {};
   int64_t num_off[spg::kMaxClasses + 1] = {};

@@ -161,3 +161,23 @@ def test_autotuned_batch_matches_oracle():
     for j, (A, B) in enumerate(jobs):
         _check_job(A, B, batch.result(j))
     batch.destroy()
+
+
+def test_batch_deterministic_mode_equals_exactly_rounded_oracle():
+    """fp64_accumulate=2 in a batch: every job's values equal the oracle's correctly rounded sums
+    bit for bit (the stacked product routes every row through the exact windowed path)."""
+    import paper_2004_13907_gb300 as sp
+    jobs = _jobs(24, seed=4)
+    jobs.append((synth.rmat(10, 16, seed=9),) * 2)
+    dA = [sp.DeviceCSR.from_host(A, "cuda") for A, _ in jobs]
+    dB = [sp.DeviceCSR.from_host(B, "cuda") for _, B in jobs]
+    batch = sp.spgemm_batch(dA, dB, opts=sp.spgemm_opts_default(fp64_accumulate=2))
+    batch.check()
+    torch.cuda.synchronize()
+    for j, (A, B) in enumerate(jobs):
+        ref = oracle.spgemm(A, B, exact_sum=True)
+        C = batch.result(j)
+        assert np.array_equal(C.row_ptr.cpu().numpy().astype(np.int64), ref.row_ptr)
+        assert np.array_equal(C.col.cpu().numpy(), ref.col)
+        assert np.array_equal(C.val.cpu().numpy(), ref.val), f"job {j}"
+    batch.destroy()
