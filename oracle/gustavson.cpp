@@ -13,7 +13,11 @@
 //   the row is emitted sorted by column, one entry for EVERY column that received a
 //   partial product (structural: a sum that cancels to 0 is still emitted).
 // The "sort then merge equal columns" of Algorithm 1 is realised by an ordered map keyed by
-// column, which holds the partial products of one row already merged.
+// column, which holds the partial products of one row already merged, or (the default for the
+// stored-order sums) by a dense accumulator per thread: one slot per column of C, the columns a
+// row touched listed as they are first hit and sorted at the end (Gustavson's own sparse
+// accumulator). Both add each entry's products in the same stored order, so their values are
+// bit-identical; the tests compare them.
 //
 // Arithmetic: FP64, each product rounded once (the build passes -ffp-contract=off so no
 // multiply-add is fused), summed in stored order. A second variant (exact_sum) returns for each
@@ -27,11 +31,13 @@
 // mag = sum of |a_ik*b_kj| (the scale of the entry's rounding error) and the number of
 // terms that entry received. Inputs in FP32 are widened to FP64 by the caller; that is
 // exact, and so is every FP32*FP32 product in FP64.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <thread>
 #include <vector>
 
@@ -158,16 +164,59 @@ static void oracle_row(int64_t i, const int64_t* a_rp, const int32_t* a_col, con
   }
 }
 
+// Dense accumulator of one thread: slots for every column of C, reset after each row.
+struct DenseAcc {
+  std::vector<double> sum, mag;
+  std::vector<int32_t> terms;
+  std::vector<int32_t> touched;
+  explicit DenseAcc(int64_t n) : sum(n, 0.0), mag(n, 0.0), terms(n, 0) {}
+};
+
+static void oracle_row_dense(int64_t i, const int64_t* a_rp, const int32_t* a_col, const double* a_val,
+                             const int64_t* b_rp, const int32_t* b_col, const double* b_val, DenseAcc& d,
+                             RowOut& out) {
+  d.touched.clear();
+  for (int64_t p = a_rp[i]; p < a_rp[i + 1]; ++p) {
+    const int32_t k = a_col[p];
+    const double a = a_val ? a_val[p] : 1.0;
+    for (int64_t q = b_rp[k]; q < b_rp[k + 1]; ++q) {
+      const double prod = a * (b_val ? b_val[q] : 1.0);
+      const int32_t j = b_col[q];
+      if (d.terms[j] == 0) d.touched.push_back(j);
+      d.sum[j] = d.sum[j] + prod;
+      d.mag[j] = d.mag[j] + std::fabs(prod);
+      d.terms[j] += 1;
+    }
+  }
+  std::sort(d.touched.begin(), d.touched.end());
+  const size_t len = d.touched.size();
+  out.col.resize(len);
+  out.val.resize(len);
+  out.mag.resize(len);
+  out.terms.resize(len);
+  for (size_t t = 0; t < len; ++t) {
+    const int32_t j = d.touched[t];
+    out.col[t] = j;
+    out.val[t] = d.sum[j];
+    out.mag[t] = d.mag[j];
+    out.terms[t] = d.terms[j];
+    d.sum[j] = 0.0;
+    d.mag[j] = 0.0;
+    d.terms[j] = 0;
+  }
+}
+
 extern "C" {
 
 // Computes rows `rows[0..nrows)` of C = A*B (all m rows when rows == NULL).
 // a_val / b_val may be NULL (pattern only: every stored value taken as 1).
 // threads <= 0 uses std::thread::hardware_concurrency().
 // exact_sum != 0: every value is the correctly rounded sum of the entry's partial products.
+// method: 0 ordered map, 1 dense accumulator of n_cols slots per thread (stored-order sums only).
 OracleResult* oracle_spgemm_ex(int64_t m, const int64_t* a_rp, const int32_t* a_col,
                                const double* a_val, const int64_t* b_rp, const int32_t* b_col,
                                const double* b_val, const int64_t* rows, int64_t nrows,
-                               int threads, int exact_sum) {
+                               int threads, int exact_sum, int method, int64_t n_cols) {
   OracleResult* r = new OracleResult();
   const int64_t count = rows ? nrows : m;
   r->rows.resize(static_cast<size_t>(count));
@@ -177,7 +226,10 @@ OracleResult* oracle_spgemm_ex(int64_t m, const int64_t* a_rp, const int32_t* a_
   r->threads = nt;
   std::atomic<int64_t> next(0);
   const int64_t chunk = 64;
+  const bool dense = !exact_sum && method == 1 && n_cols > 0;
   auto work = [&]() {
+    std::unique_ptr<DenseAcc> d;
+    if (dense) d.reset(new DenseAcc(n_cols));
     for (;;) {
       const int64_t s = next.fetch_add(chunk);
       if (s >= count) break;
@@ -185,6 +237,7 @@ OracleResult* oracle_spgemm_ex(int64_t m, const int64_t* a_rp, const int32_t* a_
       for (int64_t t = s; t < e; ++t) {
         const int64_t i = rows ? rows[t] : t;
         if (exact_sum) oracle_row_exact(i, a_rp, a_col, a_val, b_rp, b_col, b_val, r->rows[t]);
+        else if (dense) oracle_row_dense(i, a_rp, a_col, a_val, b_rp, b_col, b_val, *d, r->rows[t]);
         else oracle_row(i, a_rp, a_col, a_val, b_rp, b_col, b_val, r->rows[t]);
       }
     }
@@ -206,7 +259,7 @@ OracleResult* oracle_spgemm(int64_t m, const int64_t* a_rp, const int32_t* a_col
                             const double* a_val, const int64_t* b_rp, const int32_t* b_col,
                             const double* b_val, const int64_t* rows, int64_t nrows,
                             int threads) {
-  return oracle_spgemm_ex(m, a_rp, a_col, a_val, b_rp, b_col, b_val, rows, nrows, threads, 0);
+  return oracle_spgemm_ex(m, a_rp, a_col, a_val, b_rp, b_col, b_val, rows, nrows, threads, 0, 0, 0);
 }
 
 int64_t oracle_nnz(const OracleResult* r) { return r->nnz; }

@@ -342,3 +342,32 @@ def test_exact_sum_equals_stored_order_on_integers():
     b = oracle.spgemm(A, A, exact_sum=True)
     assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col)
     assert np.array_equal(a.val, b.val) and np.array_equal(a.mag, b.mag) and np.array_equal(a.terms, b.terms)
+
+
+@pytest.mark.parametrize("case", ["uniform", "rmat", "rect", "signed_wide", "empty"])
+def test_dense_accumulator_equals_ordered_map(case):
+    """The dense-accumulator path adds every entry's products in the same stored order as the
+    ordered map: row pointers, columns, values, magnitudes and term counts are bit-identical."""
+    if case == "uniform":
+        A = B = synth.uniform_random(800, 800, 0.01, seed=31)
+    elif case == "rmat":
+        A = B = synth.rmat(11, 16, seed=32)
+    elif case == "rect":
+        A = synth.uniform_random(300, 700, 0.02, seed=33)
+        B = synth.uniform_random(700, 5000, 0.004, seed=34)
+    elif case == "signed_wide":
+        rng = np.random.default_rng(35)
+        A = synth.random_small(60, 80, 0.3, 36)
+        A = synth.CSR(A.rows, A.cols, A.row_ptr, A.col, A.val * 10.0 ** rng.uniform(-12, 12, A.nnz))
+        B = synth.random_small(80, 50, 0.3, 37)
+    else:
+        A = synth.random_small(0, 5, 0.5, 38)
+        B = synth.random_small(5, 9, 0.5, 39)
+    a = oracle.spgemm(A, B, method="map")
+    b = oracle.spgemm(A, B, method="dense")
+    for f in ("row_ptr", "col", "mag", "terms"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    assert np.array_equal(a.val.view(np.uint64), b.val.view(np.uint64))
+    rows = np.arange(0, A.rows, 3)
+    assert np.array_equal(oracle.spgemm(A, B, rows=rows, method="dense").val,
+                          oracle.spgemm(A, B, rows=rows, method="map").val)
