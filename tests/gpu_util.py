@@ -53,3 +53,32 @@ def assert_parity(A, B, rp, col, val, rows=None, tol=TOL_F64):
         err = np.abs(val[g] - ref.val[r])
         assert np.all(err <= tol * ref.mag[r]), f"row {i} values out of tolerance"
     return ref
+
+
+def compare_all_rows(A, B, C, check, panel_products=2e8):
+    """Every row of the device product C = A*B against the oracle, in row panels cut where a
+    panel's partial products reach ``panel_products`` (so no panel of C or of the oracle's
+    output is large on the host). ``check(ref, rp, col, val, r0, r1)`` asserts one panel: rp are
+    C's row offsets of rows [r0, r1) rebased to 0, col/val the panel's entries from the device.
+    The oracle computes the next panel while this one is copied and compared."""
+    import concurrent.futures as cf
+    P = oracle.products_per_row(A, B)
+    cs = np.cumsum(P)
+    cuts = [0]
+    while cuts[-1] < A.rows:
+        done = int(cs[cuts[-1] - 1]) if cuts[-1] > 0 else 0
+        nxt = int(np.searchsorted(cs, done + panel_products, side="right"))
+        cuts.append(min(max(nxt, cuts[-1] + 1), A.rows))
+    rp = C.row_ptr.cpu().numpy().astype(np.int64)
+    with cf.ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(oracle.spgemm, A, B, np.arange(cuts[0], cuts[1], dtype=np.int64))
+        for k in range(len(cuts) - 1):
+            r0, r1 = cuts[k], cuts[k + 1]
+            ref = fut.result()
+            if k + 2 < len(cuts):
+                fut = ex.submit(oracle.spgemm, A, B, np.arange(r1, cuts[k + 2], dtype=np.int64))
+            s, e = int(rp[r0]), int(rp[r1])
+            col = C.col[s:e].cpu().numpy()
+            val = C.val[s:e].cpu().numpy().astype(np.float64)
+            check(ref, rp[r0:r1 + 1] - s, col, val, r0, r1)
+    return len(cuts) - 1

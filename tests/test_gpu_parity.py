@@ -12,7 +12,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import assert_parity, gpu_or_skip, run_gpu
+from gpu_util import assert_parity, compare_all_rows, gpu_or_skip, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -260,55 +260,69 @@ def test_repeat_numeric_on_plan_and_changed_values():
 
 
 @pytest.mark.slow
-def test_rmat_2e20_sampled_rows():
-    """The R-MAT 2^20 / degree-16 config at full size, in the bench's launch
-    configuration; rows sampled across every work class compared with the oracle, plus
-    invariants over all rows (sorted columns, nnz(C) = sum of the symbolic counts)."""
+def test_rmat_2e20_every_row(capsys):
+    """The R-MAT 2^20 / degree-16 config at full size (9.7e9 entries of C), in the bench's launch
+    configuration: EVERY row against the oracle, streamed in row panels (structure bit-exact,
+    values within 1e-12 * sum|a*b|)."""
     A = synth.rmat(20, 16, seed=0)
     import paper_2004_13907_gb300 as sp
     dA = sp.DeviceCSR.from_host(A, "cuda")
-    plan = sp.spgemm_plan(dA, dA)
+    plan = sp.spgemm_plan(dA, dA, opts=sp.spgemm_opts_default())
     sp.spgemm_symbolic(plan)
     C = sp.alloc_output(plan)
     sp.spgemm_numeric(plan, C)
     sp.spgemm_plan_check(plan)
+    info = sp.spgemm_plan_get_info(plan)
     torch.cuda.synchronize()
-    P = oracle.products_per_row(A, A)
-    assert sp.spgemm_plan_get_info(plan)["products"] == int(P.sum())
-    rp = C.row_ptr.cpu().numpy().astype(np.int64)
-    # invariant over every row: strictly increasing columns (checked in slices of C.col)
-    step = 1 << 28
-    nnz = C.col.numel()
-    for s0 in range(0, nnz - 1, step):
-        s1 = min(nnz, s0 + step + 1)
-        d = C.col[s0 + 1:s1] > C.col[s0:s1 - 1]          # position q compares q and q+1
-        lo = np.searchsorted(rp, s0 + 1, side="left")
-        hi = np.searchsorted(rp, s1 - 1, side="right")
-        b = torch.from_numpy(rp[lo:hi] - 1 - s0).to(C.col.device)
-        b = b[(b >= 0) & (b < d.numel())]
-        d[b] = True                                      # a row boundary needs no order
-        assert bool(d.all())
-        del d
-    rng = np.random.default_rng(7)
-    order = np.argsort(P)
-    picks = list(order[-6:]) + list(rng.choice(A.rows, 40, replace=False))
-    for lo, hi in [(1, 32), (33, 1024), (1025, 4096), (4097, 1 << 17), (1 << 17, 1 << 30)]:
-        ids = np.nonzero((P >= lo) & (P <= hi))[0]
-        if len(ids):
-            picks += list(rng.choice(ids, min(8, len(ids)), replace=False))
-    rows = np.unique(np.array(picks, dtype=np.int64))
-    # fetch only the sampled rows from the device
-    col_rows, val_rows, rp_s = [], [], [0]
-    for i in rows:
-        s, e = int(rp[i]), int(rp[i + 1])
-        col_rows.append(C.col[s:e].cpu().numpy())
-        val_rows.append(C.val[s:e].cpu().numpy())
-        rp_s.append(rp_s[-1] + e - s)
-    ref = oracle.spgemm(A, A, rows=rows)
-    for t, i in enumerate(rows):
-        r = slice(ref.row_ptr[t], ref.row_ptr[t + 1])
-        assert np.array_equal(col_rows[t], ref.col[r]), f"row {i}"
-        assert np.all(np.abs(val_rows[t] - ref.val[r]) <= 1e-12 * ref.mag[r]), f"row {i} values"
+    assert info["products"] == int(oracle.products_per_row(A, A).sum())
+    worst = [0.0, 0]
+
+    def check(ref, rp, col, val, r0, r1):
+        assert np.array_equal(rp, ref.row_ptr), f"row offsets differ in rows [{r0}, {r1})"
+        assert np.array_equal(col, ref.col), f"columns differ in rows [{r0}, {r1})"
+        err = np.abs(val - ref.val)
+        bad = err > 1e-12 * ref.mag
+        assert not bad.any(), f"{int(bad.sum())} values out of tolerance in rows [{r0}, {r1})"
+        nz = ref.mag > 0
+        if nz.any():
+            worst[0] = max(worst[0], float((err[nz] / ref.mag[nz]).max()))
+        worst[1] += len(col)
+
+    panels = compare_all_rows(A, A, C, check)
+    assert worst[1] == info["nnz_c"]
+    with capsys.disabled():
+        print(f"\nR-MAT 2^20 FP64: all {A.rows} rows, {worst[1]} entries in {panels} panels match the oracle; "
+              f"max |c - c_ref| / sum|p| = {worst[0]:.3e}")
     sp.spgemm_plan_destroy(plan)
     del C
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("accumulate", [0, 1])
+def test_rmat_2e17_full_default_config(accumulate):
+    """R-MAT 2^17 / degree 16 in the default launch configuration: every windowed sub-class,
+    rows with more than 512 A entries among them, compared element by element (FP64 atomics and
+    the exact fixed-point mode)."""
+    import paper_2004_13907_gb300 as sp
+    A = synth.rmat(17, 16, seed=0)
+    dA = sp.DeviceCSR.from_host(A, "cuda")
+    plan = sp.spgemm_plan(dA, dA, opts=sp.spgemm_opts_default(fp64_accumulate=accumulate))
+    sp.spgemm_symbolic(plan)
+    C = sp.alloc_output(plan)
+    sp.spgemm_numeric(plan, C)
+    sp.spgemm_plan_check(plan)
+    info = sp.spgemm_plan_get_info(plan)
+    torch.cuda.synchronize()
+    cls = dict(zip(sp._native.NUM_CLASSES, info["num_class_rows"]))
+    assert all(cls[c] > 0 for c in ("win1", "win2", "win3", "block8192", "warp1024"))
+    assert int(np.diff(A.row_ptr).max()) > 512
+    seen = [0]
+
+    def check(ref, rp, col, val, r0, r1):
+        assert np.array_equal(rp, ref.row_ptr) and np.array_equal(col, ref.col), f"rows [{r0}, {r1})"
+        assert np.all(np.abs(val - ref.val) <= 1e-12 * ref.mag), f"values in rows [{r0}, {r1})"
+        seen[0] += len(col)
+
+    compare_all_rows(A, A, C, check)
+    assert seen[0] == info["nnz_c"]
+    sp.spgemm_plan_destroy(plan)
