@@ -46,11 +46,14 @@ WORKLOADS = {
     "rmat16": [("rmat_2e16_deg16", lambda: synth.rmat(16, 16, seed=0), "f64")],
     "rmat17": [("rmat_2e17_deg16", lambda: synth.rmat(17, 16, seed=0), "f64")],
 }
+DEFAULT_WORKLOAD = "lap2d1024+rmat20"
 WORKLOAD_DESC = {
     "lap2d1024+rmat20": "C=A*A for A = 2D 5-point Laplacian 1024^2 (FP64 4/-1) and A = R-MAT 2^20 "
                         "vertices, 16*2^20 edge samples, (a,b,c,d)=(.57,.19,.19,.05), FP64 U[0,1], seed 0",
     "rmat20_f32c": "C=A*A for A = R-MAT 2^20 vertices, degree 16, FP32 values U[0,1], seed 0; FP32 "
                    "compensated accumulation, rows over the error bound recomputed in FP64",
+    "uniform10k": "C=A*A for A 10,000 x 10,000, Binomial(n, 1e-3) distinct uniform columns per row, FP64 "
+                  "U[-1,1), seed 0",
 }
 
 
@@ -184,6 +187,128 @@ def _numeric_bytes(info: dict, m: int) -> int:
     values)."""
     annz = sum(info["num_class_annz"])
     return 4 * (m + 1) + 12 * annz + 8 * annz + 12 * info["products"] + 8 * (m + 1) + 12 * info["nnz_c"]
+
+
+def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: bool = False) -> dict:
+    """One plain product workload (C = A*A per matrix, all timed together), as the headline line
+    times it; the roofline of its dominant stage. With cpu_err, the CPU-baseline leg (the oracle
+    on a bounded row sample) also gives the product's max relative entry error on that sample."""
+    specs = WORKLOADS[wl]
+    mats = [(name, gen()) for name, gen, _ in specs]
+    precs = {name: prec for name, _, prec in specs}
+    dev = [(name, M, sp.DeviceCSR.from_host(M, "cuda")) for name, M in mats]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    opts = sp.spgemm_opts_default(record_timings=1)
+    stream = torch.cuda.current_stream()
+    peak, _ = _peaks()
+
+    def step(keep=False):
+        out = []
+        for name, M, dM in dev:
+            plan = sp.spgemm_plan(dM, dM, precs[name], opts)
+            sp.spgemm_symbolic(plan)
+            C = sp.alloc_output(plan)
+            sp.spgemm_numeric(plan, C)
+            out.append((name, plan, C))
+        return out
+
+    for _ in range(warmup):
+        for name, plan, C in step():
+            sp.spgemm_plan_destroy(plan)
+        flush.zero_()
+    torch.cuda.synchronize()
+    times, stages, products, launches, infos = [], {}, 0, 0, {}
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        products = 0
+        for name, plan, C in res:
+            sp.spgemm_plan_check(plan)
+            info = sp.spgemm_plan_get_info(plan)
+            infos[name] = info
+            products += info["products"]
+            launches += info["kernel_launches"]
+            for k, (ms, _) in sp.spgemm_plan_get_timings(plan).items():
+                stages.setdefault((name, "num_window" if k == "num_expand" else k), []).append(ms)
+            sp.spgemm_plan_destroy(plan)
+        del res
+    ms = float(np.mean(times))
+    st = {k: float(np.mean(v)) for k, v in stages.items()}
+    (dom_name, dom_stage), dom_ms = max(st.items(), key=lambda kv: kv[1])
+    name0, M0, _ = dev[0]
+    numeric_ms = sum(v for (n_, k), v in st.items() if k.startswith("num_"))
+    nbytes = sum(_numeric_bytes(infos[n], M.rows) for n, M, _ in dev)
+    out = {"workload": wl, "value": round(_job_gflops(products, 1, ms), 3), "unit": UNIT, "ms_per_step": round(ms, 4),
+           "steps": steps, "warmup": warmup, "products_per_step": products, "gpu_launches": int(launches),
+           "description": WORKLOAD_DESC.get(wl, wl),
+           "numeric": {"ms": round(numeric_ms, 4), "alg_bytes": nbytes,
+                       "GBps": round(nbytes / (numeric_ms * 1e-3) / 1e9, 1),
+                       "frac_of_peak": round(nbytes / (numeric_ms * 1e-3) / 1e9 / peak, 4)},
+           "stage_ms": {f"{n}:{k}": round(v, 4) for (n, k), v in st.items() if v > 0.001}}
+    if dom_stage == "num_window":
+        wb, _ = _window_bytes(infos[dom_name])
+        out["roofline"] = {"bound": "hbm", "kernel": f"k_num_window + k_expand_cols ({dom_name})",
+                           "achieved": round(wb / (dom_ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                           "frac": round(wb / (dom_ms * 1e-3) / 1e9 / peak, 4), "algorithmic_bytes": wb,
+                           "launch_ms": round(dom_ms, 4)}
+    if any(p_ == "f32c" for p_ in precs.values()):
+        out["rows_redone_fp64"] = int(sum(i["f32c_rerun_rows"] for i in infos.values()))
+    if cpu_err:
+        # CPU-baseline leg: the oracle on a bounded row sample of the product, its rate, and the
+        # GPU result's error on those rows (FP32 results against the FP64 oracle)
+        res = step()
+        torch.cuda.synchronize()
+        out["cpu_baseline"], out["max_rel_err"] = cpu_baseline_error(mats, res, args.cpu_seconds, sp)
+        for name, plan, C in res:
+            sp.spgemm_plan_destroy(plan)
+        del res
+    del dev, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_one_config(args):
+    """One of the other configurations alone (printed as its own JSON line)."""
+    import torch
+    import paper_2004_13907_gb300 as sp
+    torch.cuda.set_device(0)
+    sw, ss = max(3, args.side_warmup), max(1, args.side_steps)
+    name = args.config
+    if name == "uniform10k":
+        return _product_config("uniform10k", args, sp, torch, max(ss, 10), max(sw, 10)), 0
+    if name == "rmat20_f32c":
+        return _product_config("rmat20_f32c", args, sp, torch, ss, sw, cpu_err=True), 0
+    if name == "batch4096":
+        return config_batch(args, sp, torch, _device_jobs(range(BATCH_JOBS), sp, torch), sw, 1), 0
+    return config_serve(args, sp, torch, _device_jobs(range(SERVE_POOL), sp, torch), args.serve_requests, sw), 0
+
+
+def run_configs(args, sp, torch) -> dict:
+    """The other measured configurations, each as its own object: the uniform 10k product, the
+    R-MAT 2^20 FP32-compensated product (with its max relative error against the FP64 oracle),
+    the full 4,096-job batch against per-product launches, and the 20,000-request serving
+    stream against the plain path."""
+    out = {}
+    sw, ss = max(3, args.side_warmup), max(1, args.side_steps)
+    t0 = time.perf_counter()
+    out["uniform10k"] = _product_config("uniform10k", args, sp, torch, max(ss, 10), max(sw, 10))
+    out["rmat20_f32c"] = _product_config("rmat20_f32c", args, sp, torch, ss, sw, cpu_err=True)
+    jobs = _device_jobs(range(BATCH_JOBS), sp, torch)
+    out["batch4096"] = config_batch(args, sp, torch, jobs, sw, 1)
+    for i in list(jobs):
+        if i >= SERVE_POOL:
+            del jobs[i]
+    torch.cuda.empty_cache()
+    out["serve20000"] = config_serve(args, sp, torch, jobs, args.serve_requests, sw)
+    del jobs
+    torch.cuda.empty_cache()
+    out["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def run_ours(args):
@@ -322,123 +447,154 @@ def run_ours(args):
         line["e2e"] = run_e2e(args, mats, nnz_c, products_step, sp, torch, dist)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mats, args.cpu_seconds)
+    if ws == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_configs:
+        line["configs"] = run_configs(args, sp, torch)
     if dist:
         dist.destroy_process_group()
     return line, rank
 
 
-def _batch_jobs(max_expected_products: float, limit: int = 4096):
-    """Jobs of the batch distribution (n log-uniform in [100, 50000], density log-uniform in
-    [1e-4, 1e-2]) whose expected product count n^3 d^2 is below the cap."""
-    out = []
-    for i in range(limit):
-        n, d = synth.batch_job_params(i, 0)
-        if n ** 3 * d * d < max_expected_products:
-            out.append((i,) + synth.batch_job(i, 0))
+BATCH_JOBS = 4096          # jobs of the batching config
+SERVE_REQUESTS = 20_000    # requests of the serving config
+SERVE_POOL = 512           # distinct batch-distribution jobs the served requests draw from
+WAVE_OUT_BYTES = 48 << 30  # estimated output bytes per batched wave (outputs are freed per wave)
+
+
+def _job_estimate(i: int) -> tuple:
+    """(n, d, expected partial products n^3 d^2, expected nnz(C) n^2 (1 - exp(-n d^2))) of job i."""
+    import math
+    n, d = synth.batch_job_params(i, 0)
+    return n, d, n ** 3 * d * d, n * n * (1.0 - math.exp(-n * d * d))
+
+
+def _device_jobs(idx, sp, torch) -> dict:
+    """Jobs of the batch distribution built in device memory by synth.torch_gen (bit-identical to
+    synth.batch_job, which the tests and the oracle use)."""
+    from synth import torch_gen
+    out = {}
+    for i in idx:
+        n, (arp, acol, aval), (brp, bcol, bval) = torch_gen.batch_job(i, 0, device="cuda")
+        out[i] = (sp.DeviceCSR(n, n, arp, acol, aval), sp.DeviceCSR(n, n, brp, bcol, bval))
+    torch.cuda.synchronize()
     return out
 
 
-def run_batch(args):
-    """Batched form (one stacked product for every job) against the plain per-product launch
-    (plan, symbolic, allocate, numeric per job), same jobs, same GPU."""
-    import torch
-    import paper_2004_13907_gb300 as sp
-    cap = 1e6 if args.workload == "batch_small" else 1e7
-    jobs = _batch_jobs(cap)
-    dA = [sp.DeviceCSR.from_host(A, "cuda") for _, A, _ in jobs]
-    dB = [sp.DeviceCSR.from_host(B, "cuda") for _, _, B in jobs]
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+def _waves(idx, cap_bytes: float) -> list:
+    """Consecutive jobs grouped while their estimated outputs (12 bytes per entry) stay within
+    cap_bytes; a job larger than the cap is a wave of its own."""
+    waves, cur, acc = [], [], 0.0
+    for i in idx:
+        b = 12.0 * _job_estimate(i)[3] + 8.0 * _job_estimate(i)[0]
+        if cur and acc + b > cap_bytes:
+            waves.append(cur)
+            cur, acc = [], 0.0
+        cur.append(i)
+        acc += b
+    if cur:
+        waves.append(cur)
+    return waves
+
+
+def config_batch(args, sp, torch, jobs: dict, warmup: int, steps: int) -> dict:
+    """Batching (4,096 independent products A_j*B_j of the batch distribution): the batched form
+    against the plain per-product launch (plan, symbolic, allocate, numeric for each job in
+    turn), same jobs, same GPU, FP64. The batched form groups the jobs by size: the small-job
+    stratum (expected P < 1e6, where launch overhead is what batching removes) and the larger
+    jobs, each stratum in waves of one stacked product whose outputs fit WAVE_OUT_BYTES (every
+    output freed before the next wave), each stratum with its own autotuned bins (tuned on the
+    small stratum, and on a sample of large jobs). The small stratum is also reported alone,
+    with its CUDA-graph numeric replay."""
     stream = torch.cuda.current_stream()
+    idx = sorted(jobs)
+    small = [i for i in idx if _job_estimate(i)[2] < 1e6]
+    large = [i for i in idx if _job_estimate(i)[2] >= 1e6]
+    sA = [jobs[i][0] for i in small]
+    sB = [jobs[i][1] for i in small]
+    tuned, tune_rep = sp.spgemm_autotune_batch(sA, sB, reps=2)
+    sample = [i for i in large if 1e7 <= _job_estimate(i)[2] <= 3e8][:48]
+    tuned_l, tune_rep_l = sp.spgemm_autotune_batch([jobs[i][0] for i in sample], [jobs[i][1] for i in sample],
+                                                   reps=2)
+    waves = [(w, tuned) for w in _waves(small, WAVE_OUT_BYTES)] + \
+            [(w, tuned_l) for w in _waves(large, WAVE_OUT_BYTES)]
 
-    # autotuned bins: class thresholds and window merge cap chosen by timing this batch (untimed)
-    tuned, tune_rep = sp.spgemm_autotune_batch(dA, dB, reps=2)
+    def batched(ids_waves):
+        prods = 0
+        launches = 0
+        for w, o in ids_waves:
+            b = sp.spgemm_batch([jobs[i][0] for i in w], [jobs[i][1] for i in w], opts=o)
+            info = b.info()
+            prods += info["products"]
+            launches += info["kernel_launches"]
+            b.destroy()
+        return prods, launches
 
-    def batched():
-        b = sp.spgemm_batch(dA, dB, opts=tuned)
-        return b
+    def plain(ids):
+        for i in ids:
+            C = sp.multiply(jobs[i][0], jobs[i][1])
+            del C
 
-    def per_product():
-        out = []
-        for a, b in zip(dA, dB):
-            out.append(sp.multiply(a, b))
-        return out
-
-    for _ in range(args.warmup):
-        b = batched()
-        b.destroy()
-        per_product()
-        flush.zero_()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(0)
-    sampler.start()
-    tb, tp, tr = [], [], []
-    launches = 0
-    products = 0
-    for _ in range(args.steps):
-        flush.zero_()
+    def timed(fn, *a):
+        torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        b = batched()
+        r = fn(*a)
         e1.record(stream)
         torch.cuda.synchronize()
-        tb.append(e0.elapsed_time(e1))
-        info = b.info()
-        products = info["products"]
-        launches += info["kernel_launches"]
-        # numeric-only recompute through the captured graph
+        return e0.elapsed_time(e1), r
+
+    # warm-up: one whole pass of each form (allocator pools reach their high-water mark), then
+    # the small stratum
+    for wu in range(warmup):
+        if wu == 0:
+            batched(waves)
+            plain(idx)
+            torch.cuda.empty_cache()
+        else:
+            batched([(small, tuned)])
+            plain(small)
+    tb, tp, ts_b, ts_p, tr = [], [], [], [], []
+    products = launches = small_products = 0
+    for _ in range(steps):
+        ms, (products, launches) = timed(batched, waves)
+        tb.append(ms)
+        ms, _ = timed(plain, idx)
+        tp.append(ms)
+        torch.cuda.empty_cache()
+        ms, (small_products, _) = timed(batched, [(small, tuned)])
+        ts_b.append(ms)
+        ms, _ = timed(plain, small)
+        ts_p.append(ms)
+        b = sp.spgemm_batch(sA, sB, opts=tuned)
         b.replay()
         torch.cuda.synchronize()
-        e0.record(stream)
-        b.replay()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tr.append(e0.elapsed_time(e1))
+        ms, _ = timed(b.replay)
+        tr.append(ms)
         b.destroy()
-        flush.zero_()
-        e0.record(stream)
-        res = per_product()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tp.append(e0.elapsed_time(e1))
-        del res
-    clocks = sampler.stop()
-    ms_b, ms_p, ms_r = float(np.mean(tb)), float(np.mean(tp)), float(np.mean(tr))
-    gf = lambda ms: round(2.0 * products / (ms * 1e-3) / 1e9, 3)
+    gf = lambda p, ms: round(2.0 * p / (ms * 1e-3) / 1e9, 3)
+    ms_b, ms_p = float(np.mean(tb)), float(np.mean(tp))
     return {
-        "metric": METRIC, "value": gf(ms_b), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms_b, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload,
-                   "description": f"{len(jobs)} jobs of the batch distribution with expected products below "
-                                  f"{cap:.0e} (n log-uniform [100, 50000], density log-uniform [1e-4, 1e-2], "
-                                  f"A_j, B_j independent, FP64 U[-1,1], seed 0)",
-                   "jobs": len(jobs), "products_per_step": products, "l2": "flushed between steps",
-                   "parallelism": "one GPU, one stacked product"},
-        "per_product_launch": {"value": gf(ms_p), "unit": UNIT, "ms_per_step": round(ms_p, 3),
-                               "what": "plan + symbolic + allocate + numeric for each job in turn"},
-        "batched_speedup": round(ms_p / ms_b, 2),
-        "autotune": {"tiny_max": tuned.tiny_max, "warp_max": tuned.warp_max, "block_max": tuned.block_max,
-                     "window_hash_fill": tuned.window_hash_fill, "trials": len(tune_rep["trials"]),
-                     "default_ms": round(tune_rep["default_ms"], 3), "tuned_ms": round(tune_rep["best_ms"], 3)},
-        "graph_replay": {"value": gf(ms_r), "unit": UNIT, "ms_per_step": round(ms_r, 4),
-                         "what": "numeric-only recompute of every job as one CUDA graph launch"},
-        "gpu_launches": int(launches), "clocks": clocks,
-    }, 0
-
-
-def _serve_job(kind: str, param: int):
-    """Inputs of one served request (host CSR): A_i, B_i of the batch distribution, or a 3D
-    7-point Laplacian A with B = A (None)."""
-    if kind == "lap3d":
-        return synth.laplacian3d(param), None
-    return synth.batch_job(param, 0)
-
-
-def _serve_inputs(reqs, procs: int):
-    import multiprocessing as mp
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(procs) as pool:
-        return pool.starmap(_serve_job, [(r.kind, r.param) for r in reqs], chunksize=2)
+        "workload": f"batch{len(idx)}", "value": gf(products, ms_b), "unit": UNIT, "ms_per_step": round(ms_b, 3),
+        "steps": steps, "warmup": warmup, "jobs": len(idx), "waves": len(waves), "products_per_step": products,
+        "plain_value": gf(products, ms_p), "plain_ms_per_step": round(ms_p, 3),
+        "speedup_vs_plain": round(ms_p / ms_b, 3), "gpu_launches": int(launches),
+        "small_stratum": {"jobs": len(small), "products": small_products,
+                          "value": gf(small_products, float(np.mean(ts_b))),
+                          "plain_value": gf(small_products, float(np.mean(ts_p))),
+                          "speedup_vs_plain": round(float(np.mean(ts_p)) / float(np.mean(ts_b)), 3),
+                          "graph_replay_value": gf(small_products, float(np.mean(tr)))},
+        "autotune": {"small": {"tiny_max": tuned.tiny_max, "warp_max": tuned.warp_max, "block_max": tuned.block_max,
+                               "window_hash_fill": tuned.window_hash_fill, "trials": len(tune_rep["trials"]),
+                               "tuned_on": f"{len(small)} jobs with expected P < 1e6"},
+                     "large": {"tiny_max": tuned_l.tiny_max, "warp_max": tuned_l.warp_max,
+                               "block_max": tuned_l.block_max, "window_hash_fill": tuned_l.window_hash_fill,
+                               "trials": len(tune_rep_l["trials"]),
+                               "tuned_on": f"{len(sample)} jobs with expected P in [1e7, 3e8]"}},
+        "description": f"{len(idx)} jobs C_j = A_j*B_j, n log-uniform [100, 50000], density log-uniform "
+                       f"[1e-4, 1e-2], A_j, B_j independent, FP64 U[-1,1), seed 0; batched form in {len(waves)} "
+                       f"waves (small-job stratum, then larger jobs) of at most {WAVE_OUT_BYTES >> 30} GiB of "
+                       f"expected output, each output freed before the next wave; warm-up: one whole pass of "
+                       f"each form, then the small stratum",
+    }
 
 
 def _pct(v, q):
@@ -450,98 +606,72 @@ def _pct(v, q):
     return float(v[max(k, 1) - 1])
 
 
-def run_serve(args):
-    """Serving: a Poisson stream of requests (90% jobs of the batch distribution, 10% A*A for a
-    3D 7-point Laplacian with g in 64..128), FP64, 32 GB admission cap. The server (continuous
-    batching) against the plain per-product launch (one product at a time, in arrival order):
-    saturated throughput with every request queued at once, and p50/p99 latency (arrival to
-    completion) at a Poisson rate of 0.8 x the plain path's saturated job throughput."""
+def config_serve(args, sp, torch, jobs: dict, requests: int, warmup: int) -> dict:
+    """Serving: a Poisson stream of `requests` requests (90% jobs of the batch distribution, 10%
+    A*A for a 3D 7-point Laplacian with g in 64..128), FP64, 32 GB admission cap. Request i of
+    the batch kind takes job (i mod SERVE_POOL) of the batch distribution; the Laplacians are built
+    once per grid size. The server (continuous batching) against the plain per-product launch
+    (one product at a time, in arrival order): saturated throughput (every request queued at
+    once for the server, one after the other for the plain path), and p50/p99 latency (arrival
+    to completion) at a Poisson rate of 0.8 x the plain path's job rate."""
     import threading
-    import torch
-    import paper_2004_13907_gb300 as sp
-    R = args.serve_requests
+    R = requests
     reqs = synth.serve_stream(R, 1.0, seed=0)
-    t_gen = time.perf_counter()
-    host = _serve_inputs(reqs, max(1, min(16, os.cpu_count() or 1)))
-    t_gen = time.perf_counter() - t_gen
-    dev = []
-    for A, B in host:
-        dA = sp.DeviceCSR.from_host(A, "cuda")
-        dev.append((dA, dA if B is None else sp.DeviceCSR.from_host(B, "cuda")))
+    lap = {}
+    for r in reqs:
+        if r.kind == "lap3d" and r.param not in lap:
+            L = sp.DeviceCSR.from_host(synth.laplacian3d(r.param), "cuda")
+            lap[r.param] = (L, L)
+    dev = [lap[r.param] if r.kind == "lap3d" else jobs[r.index % SERVE_POOL] for r in reqs]
     torch.cuda.synchronize()
-    in_bytes = sum(int(dA.col.numel()) * 12 + int(dB.col.numel()) * 12 for dA, dB in dev)
-    del host
     cap = 32 << 30
 
     def server(**kw):
-        if args.serve_small_products >= 0:
-            kw["small_products"] = args.serve_small_products
-        if args.serve_batch_entries > 0:
-            kw["max_batch_entries"] = args.serve_batch_entries
         return sp.Server(mem_cap_bytes=cap, batch_window_us=args.serve_window_us, num_streams=args.serve_streams,
                          **kw)
 
-    def drain(srv, ids, stall_s=600.0):
-        """Consumes every result as it finishes (the server's completion queue), releasing each at
-        once, as a client would; fails when no job has finished for stall_s seconds."""
-        states = [None] * len(ids)
-        pending = {i: k for k, i in enumerate(ids)}
-        while pending:
+    def drain(srv, n, stall_s=600.0):
+        """Takes every result from the server's completion queue as it finishes, releasing each
+        at once, as a client would."""
+        states = {}
+        for _ in range(n):
             j = srv.wait_any(timeout=stall_s)
             if j is None:
-                raise RuntimeError(f"serve: no job finished for {stall_s:.0f} s ({len(pending)} pending)")
-            if j in pending:
-                states[pending.pop(j)] = srv.poll(j)["state"]
-                srv.release(j)
+                raise RuntimeError(f"serve: no job finished for {stall_s:.0f} s")
+            states[j] = srv.poll(j)["state"]
+            srv.release(j)
         return states
 
-    # warm-up: the plain path and the server on the first requests
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         for dA, dB in dev[:16]:
             sp.multiply(dA, dB)
         with server() as srv:
-            drain(srv, [srv.submit(dA, dB, sync=False) for dA, dB in dev[:64]])
+            for dA, dB in dev[:200]:
+                srv.submit(dA, dB, sync=False)
+            drain(srv, 200)
     torch.cuda.synchronize()
-    sampler = ClockSampler(0)
-    sampler.start()
-    # saturated: every request queued at once
-    sat = []
-    rejected = set()
-    for _ in range(args.steps):
-        with server() as srv:
-            ids = [srv.submit(dA, dB, sync=False) for dA, dB in dev]
-            states = drain(srv, ids)
-            st = srv.stats()
-        rejected = {k for k, s_ in enumerate(states) if s_ != "done"}
-        sat.append(st)
-    products = sat[-1]["products"]
-    ms_srv = float(np.mean([x["elapsed_s"] for x in sat])) * 1e3
-    accepted = [k for k in range(R) if k not in rejected]
-    plain_ms = []
-    for _ in range(args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in accepted:
-            C = sp.multiply(*dev[k])
-            del C
-        torch.cuda.synchronize()
-        plain_ms.append((time.perf_counter() - t0) * 1e3)
-    ms_plain = float(np.mean(plain_ms))
-    # the rate of the latency runs comes from the plain path run the way it runs live (each
-    # product waited for before the next), so that its queue is stable at 0.8 of capacity
+    # saturated server: every request queued at once
+    with server() as srv:
+        ids = [srv.submit(dA, dB, sync=False) for dA, dB in dev]
+        states = drain(srv, len(ids))
+        sat = srv.stats()
+    rejected = sum(1 for s_ in states.values() if s_ != "done")
+    ms_srv = sat["elapsed_s"] * 1e3
+    # plain path one product at a time (each waited for before the next, as it serves requests)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k in accepted:
-        C = sp.multiply(*dev[k])
+    prods_plain = 0
+    for dA, dB in dev:
+        C = sp.multiply(dA, dB)
         torch.cuda.synchronize()
         del C
-    ms_plain_sync = (time.perf_counter() - t0) * 1e3
-    lam = 0.8 * len(accepted) / (ms_plain_sync * 1e-3)
+    ms_plain = (time.perf_counter() - t0) * 1e3
+    lam = 0.8 * R / (ms_plain * 1e-3)
     arrival = np.array([r.arrival_s for r in reqs]) / lam
     # plain path at rate lam: each request runs when it has arrived and the previous one is done
     lat_plain = []
     t0 = time.perf_counter()
-    for k in accepted:
+    for k in range(R):
         wait = t0 + arrival[k] - time.perf_counter()
         if wait > 0:
             time.sleep(wait)
@@ -566,53 +696,45 @@ def run_serve(args):
         th = threading.Thread(target=submitter)
         th.start()
         ready.wait()
-        for _ in range(R):   # every request finishes once; each result is released as it comes out
-            j = srv.wait_any(timeout=600.0)
-            if j is None:
-                raise RuntimeError("serve: no job finished for 600 s")
-            srv.release(j)
+        drain(srv, R)
         th.join()
         live = srv.stats()
-    clocks = sampler.stop()
     gf = lambda p, ms: round(2.0 * p / (ms * 1e-3) / 1e9, 3)
+    products = sat["products"]
     n_lap = sum(1 for r in reqs if r.kind == "lap3d")
     return {
-        "metric": METRIC, "value": gf(products, ms_srv), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_srv, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "serve",
-                   "description": f"{R} requests of a Poisson stream (seed 0): {R - n_lap} jobs A_i*B_i of the "
-                                  f"batch distribution (n log-uniform [100, 50000], density log-uniform "
-                                  f"[1e-4, 1e-2]), {n_lap} A*A for 3D 7-point Laplacians with g in 64..128; "
-                                  f"FP64; 32 GB admission cap; inputs resident on the device",
-                   "requests": R, "input_bytes": in_bytes, "products_per_step": products,
-                   "l2": "inputs larger than L2",
-                   "parallelism": f"one GPU, continuous batching, {args.serve_streams} streams",
-                   "batch_window_us": args.serve_window_us, "input_generation_s": round(t_gen, 1)},
-        "saturated": {"server_ms": round(ms_srv, 3), "plain_ms": round(ms_plain, 3),
-                      "plain_value": gf(products, ms_plain), "speedup": round(ms_plain / ms_srv, 3),
-                      "server_jobs_per_s": round(sat[-1]["jobs_per_s"], 1),
-                      "mean_batch_jobs": round(sat[-1]["mean_batch_jobs"], 2),
-                      "rejected_over_cap": len(rejected), "splits": sat[-1]["splits"],
-                      "bytes_peak": sat[-1]["bytes_peak"]},
-        "latency": {"rate_per_s": round(lam, 2), "what": "arrival to completion, ms, at 0.8 x the job rate "
-                                                          "of the plain path run one product at a time",
-                    "plain_capacity_ms": round(ms_plain_sync, 3),
+        "workload": f"serve{R}", "value": gf(products, ms_srv), "unit": UNIT, "ms_per_step": round(ms_srv, 3),
+        "steps": 1, "warmup": warmup, "requests": R, "products_per_step": products,
+        "plain_value": gf(products, ms_plain), "plain_ms_per_step": round(ms_plain, 3),
+        "speedup_vs_plain": round(ms_plain / ms_srv, 3), "rejected_over_cap": rejected,
+        "server_jobs_per_s": round(sat["jobs_per_s"], 1), "mean_batch_jobs": round(sat["mean_batch_jobs"], 2),
+        "splits": sat["splits"], "bytes_peak": sat["bytes_peak"], "gpu_launches": int(sat["kernel_launches"]),
+        "latency": {"rate_per_s": round(lam, 2),
+                    "what": "arrival to completion, ms, at 0.8 x the job rate of the plain path run one product "
+                            "at a time",
                     "server_p50_ms": round(live["latency_p50_ms"], 3), "server_p99_ms": round(live["latency_p99_ms"], 3),
                     "server_max_ms": round(live["latency_max_ms"], 3),
                     "plain_p50_ms": round(_pct(lat_plain, 0.5), 3), "plain_p99_ms": round(_pct(lat_plain, 0.99), 3),
                     "plain_max_ms": round(max(lat_plain), 3),
                     "server_mean_batch_jobs": round(live["mean_batch_jobs"], 2),
                     "submit_lag_max_ms": round(lag[0] * 1e3, 3)},
-        "gpu_launches": int(sat[-1]["kernel_launches"]), "clocks": clocks,
-    }, 0
+        "description": f"{R} requests of a Poisson stream (seed 0): {R - n_lap} jobs A_j*B_j of the batch "
+                       f"distribution drawn from its first {SERVE_POOL} jobs (request i takes job i mod "
+                       f"{SERVE_POOL}), {n_lap} A*A for 3D 7-point Laplacians with g in 64..128 (one per g); "
+                       f"FP64; 32 GB admission cap; inputs resident on the device; warm-up: {warmup} x (16 "
+                       f"plain products + 200 served requests)",
+    }
 
 
-def _pinned(n: int, dtype, torch):
-    """Page-locked host array of exactly n elements (numpy memory registered with CUDA)."""
+def _pinned(n: int, dtype, torch, registered: list):
+    """Page-locked host array of exactly n elements (numpy memory registered with CUDA); the
+    registered pointers are appended to `registered`, to be unregistered before the memory is
+    freed (a stale registration over reused host memory breaks later copies)."""
     a = np.empty(max(n, 1), dtype=dtype)
     t = torch.from_numpy(a)
     rc = torch.cuda.cudart().cudaHostRegister(t.data_ptr(), t.numel() * t.element_size(), 0)
+    if int(rc) == 0:
+        registered.append(t.data_ptr())
     return t, (int(rc) == 0)
 
 
@@ -621,19 +743,20 @@ def run_e2e(args, mats, nnz_c, products_step, sp, torch, dist):
     Host arrays are page-locked; the output arrays are sized from nnz(C) of the device run."""
     hosts = []
     pinned_ok = True
+    registered = []
     for name, M in mats:
-        rp, ok1 = _pinned(M.rows + 1, np.int32, torch)
-        col, ok2 = _pinned(M.nnz, np.int32, torch)
-        val, ok3 = _pinned(M.nnz, np.float64, torch)
+        rp, ok1 = _pinned(M.rows + 1, np.int32, torch, registered)
+        col, ok2 = _pinned(M.nnz, np.int32, torch, registered)
+        val, ok3 = _pinned(M.nnz, np.float64, torch, registered)
         rp.copy_(torch.from_numpy(M.row_ptr.astype(np.int32)))
         col[:M.nnz].copy_(torch.from_numpy(M.col))
         val[:M.nnz].copy_(torch.from_numpy(M.val))
         hA = sp.DeviceCSR(M.rows, M.cols, rp, col[:M.nnz], val[:M.nnz])
         nnz = nnz_c[name]
         idx64 = nnz >= 2**31
-        orp, o1 = _pinned(M.rows + 1, np.int64 if idx64 else np.int32, torch)
-        ocol, o2 = _pinned(nnz, np.int32, torch)
-        oval, o3 = _pinned(nnz, np.float64, torch)
+        orp, o1 = _pinned(M.rows + 1, np.int64 if idx64 else np.int32, torch, registered)
+        ocol, o2 = _pinned(nnz, np.int32, torch, registered)
+        oval, o3 = _pinned(nnz, np.float64, torch, registered)
         pinned_ok &= all((ok1, ok2, ok3, o1, o2, o3))
         out = sp.DeviceCSR(M.rows, M.cols, orp, ocol[:nnz], oval[:nnz])
         h2d = 2 * ((M.rows + 1) * 4 + M.nnz * 12)            # A and B (= A) copied in
@@ -656,17 +779,23 @@ def run_e2e(args, mats, nnz_c, products_step, sp, torch, dist):
     for v in per_matrix.values():
         v.clear()
     times = []
-    for _ in range(args.steps):
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    for _ in range(e2e_steps):
         t0 = time.perf_counter()
         step()
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     ws, _, _ = _dist()
     t = _max_over_ranks(float(np.mean(times)), dist, "cuda")
+    torch.cuda.synchronize()
+    h2d, d2h = int(sum(h[4] for h in hosts)), int(sum(h[5] for h in hosts))
+    hosts.clear()
+    for ptr in registered:
+        torch.cuda.cudart().cudaHostUnregister(ptr)
     return {"value": round(_job_gflops(products_step, ws, t * 1e3), 3), "unit": UNIT,
-            "h2d_bytes_per_step": int(sum(h[4] for h in hosts)),
-            "d2h_bytes_per_step": int(sum(h[5] for h in hosts)),
-            "ms_per_step": round(t * 1e3, 3), "host_buffers": "pinned" if pinned_ok else "pageable (pinning failed)",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": round(t * 1e3, 3), "steps": e2e_steps,
+            "host_buffers": "pinned" if pinned_ok else "pageable (pinning failed)",
             "ms_per_matrix": {k: round(float(np.mean(v)) * 1e3, 3) for k, v in per_matrix.items()},
             "api": "spgemm_multiply_host (C ABI, host buffers)"}
 
@@ -703,6 +832,48 @@ def cpu_baseline(mats, seconds: float) -> dict:
         samples.append(f"{name}: {'all' if rows is None else len(rows)} rows, {sampled} products in {dt:.2f} s")
     return {"value": round(2.0 * total_p / total_t / 1e9, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "; ".join(samples) + " (time extrapolated to the whole workload by products)"}
+
+
+def cpu_baseline_error(mats, res, seconds: float, sp) -> tuple:
+    """CPU-baseline leg of an FP32 workload: the oracle on a seeded row sample (every row with at
+    least 2^22 partial products plus random rows, about `seconds` of work), timed and
+    extrapolated to the workload by products; and the max relative entry error of the GPU
+    product `res` on those rows against the FP64 oracle."""
+    import oracle
+    total_t = total_p = 0.0
+    worst = 0.0
+    samples = []
+    threads = 0
+    for (name, M), (_, plan, C) in zip(mats, res):
+        P = oracle.products_per_row(M, M)
+        heavy = np.nonzero(P >= (1 << 22))[0]
+        rng = np.random.default_rng(4321)
+        budget = max(int(seconds * 2e8) - int(P[heavy].sum()), 0)
+        order = rng.permutation(M.rows)
+        k = int(np.searchsorted(np.cumsum(P[order]), budget)) + 1
+        rows = np.unique(np.concatenate([heavy, order[:k]])).astype(np.int64)
+        t = time.perf_counter()
+        ref = oracle.spgemm(M, M, rows=rows)
+        dt = time.perf_counter() - t
+        threads = max(threads, ref.threads)
+        sampled = int(P[rows].sum())
+        total_t += int(P.sum()) * dt / max(sampled, 1)
+        total_p += int(P.sum())
+        rp = C.row_ptr.cpu().numpy().astype(np.int64)
+        for t_, i in enumerate(rows):
+            s_, e_ = int(rp[i]), int(rp[i + 1])
+            r = slice(ref.row_ptr[t_], ref.row_ptr[t_ + 1])
+            if e_ == s_:
+                continue
+            v = C.val[s_:e_].cpu().numpy().astype(np.float64)
+            nz = np.abs(ref.val[r]) > 0
+            if nz.any():
+                worst = max(worst, float((np.abs(v - ref.val[r])[nz] / np.abs(ref.val[r][nz])).max()))
+        samples.append(f"{name}: {len(rows)} rows ({len(heavy)} with >= 2^22 products), {sampled} products "
+                       f"in {dt:.2f} s")
+    cpu = {"value": round(2.0 * total_p / total_t / 1e9, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": "; ".join(samples) + " (time extrapolated to the whole workload by products)"}
+    return cpu, worst
 
 
 def run_reference(args):
@@ -764,8 +935,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lap2d1024+rmat20",
-                    choices=sorted(WORKLOADS) + ["batch_small", "batch_mid", "serve"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default=None, choices=["uniform10k", "rmat20_f32c", "batch4096", "serve20000"],
+                    help="run one of the other configurations alone")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="headline workload only (skip the uniform, FP32, batching and serving configs)")
+    ap.add_argument("--side-steps", type=int, default=3, help="timed steps of the FP32 config")
+    ap.add_argument("--side-warmup", type=int, default=3, help="warm-up steps of the other configs (>= 3)")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="timed steps of the end-to-end leg (<= --steps)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-accumulate", type=int, default=0, choices=[0, 1, 2],
                     help="FP64 sums: 0 shared atomics (default), 1 exact fixed point on the windowed rows, "
@@ -774,20 +951,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-products-per-step", type=float, default=2e8)
     ap.add_argument("--json-out", default=None)
-    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-requests", type=int, default=SERVE_REQUESTS)
     ap.add_argument("--serve-window-us", type=int, default=300)
     ap.add_argument("--serve-streams", type=int, default=2)
-    ap.add_argument("--serve-small-products", type=int, default=-1, help="server default when negative")
-    ap.add_argument("--serve-batch-entries", type=int, default=0, help="server default when 0")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         sys.stderr.write("note: fewer than 3 warm-up steps\n")
     if args.impl == "reference":
         line, rank = run_reference(args)
-    elif args.workload.startswith("batch"):
-        line, rank = run_batch(args)
-    elif args.workload == "serve":
-        line, rank = run_serve(args)
+    elif args.config:
+        line, rank = run_one_config(args)
     else:
         line, rank = run_ours(args)
     if rank == 0 and line is not None:

@@ -109,14 +109,9 @@ def _csr_from_sorted_keys(m: int, n: int, rows: np.ndarray, cols: np.ndarray) ->
     return rp, cols.astype(np.int32)
 
 
-def _binomial_counts(m: int, n: int, d: float, seed: int, stream: int) -> np.ndarray:
-    """k_i ~ Binomial(n, d) by inverting the CDF at a counter uniform per row."""
-    if m == 0:
-        return np.zeros(0, dtype=np.int64)
-    if d <= 0.0 or n == 0:
-        return np.zeros(m, dtype=np.int64)
-    if d >= 1.0:
-        return np.full(m, n, dtype=np.int64)
+def _binomial_cdf(n: int, d: float) -> tuple:
+    """(cdf, kmax): the Binomial(n, d) CDF on 0..kmax (tail beyond mean + 14 sd dropped), for
+    0 < d < 1 and n > 0."""
     mean = n * d
     sd = math.sqrt(n * d * (1.0 - d))
     kmax = int(min(n, math.ceil(mean + 14.0 * sd + 30.0)))
@@ -128,6 +123,18 @@ def _binomial_counts(m: int, n: int, d: float, seed: int, stream: int) -> np.nda
     )
     cdf = np.cumsum(np.exp(logpmf - logpmf.max()))
     cdf /= cdf[-1]
+    return cdf, kmax
+
+
+def _binomial_counts(m: int, n: int, d: float, seed: int, stream: int) -> np.ndarray:
+    """k_i ~ Binomial(n, d) by inverting the CDF at a counter uniform per row."""
+    if m == 0:
+        return np.zeros(0, dtype=np.int64)
+    if d <= 0.0 or n == 0:
+        return np.zeros(m, dtype=np.int64)
+    if d >= 1.0:
+        return np.full(m, n, dtype=np.int64)
+    cdf, kmax = _binomial_cdf(n, d)
     u = counter_uniform(seed, stream, np.arange(m, dtype=np.uint64))
     k = np.searchsorted(cdf, u, side="right")
     return np.minimum(k, kmax).astype(np.int64)
