@@ -233,8 +233,12 @@ def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: 
             infos[name] = info
             products += info["products"]
             launches += info["kernel_launches"]
+            step_st = {}
             for k, (ms, _) in sp.spgemm_plan_get_timings(plan).items():
-                stages.setdefault((name, "num_window" if k == "num_expand" else k), []).append(ms)
+                key = (name, "num_window" if k == "num_expand" else k)   # the expansion completes the pass
+                step_st[key] = step_st.get(key, 0.0) + ms
+            for key, ms in step_st.items():
+                stages.setdefault(key, []).append(ms)
             sp.spgemm_plan_destroy(plan)
         del res
     ms = float(np.mean(times))
