@@ -276,6 +276,94 @@ def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: 
     return out
 
 
+def config_reuse(args, sp, torch, steps: int, warmup: int) -> dict:
+    """Plan reuse (the symbolic/numeric split): numeric-only recompute on an existing plan, with
+    the input values changed in place between steps (same pattern), against the whole product
+    (plan, symbolic, allocate, numeric), FP64; on the 2D Laplacian 1024^2 and R-MAT 2^20 squares,
+    and on the multigrid Galerkin coarse operator R*(A*P) of the Laplacian (2x2 aggregation, two
+    products, the second reading the first's output)."""
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def ev_time(fn):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    def chain(stages):
+        """stages: list of (A, B-or-index of an earlier stage's output); returns [(plan, C)]"""
+        out = []
+        for A, B in stages:
+            Bm = out[B][1] if isinstance(B, int) else B
+            plan = sp.spgemm_plan(A, Bm)
+            sp.spgemm_symbolic(plan)
+            C = sp.alloc_output(plan)
+            sp.spgemm_numeric(plan, C)
+            out.append((plan, C))
+        return out
+
+    def destroy(res):
+        for plan, _ in res:
+            sp.spgemm_plan_destroy(plan)
+
+    cases = {}
+    L = synth.laplacian2d(1024)
+    dL = sp.DeviceCSR.from_host(L, "cuda")
+    cases["lap2d1024"] = (dL, [(dL, dL)])
+    Rm = synth.rmat(20, 16, seed=0)
+    dRm = sp.DeviceCSR.from_host(Rm, "cuda")
+    cases["rmat20"] = (dRm, [(dRm, dRm)])
+    dP = sp.DeviceCSR.from_host(synth.aggregation_prolongator(1024), "cuda")
+    dR = sp.DeviceCSR.from_host(synth.aggregation_restrictor(1024), "cuda")
+    cases["galerkin_lap2d1024"] = (dL, [(dL, dP), (dR, 0)])
+    out = {}
+    for name, (dA, stages) in cases.items():
+        for _ in range(warmup):
+            destroy(chain(stages))
+        full = []
+        products = 0
+        for _ in range(steps):
+            ms, res = ev_time(lambda: chain(stages))
+            full.append(ms)
+            products = sum(sp.spgemm_plan_get_info(p)["products"] for p, _ in res)
+            destroy(res)
+        res = chain(stages)
+        torch.cuda.synchronize()
+
+        def numeric_only():
+            for plan, C in res:
+                sp.spgemm_numeric(plan, C)
+
+        for _ in range(warmup):
+            dA.val.mul_(1.0 + 2.0 ** -20)
+            numeric_only()
+        num = []
+        for _ in range(steps):
+            dA.val.mul_(1.0 + 2.0 ** -20)   # new values, same pattern (outside the timed region)
+            ms, _ = ev_time(numeric_only)
+            num.append(ms)
+        for plan, _ in res:
+            sp.spgemm_plan_check(plan)
+        destroy(res)
+        del res
+        ms_f, ms_n = float(np.mean(full)), float(np.mean(num))
+        out[name] = {"products": products, "full_ms": round(ms_f, 4), "numeric_only_ms": round(ms_n, 4),
+                     "full_value": round(2.0 * products / (ms_f * 1e-3) / 1e9, 3),
+                     "numeric_only_value": round(2.0 * products / (ms_n * 1e-3) / 1e9, 3),
+                     "speedup": round(ms_f / ms_n, 3), "unit": UNIT, "steps": steps, "warmup": warmup}
+    out["description"] = ("numeric-only recompute on an existing plan (input values changed in place between steps) "
+                          "against the whole product; Galerkin R*(A*P) with 2x2 aggregation of the 1024^2 Laplacian "
+                          "(coarse operator = 2 x the 512^2 Laplacian, checked in the tests)")
+    del cases, dL, dRm, dP, dR, flush
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_one_config(args):
     """One of the other configurations alone (printed as its own JSON line)."""
     import torch
@@ -285,6 +373,8 @@ def run_one_config(args):
     name = args.config
     if name == "uniform10k":
         return _product_config("uniform10k", args, sp, torch, max(ss, 10), max(sw, 10)), 0
+    if name == "plan_reuse":
+        return config_reuse(args, sp, torch, max(ss, 5), sw), 0
     if name == "rmat20_f32c":
         return _product_config("rmat20_f32c", args, sp, torch, ss, sw, cpu_err=True), 0
     if name == "batch4096":
@@ -301,6 +391,7 @@ def run_configs(args, sp, torch) -> dict:
     sw, ss = max(3, args.side_warmup), max(1, args.side_steps)
     t0 = time.perf_counter()
     out["uniform10k"] = _product_config("uniform10k", args, sp, torch, max(ss, 10), max(sw, 10))
+    out["plan_reuse"] = config_reuse(args, sp, torch, max(ss, 5), sw)
     out["rmat20_f32c"] = _product_config("rmat20_f32c", args, sp, torch, ss, sw, cpu_err=True)
     jobs = _device_jobs(range(BATCH_JOBS), sp, torch)
     out["batch4096"] = config_batch(args, sp, torch, jobs, sw, 1)
@@ -940,7 +1031,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--config", default=None, choices=["uniform10k", "rmat20_f32c", "batch4096", "serve20000"],
+    ap.add_argument("--config", default=None, choices=["uniform10k", "plan_reuse", "rmat20_f32c", "batch4096", "serve20000"],
                     help="run one of the other configurations alone")
     ap.add_argument("--no-configs", action="store_true",
                     help="headline workload only (skip the uniform, FP32, batching and serving configs)")

@@ -12,6 +12,8 @@ from .generators import (  # noqa: F401
     identity,
     laplacian2d,
     laplacian3d,
+    aggregation_prolongator,
+    aggregation_restrictor,
     rmat,
     uniform_random,
     batch_job_params,

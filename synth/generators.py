@@ -267,6 +267,32 @@ def laplacian3d(g: int, dtype=np.float64) -> CSR:
     return _stencil((g, g, g), 6.0, dtype)
 
 
+def aggregation_prolongator(g: int, dtype=np.float64) -> CSR:
+    """Piecewise-constant prolongation of a 2D multigrid hierarchy: the (g*g) x ((g/2)*(g/2))
+    matrix P with P[f, c] = 1 when fine node f = (y, x) of a row-major g x g grid lies in the
+    2x2 aggregate c = (y // 2, x // 2) (g even). One entry per fine row."""
+    if g % 2:
+        raise ValueError("g must be even")
+    h = g // 2
+    f = np.arange(g * g, dtype=np.int64)
+    y, x = f // g, f % g
+    cols = (y // 2) * h + (x // 2)
+    return CSR(g * g, h * h, np.arange(g * g + 1, dtype=np.int64), cols.astype(np.int32), np.ones(g * g, dtype=dtype))
+
+
+def aggregation_restrictor(g: int, dtype=np.float64) -> CSR:
+    """R = P^T for aggregation_prolongator(g): coarse row c lists its four fine nodes in order."""
+    if g % 2:
+        raise ValueError("g must be even")
+    h = g // 2
+    c = np.arange(h * h, dtype=np.int64)
+    cy, cx = c // h, c % h
+    base = (2 * cy) * g + 2 * cx
+    cols = np.stack([base, base + 1, base + g, base + g + 1], axis=1).reshape(-1)
+    return CSR(h * h, g * g, np.arange(0, 4 * h * h + 1, 4, dtype=np.int64), cols.astype(np.int32),
+               np.ones(4 * h * h, dtype=dtype))
+
+
 def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
          seed: int = 0, dtype=np.float64, lo: float = 0.0, hi: float = 1.0,
          chunk: int = 1 << 22) -> CSR:

@@ -326,3 +326,41 @@ def test_rmat_2e17_full_default_config(accumulate):
     compare_all_rows(A, A, C, check)
     assert seen[0] == info["nnz_c"]
     sp.spgemm_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("g", [8, 96, 1024])
+def test_galerkin_triple_product(g):
+    """Multigrid coarse operator R*(A*P) with 2x2 aggregation on the 2D Laplacian, as two library
+    products (the second takes the first's device output as its B): A*P matches the oracle and
+    R*(A*P) is exactly 2 x the coarse 5-point Laplacian; then the values of A change and both
+    numeric passes rerun on their plans."""
+    import paper_2004_13907_gb300 as sp
+    A = synth.laplacian2d(g)
+    P = synth.aggregation_prolongator(g)
+    R = synth.aggregation_restrictor(g)
+    dA, dP, dR = (sp.DeviceCSR.from_host(M, "cuda") for M in (A, P, R))
+    p1 = sp.spgemm_plan(dA, dP)
+    sp.spgemm_symbolic(p1)
+    AP = sp.alloc_output(p1)
+    sp.spgemm_numeric(p1, AP)
+    p2 = sp.spgemm_plan(dR, AP)
+    sp.spgemm_symbolic(p2)
+    Ac = sp.alloc_output(p2)
+    sp.spgemm_numeric(p2, Ac)
+    sp.spgemm_plan_check(p1)
+    sp.spgemm_plan_check(p2)
+    H = AP.to_host()
+    assert_parity(A, P, H.row_ptr.numpy().astype(np.int64), H.col.numpy(), H.val.numpy())
+    L = synth.laplacian2d(g // 2)
+    Hc = Ac.to_host()
+    assert np.array_equal(Hc.row_ptr.numpy().astype(np.int64), L.row_ptr)
+    assert np.array_equal(Hc.col.numpy(), L.col)
+    assert np.array_equal(Hc.val.numpy(), 2.0 * L.val)
+    # plan reuse: A scaled by 3 in place (same pattern), both numeric passes again
+    dA.val.mul_(3.0)
+    sp.spgemm_numeric(p1, AP)
+    sp.spgemm_numeric(p2, Ac)
+    sp.spgemm_plan_check(p2)
+    assert np.array_equal(Ac.val.cpu().numpy(), 6.0 * L.val)
+    sp.spgemm_plan_destroy(p1)
+    sp.spgemm_plan_destroy(p2)

@@ -371,3 +371,21 @@ def test_dense_accumulator_equals_ordered_map(case):
     rows = np.arange(0, A.rows, 3)
     assert np.array_equal(oracle.spgemm(A, B, rows=rows, method="dense").val,
                           oracle.spgemm(A, B, rows=rows, method="map").val)
+
+
+@pytest.mark.parametrize("g", [2, 4, 10, 64])
+def test_galerkin_coarse_laplacian_closed_form(g):
+    """Multigrid Galerkin product R*(A*P) with 2x2 aggregation (P piecewise constant, R = P^T) of
+    the 2D 5-point Laplacian: every coarse entry sums the fine couplings between two aggregates,
+    16 - 8 = 8 on the diagonal and -2 between neighbouring aggregates, i.e. exactly twice the
+    5-point Laplacian of the coarse grid (Dirichlet boundaries included)."""
+    A = synth.laplacian2d(g)
+    P = synth.aggregation_prolongator(g)
+    R = synth.aggregation_restrictor(g)
+    assert np.array_equal(R.to_dense(), P.to_dense().T)
+    AP = oracle.spgemm(A, P)
+    APc = synth.CSR(A.rows, P.cols, AP.row_ptr, AP.col, AP.val)
+    Ac = oracle.spgemm(R, APc)
+    L = synth.laplacian2d(g // 2)
+    assert np.array_equal(Ac.row_ptr, L.row_ptr) and np.array_equal(Ac.col, L.col)
+    assert np.array_equal(Ac.val, 2.0 * L.val)
