@@ -45,6 +45,7 @@ WORKLOADS = {
     "uniform10k": [("uniform_10k_d1e-3", lambda: synth.uniform_random(10_000, 10_000, 1e-3, seed=0), "f64")],
     "rmat16": [("rmat_2e16_deg16", lambda: synth.rmat(16, 16, seed=0), "f64")],
     "rmat17": [("rmat_2e17_deg16", lambda: synth.rmat(17, 16, seed=0), "f64")],
+    "rmat17_f32c": [("rmat_2e17_deg16_f32", lambda: synth.rmat(17, 16, seed=0, dtype=np.float32), "f32c")],
 }
 DEFAULT_WORKLOAD = "lap2d1024+rmat20"
 WORKLOAD_DESC = {
@@ -125,12 +126,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _traffic(kernel_file: str, workload: str, root: str = ROOT):
-    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, when it was
-    taken on this workload with the kernel source as it is now (else None)."""
+def _traffic(alg_bytes: int, root: str = ROOT):
+    """DRAM bytes of the windowed pass (k_num_window + k_expand_cols) per launch: the committed
+    small-case record (R-MAT 2^17, one-pass ncu launch list) gives DRAM bytes per algorithmic byte,
+    scaled to this launch by its algorithmic bytes; None when the record was taken on another
+    version of the kernel source."""
     import hashlib
-    path = os.path.join(root, "profiles", f"k_num_window_{workload}.md")
-    src = os.path.join(root, "paper_2004_13907_gb300", "csrc", kernel_file)
+    path = os.path.join(root, "profiles", "k_num_window_rmat17.md")
+    src = os.path.join(root, "paper_2004_13907_gb300", "csrc", "k_window.cu")
     try:
         want = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         fields = {}
@@ -141,7 +144,7 @@ def _traffic(kernel_file: str, workload: str, root: str = ROOT):
                 fields[m.group(1).strip()] = m.group(2).strip().strip("`")
         if fields.get("kernel source sha256[:16]") != want:
             return None
-        return int(fields["dram bytes per launch"].replace(",", ""))
+        return int(round(float(fields["dram bytes per algorithmic byte"]) * alg_bytes))
     except Exception:
         return None
 
@@ -179,6 +182,20 @@ def _window_bytes(info: dict) -> tuple:
     prods = sum(info["num_class_products"][0:4])
     cnnz = sum(info["num_class_cnnz"][0:4])
     return 8 * rows + 20 * annz + 12 * prods + 12 * cnnz, prods
+
+
+def _class_bytes(info: dict, vbytes: int = 8) -> dict:
+    """Algorithmic bytes of each numeric row class's kernel: per row 8 (its A row pointers) + 8
+    (its C row pointer), per A entry 4 + v (column, value) + 8 (start and end of the named B row),
+    per partial product 4 + v (the gathered B column and value), per entry of C 4 + v."""
+    import paper_2004_13907_gb300 as sp
+    out = {}
+    for c, name in enumerate(sp._native.NUM_CLASSES):
+        rows = info["num_class_rows"][c]
+        if rows and name != "empty":
+            out[name] = (16 * rows + (12 + vbytes) * info["num_class_annz"][c] +
+                         (4 + vbytes) * info["num_class_products"][c] + (4 + vbytes) * info["num_class_cnnz"][c])
+    return out
 
 
 def _numeric_bytes(info: dict, m: int) -> int:
@@ -498,7 +515,9 @@ def run_ours(args):
                 "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": bytes_,
-                "launch_ms": round(dom_ms, 4), "traffic": _traffic("k_window.cu", args.workload)}
+                "launch_ms": round(dom_ms, 4), "traffic": _traffic(bytes_),
+                "traffic_source": "R-MAT 2^17 DRAM bytes per algorithmic byte (profiles/k_num_window_rmat17.md) x "
+                                  "this launch's algorithmic bytes; B fits L2 at 2^17, so a lower bound here"}
         if all(p == "f64" for p in precs.values()):
             roof.update(_fp64_pipe(wprods, dom_ms,
                                    torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count,
@@ -518,6 +537,7 @@ def run_ours(args):
             "numeric_alg_bytes": _numeric_bytes(info, d["rows"]),
             "num_class_rows": {sp._native.NUM_CLASSES[c]: info["num_class_rows"][c]
                                for c in range(len(sp._native.NUM_CLASSES)) if info["num_class_rows"][c]},
+            "num_class_alg_bytes": _class_bytes(info, 4 if precs[name] == "f32c" else 8),
         }
         nb = breakdown[name]["numeric_alg_bytes"]
         breakdown[name]["numeric_GBps"] = round(nb / (breakdown[name]["numeric_ms"] * 1e-3) / 1e9, 1)

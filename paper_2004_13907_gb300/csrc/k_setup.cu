@@ -72,30 +72,57 @@ __device__ __forceinline__ int32_t aggregated_slot(int32_t* counters, int cls, b
   return base + rank;
 }
 
-// P_i for a tile of kTileRows rows (256 threads, four rows each). Short rows are summed
-// by their own thread, rows with more than 64 entries by the whole warp.
+// P_i for 256 rows (a quarter of a tile of kTileRows rows; one row per thread, so that even a
+// small matrix spreads over many blocks). Short rows are summed by their own thread, rows with
+// more than 64 entries by the whole warp, and rows with more than kCountBlockNa entries by the
+// whole block after the others. The block adds its class counts, sum and maximum of P_i into its
+// tile's (zeroed) histogram with global atomics.
+// Rows with more entries than this are counted by the whole block of k_count.
+constexpr int64_t kCountBlockNa = 2048;
+
+// Row `row` of A as [a0, a0 + na) clamped to the stored entries, so that an input the
+// validation kernels have not yet rejected cannot send a read outside A's arrays.
+__device__ __forceinline__ void clamped_row(const DevCsr& A, int64_t row, int64_t& a0, int64_t& na) {
+  int64_t s = A.rp[row], e = A.rp[row + 1];
+  s = s < 0 ? 0 : (s > A.nnz ? A.nnz : s);
+  e = e < s ? s : (e > A.nnz ? A.nnz : e);
+  a0 = s;
+  na = e - s;
+}
+
 __global__ void __launch_bounds__(256) k_count(DevCsr A, DevCsr B, ClassParams cp, int64_t* P,
                                                int32_t* nnz_row, int32_t* tile_hist,
                                                int64_t* tile_sum, int64_t* tile_max) {
   __shared__ int32_t hist[kMaxClasses];
   __shared__ unsigned long long s_sum, s_max;
+  __shared__ int32_t s_ndef;                 // rows left to the whole block (longest rows)
+  __shared__ int64_t s_def[256];
+  __shared__ long long s_red[8];
   if (threadIdx.x < kMaxClasses) hist[threadIdx.x] = 0;
-  if (threadIdx.x == 0) { s_sum = 0; s_max = 0; }
+  if (threadIdx.x == 0) { s_sum = 0; s_max = 0; s_ndef = 0; }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int64_t t = blockIdx.x;
+  const int64_t t = blockIdx.x / (kTileRows / 256);   // the tile this block belongs to
   unsigned long long my_sum = 0, my_max = 0;
-  for (int r = 0; r < kTileRows / 256; ++r) {
-    const int64_t row = t * kTileRows + r * 256 + threadIdx.x;
+  {
+    const int64_t row = blockIdx.x * int64_t(256) + threadIdx.x;
     const bool valid = row < A.rows;
     int64_t a0 = 0, na = 0;
-    if (valid) { a0 = A.rp[row]; na = A.rp[row + 1] - a0; }
+    if (valid) {
+      // the validation kernels run ahead in the same stream and the host reads their verdict
+      // only after this pass, so a row range or column of an invalid input is clamped here
+      // (its counts are then meaningless, but every access stays inside the arrays)
+      clamped_row(A, row, a0, na);
+    }
     int64_t p = 0;
-    const bool longrow = valid && na > 64;
-    if (valid && !longrow) {
+    const bool blockrow = valid && na > kCountBlockNa;   // summed by the whole block below
+    const bool longrow = valid && na > 64 && !blockrow;
+    if (blockrow) s_def[atomicAdd(&s_ndef, 1)] = row;
+    if (valid && !longrow && !blockrow) {
+#pragma unroll 4
       for (int64_t j = 0; j < na; ++j) {
         const int32_t k = A.col[a0 + j];
-        p += B.rp[k + 1] - B.rp[k];
+        if (k >= 0 && k < B.rows) p += B.rp[k + 1] - B.rp[k];
       }
     }
     unsigned lm = __ballot_sync(0xffffffffu, longrow);
@@ -107,13 +134,13 @@ __global__ void __launch_bounds__(256) k_count(DevCsr A, DevCsr B, ClassParams c
       int64_t acc = 0;
       for (int64_t j = lane; j < sna; j += 32) {
         const int32_t k = A.col[sa0 + j];
-        acc += B.rp[k + 1] - B.rp[k];
+        if (k >= 0 && k < B.rows) acc += B.rp[k + 1] - B.rp[k];
       }
       acc = warp_sum(acc);
       if (lane == src) p = acc;
     }
     int cls = kSymZero;
-    if (valid) {
+    if (valid && !blockrow) {
       const int32_t na32 = na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na);
       cls = sym_class(p, na32, row_params(cp, row));
       P[row] = p;
@@ -121,7 +148,35 @@ __global__ void __launch_bounds__(256) k_count(DevCsr A, DevCsr B, ClassParams c
       my_sum += static_cast<unsigned long long>(p);
       my_max = my_max > static_cast<unsigned long long>(p) ? my_max : static_cast<unsigned long long>(p);
     }
-    aggregated_slot(hist, cls, valid);
+    aggregated_slot(hist, cls, valid && !blockrow);
+  }
+  __syncthreads();
+  // the longest rows of the tile, one at a time, their entries spread over all 256 threads
+  const int ndef = s_ndef;
+  for (int d = 0; d < ndef; ++d) {
+    const int64_t row = s_def[d];
+    int64_t a0, na;
+    clamped_row(A, row, a0, na);
+    long long acc = 0;
+    for (int64_t j = threadIdx.x; j < na; j += 256) {
+      const int32_t k = A.col[a0 + j];
+      if (k >= 0 && k < B.rows) acc += B.rp[k + 1] - B.rp[k];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long p = 0;
+      for (int w = 0; w < 8; ++w) p += s_red[w];
+      const int32_t na32 = na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na);
+      const int cls = sym_class(p, na32, row_params(cp, row));
+      P[row] = p;
+      if (cls == kSymZero) nnz_row[row] = 0;
+      atomicAdd(&hist[cls], 1);
+      my_sum += static_cast<unsigned long long>(p);
+      my_max = my_max > static_cast<unsigned long long>(p) ? my_max : static_cast<unsigned long long>(p);
+    }
+    __syncthreads();
   }
   my_sum = warp_sum(my_sum);
   my_max = warp_min(~my_max);
@@ -131,10 +186,10 @@ __global__ void __launch_bounds__(256) k_count(DevCsr A, DevCsr B, ClassParams c
     atomicMax(&s_max, my_max);
   }
   __syncthreads();
-  if (threadIdx.x < kMaxClasses) tile_hist[t * kMaxClasses + threadIdx.x] = hist[threadIdx.x];
+  if (threadIdx.x < kMaxClasses && hist[threadIdx.x]) atomicAdd(&tile_hist[t * kMaxClasses + threadIdx.x], hist[threadIdx.x]);
   if (threadIdx.x == 0) {
-    tile_sum[t] = static_cast<int64_t>(s_sum);
-    if (tile_max) tile_max[t] = static_cast<int64_t>(s_max);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&tile_sum[t]), s_sum);
+    if (tile_max) atomicMax(reinterpret_cast<unsigned long long*>(&tile_max[t]), s_max);
   }
 }
 
@@ -197,7 +252,8 @@ __global__ void __launch_bounds__(256) k_scatter_sym(DevCsr A, ClassParams cp, c
     const bool valid = row < A.rows;
     int cls = 0;
     if (valid) {
-      const int64_t na = A.rp[row + 1] - A.rp[row];
+      int64_t a0, na;
+      clamped_row(A, row, a0, na);   // the same row length k_count classified (before validation's verdict)
       cls = sym_class(P[row], na > 0x7fffffff ? 0x7fffffff : static_cast<int32_t>(na), row_params(cp, row));
     }
     const int32_t pos = aggregated_slot(base, cls, valid);
@@ -355,8 +411,11 @@ int launch_count(const DevCsr& A, const DevCsr& B, ClassParams cp, int64_t* P, i
                   int32_t* tile_hist, int64_t* tile_sum, int64_t* tile_max, cudaStream_t s) {
   const int64_t ntiles = (A.rows + kTileRows - 1) / kTileRows;
   if (ntiles == 0) return 0;
-  k_count<<<static_cast<unsigned>(ntiles), 256, 0, s>>>(A, B, cp, P, nnz_row, tile_hist, tile_sum,
-                                                        tile_max);
+  cudaMemsetAsync(tile_hist, 0, sizeof(int32_t) * ntiles * kMaxClasses, s);
+  cudaMemsetAsync(tile_sum, 0, sizeof(int64_t) * ntiles, s);
+  if (tile_max) cudaMemsetAsync(tile_max, 0, sizeof(int64_t) * ntiles, s);
+  const int64_t blocks = (A.rows + 255) / 256;
+  k_count<<<static_cast<unsigned>(blocks), 256, 0, s>>>(A, B, cp, P, nnz_row, tile_hist, tile_sum, tile_max);
   return 1;
 }
 

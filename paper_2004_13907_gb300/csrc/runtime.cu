@@ -133,12 +133,12 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   if (o.validate) {
     uint32_t* starts = ws_get<uint32_t>(p, validate_words(A->nnz > B->nnz ? A->nnz : B->nnz), &st);
     if (st) return st;
+    // no wait here: the count kernels clamp every access, and the error word is read with the
+    // plan's summary below (an invalid input is reported before any other pass runs)
     conv += launch_validate(p->A, starts, &p->summary->err, s);
     conv += launch_validate(p->B, starts, &p->summary->err, s);
     stage_end(p, SPGEMM_STAGE_VALIDATE, conv, s);
     if ((st = cuda_status(cudaGetLastError(), "launching validation")) != SPGEMM_OK) return st;
-    if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
-    if (h.err) return error_bits_status(h.err);
   } else {
     stage_end(p, SPGEMM_STAGE_VALIDATE, conv, s);
   }
@@ -155,6 +155,9 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
     std::memcpy(p->sym_off, h.class_off, sizeof(p->sym_off));
     p->total_products = h.total;
     p->max_row_products = h.max_row;
+  } else if (o.validate) {
+    if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
+    if (h.err) return error_bits_status(h.err);
   }
   const int64_t nwin = p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0];
   if (nwin > 0) {
@@ -206,8 +209,14 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
     nl += launch_sym_warp(7, p->A, p->B, seg(kSymWarp1), cnt(kSymWarp1), p->nnz_row, err, p->num_sms, s);
     stage_end(p, SPGEMM_STAGE_SYM_WARP, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_TINY, s);
-    nl = launch_sym_tiny(p->A, p->B, seg(kSymTiny), cnt(kSymTiny), p->nnz_row, p->num_sms, s);
-    nl += launch_sym_micro(p->A, p->B, seg(kSymMicro), cnt(kSymMicro), p->nnz_row, p->num_sms, s);
+    if (cnt(kSymMicro) < kMicroMinRows) {
+      // few micro rows: a thread-per-row merge is one long chain of dependent loads, so they join
+      // the tiny rows (a warp per row; every micro row qualifies), which come just before them
+      nl = launch_sym_tiny(p->A, p->B, seg(kSymTiny), cnt(kSymTiny) + cnt(kSymMicro), p->nnz_row, p->num_sms, s);
+    } else {
+      nl = launch_sym_tiny(p->A, p->B, seg(kSymTiny), cnt(kSymTiny), p->nnz_row, p->num_sms, s);
+      nl += launch_sym_micro(p->A, p->B, seg(kSymMicro), cnt(kSymMicro), p->nnz_row, p->num_sms, s);
+    }
     stage_end(p, SPGEMM_STAGE_SYM_TINY, nl, s);
     stage_begin(p, SPGEMM_STAGE_SYM_SCAN, s);
     nl = launch_num_tiles(p->A, p->cp, p->P, p->nnz_row, p->tile_hist, p->tile_sum, &p->summary->cls_sums[0][0], s);
@@ -362,9 +371,10 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       stage_end(p, SPGEMM_STAGE_NUM_WARP, nl, s);
     }
     stage_begin(p, SPGEMM_STAGE_NUM_TINY, s);
-    nl = launch_num_tiny(mode, p->A, p->B, seg(kNumTiny), cnt(kNumTiny), p->c_off, C->col, C->val, p->rerun_flag,
-                         p->abase, err, p->num_sms, s);
-    if (!f32c)
+    const bool micro_as_tiny = f32c || cnt(kNumMicro) < kMicroMinRows;   // (F32 plans have no micro rows)
+    nl = launch_num_tiny(mode, p->A, p->B, seg(kNumTiny), cnt(kNumTiny) + (micro_as_tiny ? cnt(kNumMicro) : 0),
+                         p->c_off, C->col, C->val, p->rerun_flag, p->abase, err, p->num_sms, s);
+    if (!micro_as_tiny)
       nl += launch_num_micro(p->A, p->B, seg(kNumMicro), cnt(kNumMicro), p->c_off, C->col,
                              static_cast<double*>(C->val), p->abase, err, p->num_sms, s);
     stage_end(p, SPGEMM_STAGE_NUM_TINY, nl, s);

@@ -99,6 +99,10 @@ T* ws_alloc(spgemm_plan_s* p, int64_t count, spgemm_status* st);
 spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s);
 spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s);
 spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s);
+// Below this many micro rows (at most 8 A entries and 32 partial products) the rows take the
+// warp-per-row tiny kernels instead of the thread-per-row merge, whose dependent loads make it
+// pay only when many rows run at once.
+constexpr int64_t kMicroMinRows = 32768;
 // Bytes of FP64 scratch the FP32 rerun of windowed rows works in (rows of the plan's width).
 constexpr int64_t kRerunScratchBytes = int64_t(256) << 20;
 // Device bytes the numeric pass of a plan past its symbolic pass will still allocate (FP32 rerun
