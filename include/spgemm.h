@@ -307,6 +307,32 @@ spgemm_status spgemm_autotune_batch(int64_t n_jobs, const spgemm_csr_in* A, cons
                                     spgemm_prec prec, const spgemm_opts* base, int32_t reps,
                                     void* stream, spgemm_opts* best, spgemm_tune_report* report);
 
+/* ---- Format front-ends. The paper's CPU side reorganises the input matrices into its streamed
+ * row bundles and back (Sec. II); here the reorganisation between formats runs on the device, as
+ * a stable radix sort of the entries by their new row (see formats.cu). CSC is the CSR of the
+ * transpose, so a product of CSC matrices needs no conversion: C = A*B in CSC is
+ * C^T = B^T * A^T in CSR, i.e. spgemm_plan(B_csc viewed as CSR, A_csc viewed as CSR).
+ *
+ * spgemm_csr_transpose: T = M^T in CSR (= M in CSC). M: device CSR (int32 or int64 row_ptr),
+ * values of value_bytes bytes (8: FP64, 4: FP32) copied as they are. T: caller-allocated device
+ * arrays, row_ptr[M.cols + 1] (T->idx64_rowptr selects its type), col/val[M.nnz]; T->rows, cols
+ * and nnz are set on return. Rows of T list their entries in ascending column (the order of M's
+ * rows). Scratch (about 24 bytes per entry) comes from `alloc` (NULL: the library pool) on
+ * `stream` and is freed before return; the call waits for `stream`. Errors: INVALID_ARG (NULL
+ * arrays, bad value_bytes), INVALID_CSR (a column of M outside [0, M.cols)), UNSUPPORTED
+ * (nnz >= 2^32), INDEX_OVERFLOW (int32 row_ptr too small).
+ *
+ * spgemm_coo_to_csr: canonical CSR from nnz (row, col, val) triples in any order (device arrays,
+ * int32 indices, values of value_bytes bytes). C: caller-allocated, row_ptr[rows + 1], col/val[nnz];
+ * columns come out sorted within each row. A repeated (row, col) pair or an index out of range
+ * returns INVALID_CSR (the output of this library's products must be canonical). Scratch, waiting
+ * and the other errors as for spgemm_csr_transpose. */
+spgemm_status spgemm_csr_transpose(const spgemm_csr_in* M, int32_t value_bytes, spgemm_csr_out* T,
+                                   const spgemm_allocator* alloc, void* stream);
+spgemm_status spgemm_coo_to_csr(int64_t rows, int64_t cols, int64_t nnz, const int32_t* row, const int32_t* col,
+                                const void* val, int32_t value_bytes, spgemm_csr_out* C,
+                                const spgemm_allocator* alloc, void* stream);
+
 /* C = A*B without allocating any device memory, for callers that cannot allocate while they
  * call: services that reserve the whole device up front and hand out fixed buffers (an
  * allocation would fail or take memory promised to someone else), and real-time loops that

@@ -27,7 +27,7 @@ __all__ = [
     "spgemm_plan", "spgemm_symbolic", "spgemm_numeric", "spgemm_plan_get_info",
     "spgemm_plan_check", "spgemm_plan_get_timings", "spgemm_plan_destroy", "spgemm_multiply_host", "spgemm_multiply_noalloc",
     "spgemm_last_error", "spgemm_version", "multiply", "lib", "Batch", "spgemm_batch", "Server",
-    "spgemm_server_cfg_default", "spgemm_autotune_batch",
+    "spgemm_server_cfg_default", "spgemm_autotune_batch", "csr_transpose", "coo_to_csr", "multiply_csc",
 ]
 
 
@@ -323,6 +323,50 @@ def spgemm_multiply_noalloc(A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, stream=Non
         err.nnz_c = int(nnz.value)
         raise err
     return int(nnz.value)
+
+
+def csr_transpose(M: DeviceCSR, stream=None, idx64: bool | None = None) -> DeviceCSR:
+    """M^T in CSR (the CSC arrays of M), converted on the device (spgemm_csr_transpose)."""
+    vb = 4 if M.val.dtype == torch.float32 else 8
+    if idx64 is None:
+        idx64 = M.nnz > 0x7FFFFFFF
+    T = DeviceCSR(M.cols, M.rows, torch.empty(M.cols + 1, dtype=torch.int64 if idx64 else torch.int32,
+                                              device=M.col.device),
+                  torch.empty(M.nnz, dtype=torch.int32, device=M.col.device),
+                  torch.empty(M.nnz, dtype=M.val.dtype, device=M.col.device))
+    a, t = M.as_in(), T.as_out()
+    _native.check(lib().spgemm_csr_transpose(ctypes.byref(a), vb, ctypes.byref(t), None, _stream_handle(stream)))
+    return T
+
+
+def coo_to_csr(rows: int, cols: int, row: torch.Tensor, col: torch.Tensor, val: torch.Tensor, stream=None,
+               idx64: bool | None = None) -> DeviceCSR:
+    """Canonical CSR (columns sorted within each row) from device COO triples in any order
+    (spgemm_coo_to_csr); a repeated (row, col) pair raises INVALID_CSR."""
+    nnz = int(row.numel())
+    if int(col.numel()) != nnz or int(val.numel()) != nnz:
+        raise ValueError("row, col and val differ in length")
+    row = row.to(torch.int32).contiguous()
+    col = col.to(torch.int32).contiguous()
+    val = val.contiguous()
+    vb = 4 if val.dtype == torch.float32 else 8
+    if idx64 is None:
+        idx64 = nnz > 0x7FFFFFFF
+    C = DeviceCSR(rows, cols, torch.empty(rows + 1, dtype=torch.int64 if idx64 else torch.int32, device=val.device),
+                  torch.empty(nnz, dtype=torch.int32, device=val.device), torch.empty(nnz, dtype=val.dtype,
+                                                                                     device=val.device))
+    c = C.as_out()
+    _native.check(lib().spgemm_coo_to_csr(rows, cols, nnz, row.data_ptr(), col.data_ptr(), val.data_ptr(), vb,
+                                          ctypes.byref(c), None, _stream_handle(stream)))
+    return C
+
+
+def multiply_csc(A_csc: DeviceCSR, B_csc: DeviceCSR, prec=F64, opts: _native.Opts | None = None,
+                 stream=None) -> DeviceCSR:
+    """C = A*B for matrices held in CSC. Each argument is the CSR view of the matrix's
+    transpose (its CSC arrays: column pointers, row indices, values); the result is the CSR view
+    of C^T, i.e. C in CSC. No conversion runs: C^T = B^T * A^T is a CSR product of the views."""
+    return multiply(B_csc, A_csc, prec, opts, stream)
 
 
 def spgemm_multiply_host(A, B, prec=F64, opts: _native.Opts | None = None, stream=None,

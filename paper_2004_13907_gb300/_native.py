@@ -126,6 +126,10 @@ SIGNATURES = {
                                      ctypes.POINTER(CsrOut), c_i64, ctypes.POINTER(c_i64)]),
     "spgemm_multiply_noalloc": (c_i32, [ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut),
                                         c_i64, ctypes.POINTER(c_i64), c_vp]),
+    "spgemm_csr_transpose": (c_i32, [ctypes.POINTER(CsrIn), c_i32, ctypes.POINTER(CsrOut), ctypes.POINTER(Allocator),
+                                     c_vp]),
+    "spgemm_coo_to_csr": (c_i32, [c_i64, c_i64, c_i64, c_vp, c_vp, c_vp, c_i32, ctypes.POINTER(CsrOut),
+                                  ctypes.POINTER(Allocator), c_vp]),
     "spgemm_batch": (c_i32, [c_i64, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), c_i32, ctypes.POINTER(Opts),
                              ctypes.POINTER(Allocator), c_vp, ctypes.POINTER(c_vp)]),
     "spgemm_batch_result": (c_i32, [c_vp, c_i64, ctypes.POINTER(CsrOut)]),
