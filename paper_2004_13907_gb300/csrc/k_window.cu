@@ -394,6 +394,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
           }
           __syncthreads();
         }
+        // a resident row with a stored bitmap builds its pass-2 chunk inside the rank prefix's scan
+        const bool fused = stored && resident && split != nullptr;
         // rank prefix over the window's words: each thread owns kWordsPerThread consecutive
         // words of one group. A stored bitmap is read here straight into the thread's registers
         // and copied to shared memory; its window's whole blocks are stored (zero past the row's
@@ -421,8 +423,39 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
           int c = 0;
 #pragma unroll
           for (int t = 0; t < kWordsPerThread; ++t) c += __popc(wv[t]);
-          int32_t tot;
-          const int32_t tpre = block_excl_scan<int32_t>(c, s_scan32, &tot);
+          int32_t tot, tpre;
+          if (fused) {
+            // the same scan also numbers the chunk's B segments for pass 2 (whose offsets this
+            // thread already holds): one 64-bit word per thread carries its segment length (bits
+            // 0-31; a chunk's products fit 32 bits), whether it is non-empty (bits 32-41) and its
+            // words' set bits (bits 42-60)
+            int64_t bs = 0;
+            int32_t len = 0;
+            if (threadIdx.x < na) {
+              bs = e_rs[threadIdx.x] + ps0;
+              len = ps1 - ps0;
+            }
+            const long long packed = static_cast<long long>(static_cast<uint32_t>(len)) |
+                                     (static_cast<long long>(len > 0) << 32) | (static_cast<long long>(c) << 42);
+            long long ptot;
+            const long long ex = block_excl_scan<long long>(packed, s_scan64, &ptot);
+            tpre = static_cast<int32_t>(ex >> 42);
+            tot = static_cast<int32_t>(ptot >> 42);
+            if (len > 0) {
+              const int pos = static_cast<int>((ex >> 32) & 0x3ff);
+              c_bs[pos] = bs;
+              c_excl[pos] = static_cast<int32_t>(ex & 0xffffffffLL);
+              c_ent[pos] = threadIdx.x;
+            }
+            if (threadIdx.x == 0) {
+              const int nent = static_cast<int>((ptot >> 32) & 0x3ff);
+              c_excl[nent] = static_cast<int32_t>(ptot & 0xffffffffLL);
+              s_ctl[6] = nent;
+              s_ctl[7] = static_cast<int32_t>(ptot & 0xffffffffLL);
+            }
+          } else {
+            tpre = block_excl_scan<int32_t>(c, s_scan32, &tot);
+          }
           constexpr int kThreadsPerGroup = kGroupWords / kWordsPerThread;
           const int lead = lane & ~(kThreadsPerGroup - 1);
           const int32_t gbase = __shfl_sync(0xffffffffu, tpre, lead);
@@ -450,8 +483,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
         }
         // pass 2: accumulate a_ik * b_kj by rank
         for (int64_t base = 0; base < na; base += kNumThreads) {
-          if (na > kNumThreads || stored) build_chunk(a0, na, base, resident, b0, b1, w0, w1, ps0, ps1);
-          const int nent = s_ctl[6];    // the single chunk of a resident row is kept from pass 1
+          if (na > kNumThreads || (stored && !fused)) build_chunk(a0, na, base, resident, b0, b1, w0, w1, ps0, ps1);
+          const int nent = s_ctl[6];    // a resident row's single chunk: from pass 1 or the prefix scan
           const int32_t total = s_ctl[7];
           int32_t per = (total + kWarps - 1) / kWarps;
           per = (per + 31) & ~31;
