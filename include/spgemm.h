@@ -137,7 +137,13 @@ typedef struct spgemm_opts {
                                    bit. In 1 and 2 a row whose products span more than about 2^40
                                    in magnitude, or hold subnormal or non-finite values, is redone
                                    with FP64 atomics (counted in f32c_rerun_rows) */
-  int32_t reserved[10];
+  int32_t general_path;       /* 1: never take the small-product path. By default an F64 product
+                                 with at most 65,536 rows and 32,768 columns of C and the default
+                                 class options runs as a warp per row over a bitmap of all columns
+                                 (one symbolic kernel, a scan, one numeric kernel around the single
+                                 host read of nnz(C)); a row of C with more than 1,024 entries, or
+                                 this flag, sends it through the general row classes */
+  int32_t reserved[9];
 } spgemm_opts;
 
 /* Opaque plan: the work description of one product (row counts, row classes, row
@@ -199,6 +205,13 @@ void spgemm_opts_default(spgemm_opts* opts);
  * (the partial products of Algorithm 1's inner loops), and group the rows into classes by
  * work on the device. A and B are read on `stream`; the plan keeps their pointers.
  * Blocks `stream` once to read back the class sizes and sum_i P_i.
+ * Small products take a path of their own: F64, 1 <= A.rows <= 65,536, B.cols <= 32,768, the
+ * default class options (tiny_max 32, warp_max 1024, block_max 2048, window_hash_fill 4096,
+ * force_window 0, fp64_accumulate 0) and general_path 0. There the plan does not block: one
+ * warp per row of A counts and then computes its row over a bitmap of all columns of C, and
+ * INVALID_CSR in A, sum_i P_i and the class counters (every row in the 1024-slot warp class)
+ * come with spgemm_symbolic, which reads them back in its one host read. A row of C over
+ * 1,024 entries sends spgemm_symbolic back through the general plan (one more host read).
  * Errors: INVALID_ARG (NULL pointers, A.cols != B.rows, negative sizes, prec mismatch),
  * INVALID_CSR, OOM, CUDA, UNSUPPORTED (sizes beyond int32 column indices). */
 spgemm_status spgemm_plan(const spgemm_csr_in* A, const spgemm_csr_in* B, spgemm_prec prec,

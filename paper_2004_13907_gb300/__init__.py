@@ -47,8 +47,13 @@ def _vdtype(prec: int) -> torch.dtype:
     return torch.float64 if prec == F64 else torch.float32
 
 
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream_handle(stream) -> int:
     if stream is None:
+        if _raw_stream is not None:
+            return _raw_stream(torch._C._cuda_getDevice())
         return torch.cuda.current_stream().cuda_stream
     if isinstance(stream, torch.cuda.Stream):
         return stream.cuda_stream

@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspgemm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["k_setup.cu", "k_symbolic.cu", "k_numeric.cu", "k_window.cu", "runtime.cu", "api.cu",
-           "host_entry.cu", "noalloc.cu", "batch.cu", "server.cu", "autotune.cu", "k_rerun.cu", "formats.cu"]
+           "host_entry.cu", "noalloc.cu", "batch.cu", "server.cu", "autotune.cu", "k_rerun.cu", "formats.cu", "k_small.cu"]
 
 
 def _nvcc() -> str:

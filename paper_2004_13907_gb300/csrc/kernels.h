@@ -25,8 +25,44 @@ struct Summary {
   int64_t max_row;        // max P_i
   unsigned long long cls_sums[kMaxClasses][3];  // per numeric class: sum P_i, sum nnz(A_i), sum nnz(C_i)
   uint32_t err;
-  uint32_t pad;
+  uint32_t small_flags;   // small-product path: bit 0 = a row of C exceeds kSmallCap entries
+  unsigned long long small_products;   // small-product path: sum of P_i
+  uint32_t small_done;    // small-product path: blocks of the symbolic kernel that have finished
 };
+
+// ---- small products of narrow matrices (k_small.cu): a warp per row with a bitmap of all n
+// columns; taken for F64 plans with m <= kSmallMaxRows and n <= kSmallMaxCols, left for the
+// general path when a row of C has more than kSmallCap entries.
+constexpr int64_t kSmallMaxRows = 65536;
+constexpr int64_t kSmallMaxCols = 32768;
+constexpr int kSmallCap = 1024;
+// A CSR input with its row pointers as the caller stores them.
+struct SmallCsr {
+  int64_t rows, cols, nnz;
+  const void* rp;        // int32 or int64 row pointers
+  int32_t rp64;
+  const int32_t* col;
+  const void* val;
+};
+bool small_path_fits(int64_t m, int64_t n);
+// The symbolic kernel's grid: `blocks` blocks, each a contiguous run of `run` rows, its warps
+// taking `groups` rows at a time.
+struct SmallGrid {
+  int64_t blocks, run;
+  int groups;
+};
+SmallGrid small_sym_grid(const SmallCsr& A, int64_t n, int num_sms);
+// Symbolic pass, validation of A and B (when `check`) and the offsets of C's rows, in one kernel:
+// nnz_row[i], loc[i] (row i's offset within its block's run), blk[b] (run b's offset, b <= blocks,
+// blk[blocks] = nnz(C)), summary->total (nnz(C)), max_row (longest row of C), small_products,
+// small_flags, err. The summary must start zeroed.
+int launch_small_symbolic(const SmallCsr& A, const SmallCsr& B, SmallGrid g, int check, int32_t* nnz_row,
+                          int32_t* loc, int64_t* blk, Summary* sum, cudaStream_t s);
+// Numeric pass: the row pointers (int32 or int64), columns and values of C; `cap` = the longest
+// row of C (at most kSmallCap).
+int launch_small_numeric(const SmallCsr& A, const SmallCsr& B, SmallGrid g, int cap, const int32_t* nnz_row,
+                         const int32_t* loc, const int64_t* blk, void* crp, int crp64, int32_t* ccol, double* cval,
+                         uint32_t* err, int num_sms, cudaStream_t s);
 
 // ---- setup / scan kernels (k_setup.cu)
 int launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t s);

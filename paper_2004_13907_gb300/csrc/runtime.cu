@@ -2,8 +2,10 @@
 // symbolic (per-class symbolic kernels, row-offset scan, numeric classes) and numeric
 // (per-class numeric kernels). Two host synchronisations per product: after the plan
 // (class sizes, sum of P_i) and after the symbolic pass (nnz(C), so the caller can
-// allocate C).
+// allocate C); one, after the symbolic pass, on the small-product path.
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "runtime.h"
 
@@ -26,9 +28,41 @@ template <typename T>
 T* ws_get(spgemm_plan_s* p, int64_t count, spgemm_status* st) { return ws_alloc<T>(p, count, st); }
 
 
+// Page-locked host copies of the summary, shared by all plans: a read takes one from the free
+// list (allocating one on first need) and returns it, so the copy runs as a direct DMA.
+std::mutex g_pinned_mu;
+std::vector<Summary*> g_pinned_free;
+
+Summary* pinned_take() {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    if (!g_pinned_free.empty()) {
+      Summary* h = g_pinned_free.back();
+      g_pinned_free.pop_back();
+      return h;
+    }
+  }
+  void* h = nullptr;
+  if (cudaMallocHost(&h, sizeof(Summary)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return static_cast<Summary*>(h);
+}
+
+void pinned_give(Summary* h) {
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.push_back(h);
+}
+
 spgemm_status read_summary(spgemm_plan_s* p, Summary* h, cudaStream_t s) {
-  cudaError_t e = cudaMemcpyAsync(h, p->summary, sizeof(Summary), cudaMemcpyDeviceToHost, s);
+  Summary* hp = pinned_take();
+  cudaError_t e = cudaMemcpyAsync(hp ? hp : h, p->summary, sizeof(Summary), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (hp) {
+    if (e == cudaSuccess) *h = *hp;
+    pinned_give(hp);
+  }
   if (e != cudaSuccess) return cuda_status(e, "reading the pass summary");
   return SPGEMM_OK;
 }
@@ -76,6 +110,44 @@ void destroy_events(spgemm_plan_s* p) {
   p->ev_made = false;
 }
 
+namespace {
+
+SmallCsr small_csr(const spgemm_csr_in& M) {
+  return SmallCsr{M.rows, M.cols, M.nnz, M.row_ptr, M.idx64_rowptr, static_cast<const int32_t*>(M.col), M.val};
+}
+
+// The small-product path's plan: one workspace block for the summary, the row counts, their
+// offsets within the symbolic kernel's runs of rows and the runs' offsets; nothing is launched
+// but the summary's clearing (the symbolic kernel checks A and B itself) and nothing is read
+// back.
+spgemm_status plan_small(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_csr_in* B, cudaStream_t s) {
+  spgemm_status st = SPGEMM_OK;
+  const int64_t m = A->rows;
+  auto r256 = [](int64_t b) { return static_cast<size_t>((b + 255) & ~int64_t(255)); };
+  p->small_grid = small_sym_grid(small_csr(*A), B->cols, p->num_sms);
+  const size_t sum_bytes = r256(sizeof(Summary));
+  const size_t blk_bytes = r256(8 * (p->small_grid.blocks + 1));
+  const size_t row_bytes = r256(4 * m);
+  unsigned char* w = ws_get<unsigned char>(p, static_cast<int64_t>(sum_bytes + blk_bytes + 2 * row_bytes), &st);
+  if (st) return st;
+  p->summary = reinterpret_cast<Summary*>(w);
+  p->small_blk = reinterpret_cast<int64_t*>(w + sum_bytes);
+  p->nnz_row = reinterpret_cast<int32_t*>(w + sum_bytes + blk_bytes);
+  p->small_loc = reinterpret_cast<int32_t*>(w + sum_bytes + blk_bytes + row_bytes);
+  p->a_in = *A;
+  p->b_in = *B;
+  p->A = DevCsr{m, A->cols, A->nnz, nullptr, static_cast<const int32_t*>(A->col), A->val};
+  p->B = DevCsr{B->rows, B->cols, B->nnz, nullptr, static_cast<const int32_t*>(B->col), B->val};
+  cudaMemsetAsync(p->summary, 0, sizeof(Summary), s);
+  stage_end(p, SPGEMM_STAGE_VALIDATE, 0, s);
+  if ((st = cuda_status(cudaGetLastError(), "clearing the plan summary")) != SPGEMM_OK) return st;
+  p->state = 0;
+  return SPGEMM_OK;
+}
+
+
+}  // namespace
+
 spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_csr_in* B,
                        cudaStream_t s) {
   spgemm_status st = SPGEMM_OK;
@@ -87,6 +159,13 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   const int64_t* brp = static_cast<const int64_t*>(B->row_ptr);
   int conv = 0;
   stage_begin(p, SPGEMM_STAGE_VALIDATE, s);
+  const spgemm_opts& o = p->opts;
+  // small narrow F64 products with the default class options: a warp per row over a bitmap of all
+  // columns (k_small.cu), one host read in all
+  p->small = p->prec == SPGEMM_F64 && !p->abase && !p->awidth && !o.general_path && !o.force_window &&
+             o.fp64_accumulate == 0 && o.tiny_max == 32 && o.warp_max == 1024 && o.block_max == 2048 &&
+             o.window_hash_fill == 4096 && m > 0 && small_path_fits(m, n);
+  if (p->small) return plan_small(p, A, B, s);
   if (!A->idx64_rowptr) {
     int64_t* t = ws_get<int64_t>(p, m + 1, &st);
     if (st) return st;
@@ -101,7 +180,6 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   }
   p->A = DevCsr{m, A->cols, A->nnz, arp, A->col, A->val};
   p->B = DevCsr{B->rows, n, B->nnz, brp, B->col, B->val};
-  const spgemm_opts& o = p->opts;
   if (p->width <= 0) p->width = n;
   p->cp.n = p->width;
   p->cp.rwidth = p->awidth;
@@ -188,6 +266,38 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
 spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
   spgemm_status st;
   const int64_t m = p->A.rows;
+  if (p->small) {
+    stage_begin(p, SPGEMM_STAGE_SYM_WARP, s);
+    const int nl = launch_small_symbolic(small_csr(p->a_in), small_csr(p->b_in), p->small_grid, p->opts.validate,
+                                         p->nnz_row, p->small_loc, p->small_blk, p->summary, s);
+    stage_end(p, SPGEMM_STAGE_SYM_WARP, nl, s);
+    if ((st = cuda_status(cudaGetLastError(), "launching the small-product symbolic pass")) != SPGEMM_OK) return st;
+    Summary h;
+    if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
+    if (h.err) return error_bits_status(h.err);
+    if (h.small_flags) {
+      // a row of C is too long for the small path: plan and count again through the row classes
+      const spgemm_csr_in a = p->a_in, b = p->b_in;
+      p->opts.general_path = 1;
+      p->small = false;
+      if ((st = plan_run(p, &a, &b, s)) != SPGEMM_OK) return st;
+      return symbolic_run(p, s);
+    }
+    p->total_products = static_cast<int64_t>(h.small_products);
+    p->nnz_c = h.total;
+    p->small_cap = static_cast<int>(h.max_row);
+    // every row counts as one warp-table row in the plan's class counters
+    for (int c = 0; c <= kMaxClasses; ++c) {
+      p->sym_off[c] = c <= kSymWarp3 ? 0 : m;
+      p->num_off[c] = c <= kNumWarp3 ? 0 : m;
+    }
+    std::memset(p->cls_sums, 0, sizeof(p->cls_sums));
+    p->cls_sums[kNumWarp3][0] = static_cast<unsigned long long>(h.small_products);
+    p->cls_sums[kNumWarp3][1] = static_cast<unsigned long long>(p->A.nnz);
+    p->cls_sums[kNumWarp3][2] = static_cast<unsigned long long>(h.total);
+    p->state = 1;
+    return SPGEMM_OK;
+  }
   auto seg = [&](int c) { return p->perm_s + p->sym_off[c]; };
   auto cnt = [&](int c) { return p->sym_off[c + 1] - p->sym_off[c]; };
   uint32_t* err = &p->summary->err;
@@ -287,10 +397,22 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
   const int mode = f32c ? kModeF32C : kModeF64;
   // FP64 windowed rows: exact fixed-point accumulation when the caller asks for it
   const bool fx = !f32c && p->opts.fp64_accumulate != 0;
-  stage_begin(p, SPGEMM_STAGE_NUM_ROWPTR, s);
-  int nl = launch_write_rowptr(p->c_off, m + 1, C->row_ptr, C->idx64_rowptr, s);
-  stage_end(p, SPGEMM_STAGE_NUM_ROWPTR, nl, s);
   p->f32c_rerun_rows = 0;
+  int nl;
+  if (p->small) {
+    // the numeric kernel writes C's row pointers as well
+    stage_begin(p, SPGEMM_STAGE_NUM_WARP, s);
+    nl = launch_small_numeric(small_csr(p->a_in), small_csr(p->b_in), p->small_grid, p->small_cap, p->nnz_row,
+                              p->small_loc, p->small_blk, C->row_ptr, C->idx64_rowptr, C->col,
+                              static_cast<double*>(C->val), &p->summary->err, p->num_sms, s);
+    stage_end(p, SPGEMM_STAGE_NUM_WARP, nl, s);
+    if ((st = cuda_status(cudaGetLastError(), "launching the small-product numeric pass")) != SPGEMM_OK) return st;
+    p->state = 2;
+    return SPGEMM_OK;
+  }
+  stage_begin(p, SPGEMM_STAGE_NUM_ROWPTR, s);
+  nl = launch_write_rowptr(p->c_off, m + 1, C->row_ptr, C->idx64_rowptr, s);
+  stage_end(p, SPGEMM_STAGE_NUM_ROWPTR, nl, s);
   if (m > 0) {
     auto seg = [&](int c) { return p->perm_n + p->num_off[c]; };
     auto cnt = [&](int c) { return p->num_off[c + 1] - p->num_off[c]; };

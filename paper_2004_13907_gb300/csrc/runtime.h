@@ -73,6 +73,12 @@ struct spgemm_plan_s {
   int32_t* rerun_flag = nullptr;     // per row: 1 = recompute in FP64
   uint16_t* bexp = nullptr;          // largest biased exponent per row of B (exact FP64 accumulation)
   bool fx_rerun_pending = false;     // the last numeric pass listed FP64 reruns in counters[6]
+  bool small = false;                // the small-product path (k_small.cu) holds this plan
+  int small_cap = 0;                 // small path: longest row of C (from the symbolic pass)
+  spg::SmallGrid small_grid{};       // small path: the symbolic kernel's runs of rows
+  int32_t* small_loc = nullptr;      // small path: row offsets within their run
+  int64_t* small_blk = nullptr;      // small path: offsets of the runs (and nnz(C) last)
+  spgemm_csr_in a_in{}, b_in{};      // small path: the inputs as the caller gave them
   int32_t* rerun_list = nullptr;
   int64_t sym_off[spg::kMaxClasses + 1] = {};
   int64_t num_off[spg::kMaxClasses + 1] = {};

@@ -60,32 +60,31 @@ def test_reference_arm_is_rank0_only(monkeypatch):
 
 
 def test_traffic_lookup_reads_the_profile_only_for_the_current_source(tmp_path):
-    """The bench's roofline traffic comes from a committed ncu summary whose recorded source hash
-    matches the kernel file as it is; a stale summary gives None."""
+    """The bench's roofline traffic comes from a committed ncu summary (DRAM bytes per algorithmic
+    byte of the windowed pass) whose recorded source hash matches the kernel file as it is; a stale
+    summary gives None."""
     import hashlib
     sys.path.insert(0, ROOT)
     import bench
     (tmp_path / "profiles").mkdir()
     csrc = tmp_path / "paper_2004_13907_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    (csrc / "k.cu").write_text("__global__ void k() {}\n")
-    sha = hashlib.sha256((csrc / "k.cu").read_bytes()).hexdigest()[:16]
-    prof = tmp_path / "profiles" / "k_num_window_w.md"
-    prof.write_text(f"# k\n\n- kernel source sha256[:16]: `{sha}`\n- k: 1 B read, 2 B written\n"
-                    "- dram bytes per launch: 1,234\n")
-    assert bench._traffic("k.cu", "w", root=str(tmp_path)) == 1234
-    (csrc / "k.cu").write_text("__global__ void k() { }\n")
-    assert bench._traffic("k.cu", "w", root=str(tmp_path)) is None
-    assert bench._traffic("k.cu", "other", root=str(tmp_path)) is None
+    (csrc / "k_window.cu").write_text("__global__ void k() {}\n")
+    sha = hashlib.sha256((csrc / "k_window.cu").read_bytes()).hexdigest()[:16]
+    prof = tmp_path / "profiles" / "k_num_window_rmat17.md"
+    prof.write_text(f"# k\n\n- kernel source sha256[:16]: `{sha}`\n- dram bytes per algorithmic byte: 0.25\n")
+    assert bench._traffic(4000, root=str(tmp_path)) == 1000
+    (csrc / "k_window.cu").write_text("__global__ void k() { }\n")
+    assert bench._traffic(4000, root=str(tmp_path)) is None
 
 
 def test_committed_window_profile_parses():
-    """The committed summary of the windowed pass on the default workload carries a source hash
-    and a per-launch byte count."""
+    """The committed small-case summary of the windowed pass carries a source hash and a ratio of
+    DRAM bytes to algorithmic bytes."""
     import re
-    text = open(os.path.join(ROOT, "profiles", "k_num_window_lap2d1024+rmat20.md")).read()
+    text = open(os.path.join(ROOT, "profiles", "k_num_window_rmat17.md")).read()
     assert re.search(r"- kernel source sha256\[:16\]: `[0-9a-f]{16}`", text)
-    assert re.search(r"- dram bytes per launch: [0-9,]+", text)
+    assert re.search(r"- dram bytes per algorithmic byte: [0-9.]+", text)
 
 
 def test_fp64_pipe_fraction():

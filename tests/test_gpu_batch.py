@@ -135,7 +135,7 @@ def test_batch_mixed_widths(force_window):
     # own column counts but below the widest job's)
     want = np.zeros(16, dtype=np.int64)
     for a, b in zip(dA, dB):
-        plan = sp.spgemm_plan(a, b, opts=sp.spgemm_opts_default(force_window=force_window))
+        plan = sp.spgemm_plan(a, b, opts=sp.spgemm_opts_default(force_window=force_window, general_path=1))
         want += np.array(sp.spgemm_plan_get_info(plan)["sym_class_rows"])
         sp.spgemm_plan_destroy(plan)
     assert np.array_equal(np.array(batch.info()["sym_class_rows"]), want)

@@ -27,11 +27,13 @@ def opts(**kw):
     return sp.spgemm_opts_default(**kw)
 
 
-def test_uniform_10k_full():
-    """C = A*A, A 10,000 x 10,000 at density 1e-3 (~10 per row), values U[-1,1]."""
+@pytest.mark.parametrize("general", [0, 1])
+def test_uniform_10k_full(general):
+    """C = A*A, A 10,000 x 10,000 at density 1e-3 (~10 per row), values U[-1,1]: the small-product
+    path and the general row classes."""
     A = synth.uniform_random(10_000, 10_000, 1e-3, seed=0)
-    rp, col, val, info0, info, _ = run_gpu(A, A)
-    assert info0["products"] == int(oracle.products_per_row(A, A).sum())
+    rp, col, val, info0, info, _ = run_gpu(A, A, opts=opts(general_path=general))
+    assert info["products"] == int(oracle.products_per_row(A, A).sum())
     assert_parity(A, A, rp, col, val)
 
 
@@ -53,9 +55,10 @@ def test_laplacian2d_1024_full():
 
 
 @pytest.mark.parametrize("scale", [10, 13, 15])
-def test_rmat_small_full(scale):
+@pytest.mark.parametrize("general", [0, 1])
+def test_rmat_small_full(scale, general):
     A = synth.rmat(scale, 16, seed=3)
-    rp, col, val, info0, info, _ = run_gpu(A, A)
+    rp, col, val, info0, info, _ = run_gpu(A, A, opts=opts(general_path=general))
     assert_parity(A, A, rp, col, val)
 
 
@@ -146,7 +149,7 @@ def test_micro_and_tiny_rows(kw):
     """Rows around the micro/tiny boundary (nnz(A_i) from 0 to 12, B rows of 0-3 entries over
     300 columns, so heads collide often and some rows exceed 32 products)."""
     A, B = _short_rows(4000, 5000, 300, lambda i: i % 13, 3, seed=40)
-    rp, col, val, _, info, _ = run_gpu(A, B, opts=opts(**kw))
+    rp, col, val, _, info, _ = run_gpu(A, B, opts=opts(general_path=1, **kw))
     assert_parity(A, B, rp, col, val)
     if not kw:
         import paper_2004_13907_gb300 as sp
@@ -193,7 +196,13 @@ def test_empty_rows_mixed_with_heavy_rows():
 
 
 def test_invalid_csr_is_reported():
+    """The general path reports invalid inputs at the plan (the small-product path, which plans
+    without a host read, reports them at the symbolic pass: tests/test_gpu_small.py)."""
     import paper_2004_13907_gb300 as sp
+
+    def plan(a, b):
+        return sp.spgemm_plan(a, b, opts=sp.spgemm_opts_default(general_path=1))
+
     A = synth.uniform_random(50, 50, 0.1, seed=18)
     col = A.col.copy()
     r = int(np.argmax(np.diff(A.row_ptr) >= 2))
@@ -202,31 +211,31 @@ def test_invalid_csr_is_reported():
     bad = synth.CSR(A.rows, A.cols, A.row_ptr, col, A.val)
     dA = sp.DeviceCSR.from_host(bad, "cuda")
     with pytest.raises(sp.SpgemmError) as ei:
-        sp.spgemm_plan(dA, dA)
+        plan(dA, dA)
     assert ei.value.name == "INVALID_CSR"
     col2 = A.col.copy()
     col2[0] = 50                                     # out of range
     dA = sp.DeviceCSR.from_host(synth.CSR(A.rows, A.cols, A.row_ptr, col2, A.val), "cuda")
     with pytest.raises(sp.SpgemmError) as ei:
-        sp.spgemm_plan(dA, dA)
+        plan(dA, dA)
     assert ei.value.name == "INVALID_CSR"
     col3 = A.col.copy()
     col3[s + 1] = col3[s]                            # repeated column in a row
     dA = sp.DeviceCSR.from_host(synth.CSR(A.rows, A.cols, A.row_ptr, col3, A.val), "cuda")
     with pytest.raises(sp.SpgemmError) as ei:
-        sp.spgemm_plan(dA, dA)
+        plan(dA, dA)
     assert ei.value.name == "INVALID_CSR"
     rp4 = A.row_ptr.copy()
     rp4[r + 1], rp4[r + 2] = rp4[r + 2], rp4[r + 1]  # decreasing row pointers (inside [0, nnz])
     if rp4[r + 1] != rp4[r + 2]:
         dA = sp.DeviceCSR.from_host(synth.CSR(A.rows, A.cols, rp4, A.col, A.val), "cuda")
         with pytest.raises(sp.SpgemmError) as ei:
-            sp.spgemm_plan(dA, dA)
+            plan(dA, dA)
         assert ei.value.name == "INVALID_CSR"
     # a valid matrix whose rows start below the previous row's last column passes
     ok = synth.CSR(3, 6, np.array([0, 2, 3, 5]), np.array([3, 5, 0, 1, 4], dtype=np.int32), np.ones(5))
-    sp.spgemm_plan_destroy(sp.spgemm_plan(sp.DeviceCSR.from_host(ok, "cuda"),
-                                          sp.DeviceCSR.from_host(synth.identity(6), "cuda")))
+    sp.spgemm_plan_destroy(plan(sp.DeviceCSR.from_host(ok, "cuda"),
+                                sp.DeviceCSR.from_host(synth.identity(6), "cuda")))
 
 
 def test_host_entry_matches_oracle():
