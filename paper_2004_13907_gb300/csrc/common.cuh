@@ -129,6 +129,19 @@ __device__ __forceinline__ bool f32c_within_bound(float res, float mag, int t) {
   return g * g * mag_ub <= u * fabsf(res) * (1.0f - 8.0f * u);
 }
 
+// The same bound when every partial product is non-negative (A's and B's values are): then
+// sum|p| equals the exact sum S, and |res - S| <= (u + gamma_t^2) S gives S <= |res| / (1 - u -
+// gamma_t^2), so the test gamma_t^2 S <= u |res| holds whenever gamma_t^2 <= u (1 - 8u) (1 - u -
+// gamma_t^2): a condition on the term count alone (t up to about 4,000).
+__device__ __forceinline__ bool f32c_within_count(int t) {
+  const float u = 5.9604644775390625e-8f;   // 2^-24
+  const float tu = static_cast<float>(t) * u;
+  if (tu >= 0.5f) return false;
+  const float g = tu / (1.0f - tu);
+  const float g2 = g * g * (1.0f + 8.0f * u);
+  return g2 <= u * (1.0f - 8.0f * u) * (1.0f - u - g2);
+}
+
 // Modes of the accumulating kernels: FP64 values summed with FP64 shared atomics; FP32 values
 // with compensated FP32 accumulation; FP32 values recomputed in FP64 and rounded once to FP32;
 // FP64 values summed exactly in integer fixed point (below).

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     void* __restrict__ cval_, int32_t* __restrict__ row_flag, const int32_t* __restrict__ abase,
     const int32_t* __restrict__ awidth, int64_t width_all, const uint32_t* __restrict__ wbits,
     const int64_t* __restrict__ woff, const uint16_t* __restrict__ bexp, const int32_t* __restrict__ dev_count,
-    uint32_t* err) {
+    const int32_t* __restrict__ negflag, uint32_t* err) {
   using G = WinGeom<Mode>;
   constexpr int kSmemBits = G::kSmemBits;
   constexpr int kSmemPre = G::kSmemPre;
@@ -176,6 +176,9 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     return (Mode == kModeF64 || Mode == kModeF64X) ? av64[q] : static_cast<double>(av32[q]);
   };
   const bool cnt_cached = nblocks <= kCntCache;
+  // kModeF32C: every partial product is non-negative (no value of A or B is negative), so the
+  // bound needs no sum of |p| (f32c_within_count)
+  const bool nonneg = Mode == kModeF32C && negflag != nullptr && *negflag == 0;
   if (dev_count) {   // the rows to redo are listed on the device
     const int64_t dc = *dev_count;
     count = dc < count ? dc : count;
@@ -257,6 +260,9 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     const int64_t width = awidth ? awidth[i] : width_all;
     const int64_t row_blocks = (width + kBlockCols - 1) / kBlockCols;   // counted by the symbolic pass
     const bool resident = na <= kNumThreads;
+    // kModeF32C with non-negative products: an entry has at most na terms, so when na itself
+    // passes the term-count bound no entry needs counting
+    const bool count_terms = !nonneg || !f32c_within_count(na < (int64_t(1) << 30) ? static_cast<int>(na) : (1 << 30));
     if (cnt_cached)
       for (int64_t b = threadIdx.x; b < row_blocks; b += kNumThreads) s_cnt[b] = gcnt[b];
     if (resident && threadIdx.x < na) {
@@ -542,8 +548,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
                   const float bp = nw - old;
                   const float q = (old - (nw - bp)) + (ph - bp);
                   atomicAdd(&f_c[r], q + pl);
-                  atomicAdd(&f_m[r], fabsf(ph));
-                  atomicAdd(&f_t[r], 1);
+                  if (!nonneg) atomicAdd(&f_m[r], fabsf(ph));
+                  if (count_terms) atomicAdd(&f_t[r], 1);
                 } else if constexpr (Mode == kModeF64X) {
                   uint32_t c0, c1, c2;
                   int32_t ct;
@@ -584,7 +590,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
           for (int r = threadIdx.x; r < ncnt; r += kNumThreads) {
             const float res = f_s[r] + f_c[r];
             if (out + r < out_end) static_cast<float*>(cval_)[out + r] = res;
-            missed |= !f32c_within_bound(res, f_m[r], f_t[r]);
+            missed |= nonneg ? count_terms && !f32c_within_count(f_t[r]) : !f32c_within_bound(res, f_m[r], f_t[r]);
             f_s[r] = 0.f; f_c[r] = 0.f; f_m[r] = 0.f; f_t[r] = 0;
           }
           if (missed) row_flag[i] = 1;
@@ -819,8 +825,8 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
                       int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag,
                       const int32_t* abase, const int32_t* awidth, int64_t width, const uint32_t* wbits,
-                      const int64_t* woff, const uint16_t* bexp, const int32_t* dev_count, int num_sms,
-                      uint32_t* err, cudaStream_t s) {
+                      const int64_t* woff, const uint16_t* bexp, const int32_t* dev_count,
+                      const int32_t* negflag, int num_sms, uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   auto go = [&](auto kernel, int smem, int per_sm) {
@@ -829,13 +835,39 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
     kernel<<<static_cast<unsigned>(g), kNumThreads, smem, s>>>(A, B, perm, count, counter, c_off, win_slot,
                                                                blockcnt, nblocks, nslots, split, merge_cap,
                                                                ccol, cval, row_flag, abase, awidth, width, wbits,
-                                                               woff, bexp, dev_count, err);
+                                                               woff, bexp, dev_count, negflag, err);
   };
   if (mode == kModeF32C) go(k_num_window<kModeF32C>, WinGeom<kModeF32C>::kSmemBytes, 2);
   else if (mode == kModeF32R) go(k_num_window<kModeF32R>, WinGeom<kModeF32R>::kSmemBytes, 2);
   else if (mode == kModeF64X) go(k_num_window<kModeF64X>, WinGeom<kModeF64X>::kSmemBytes, 2);
   else go(k_num_window<kModeF64>, WinGeom<kModeF64>::kSmemBytes, 2);
   return 1;
+}
+
+// flag = 1 if any of the n FP32 values is negative, infinite or NaN (the flag starts at 0).
+__global__ void __launch_bounds__(256) k_any_negative(const uint32_t* __restrict__ v, int64_t n,
+                                                      int32_t* __restrict__ flag) {
+  bool neg = false;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t x = v[i];
+    neg |= (x & 0x80000000u) != 0u || (x & 0x7fffffffu) >= 0x7f800000u;   // also infinities
+  }
+  if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+int launch_negative_check(const void* a, int64_t na, const void* b, int64_t nb, int32_t* flag, int num_sms,
+                          cudaStream_t s) {
+  cudaMemsetAsync(flag, 0, sizeof(int32_t), s);
+  int nl = 0;
+  for (int t = 0; t < 2; ++t) {
+    const int64_t n = t == 0 ? na : nb;
+    if (n <= 0) continue;
+    int64_t g = (n + 255) / 256;
+    if (g > int64_t(num_sms) * 8) g = int64_t(num_sms) * 8;
+    k_any_negative<<<static_cast<unsigned>(g), 256, 0, s>>>(static_cast<const uint32_t*>(t == 0 ? a : b), n, flag);
+    ++nl;
+  }
+  return nl;
 }
 
 // Largest biased exponent of the values of every row of B (0 for an empty row): a warp per row.

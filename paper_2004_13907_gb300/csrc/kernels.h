@@ -145,8 +145,11 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
                       int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag,
                       const int32_t* abase, const int32_t* awidth, int64_t width, const uint32_t* wbits,
-                      const int64_t* woff, const uint16_t* bexp, const int32_t* dev_count, int num_sms,
-                      uint32_t* err, cudaStream_t s);
+                      const int64_t* woff, const uint16_t* bexp, const int32_t* dev_count,
+                      const int32_t* negflag, int num_sms, uint32_t* err, cudaStream_t s);
+// *flag = 1 if a value of the FP32 arrays a[na] or b[nb] is negative, infinite or NaN, else 0.
+int launch_negative_check(const void* a, int64_t na, const void* b, int64_t nb, int32_t* flag, int num_sms,
+                          cudaStream_t s);
 // Largest biased exponent of the values of every row of B (FP64), for the exact accumulation mode
 int launch_brow_exponent(const DevCsr& B, uint16_t* bexp, int num_sms, cudaStream_t s);
 // F32-compensated rerun lists: the rows of perm[0, count) whose flag is set (all rows when

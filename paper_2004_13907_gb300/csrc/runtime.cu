@@ -447,6 +447,10 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
     stage_begin(p, SPGEMM_STAGE_NUM_WINDOW, s);
     nl = 0;
     if (fx && nwin > 0) nl += launch_brow_exponent(p->B, p->bexp, p->num_sms, s);
+    // FP32 compensated: whether every value of A and B is non-negative (then the windowed rows'
+    // error bound needs no sum of |p|), read by the window kernel on the device
+    if (f32c && nwin > 0) nl += launch_negative_check(p->A.val, p->A.nnz, p->B.val, p->B.nnz, p->counters + 8,
+                                                      p->num_sms, s);
     if (nwin > 0 && !p->split_tried) {
       // split table of B, once per plan, when it fits the budget (else the kernel searches)
       p->split_tried = true;
@@ -459,7 +463,7 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
     nl += launch_num_window(fx ? kModeF64X : mode, p->A, p->B, seg(kNumWin0), nwin, p->counters + 1, p->c_off,
                             p->win_slot, p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col,
                             C->val, p->rerun_flag, p->abase, p->awidth, p->width, p->wbits, p->woff, p->bexp,
-                            nullptr, p->num_sms, err, s);
+                            nullptr, f32c ? p->counters + 8 : nullptr, p->num_sms, err, s);
     if (fx && nwin > 0) {
       // rows outside the fixed-point range (a very wide spread of product magnitudes, subnormal or
       // non-finite values) are redone with FP64 shared atomics; the list stays on the device
@@ -467,7 +471,7 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       nl += launch_num_window(kModeF64, p->A, p->B, p->rerun_list, nwin, p->counters + 7, p->c_off, p->win_slot,
                               p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
                               nullptr, p->abase, p->awidth, p->width, p->wbits, p->woff, nullptr, p->counters + 6,
-                              p->num_sms, err, s);
+                              nullptr, p->num_sms, err, s);
       p->fx_rerun_pending = true;
     }
     stage_end(p, SPGEMM_STAGE_NUM_WINDOW, nl, s);

@@ -181,3 +181,19 @@ def test_rmat_2e17_f32c_full():
 
     compare_all_rows(A, A, C, check)
     sp.spgemm_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("t,sign,rerun", [(1000, 1.0, 0), (5000, 1.0, 1), (1000, -1.0, 0)])
+def test_term_count_bound_of_nonnegative_products(t, sign, rerun):
+    """With no negative value in A or B every partial product is non-negative, so the bound of an
+    entry depends on its term count alone (about 4,000 terms at most); a value of either sign
+    sends the kernel back to the bound with sum|p|. C = [[sum of t products]]."""
+    import paper_2004_13907_gb300 as sp
+    a = np.ones((1, t), dtype=np.float32)
+    a[0, 7] = sign
+    A = synth.from_dense(a).astype(np.float32)
+    B = synth.from_dense(np.ones((t, 1), dtype=np.float32)).astype(np.float32)
+    rp, col, val, _, info, _ = run_gpu(A, B, prec="f32c")
+    assert info["f32c_rerun_rows"] == rerun
+    assert val.tolist() == [float(t - 1 + sign)]
+    _check(A, B, rp, col, val)
