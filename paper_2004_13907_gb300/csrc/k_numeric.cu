@@ -182,22 +182,75 @@ __global__ void __launch_bounds__(256) k_num_micro(DevCsr A, DevCsr B, const int
   }
 }
 
-// Accumulate v into the slot of `key` (linear probing; keys are columns, kEmpty = free).
+// Value q of an FP64 (kModeF64) or FP32 (kModeF32C) array, as a double (exact).
+template <int Mode>
+__device__ __forceinline__ double value_at(const void* v, int64_t q) {
+  if constexpr (Mode == kModeF32C) return static_cast<double>(static_cast<const float*>(v)[q]);
+  else return static_cast<const double*>(v)[q];
+}
+
+// The slot of `key` (linear probing; keys are columns, kEmpty = free), claimed if new; -1 when
+// the table is full.
 template <int LOG2S>
-__device__ __forceinline__ void hash_accumulate(int32_t* keys, double* vals, int32_t key, double v,
-                                                uint32_t* err) {
+__device__ __forceinline__ int hash_claim(int32_t* keys, int32_t key) {
   constexpr int S = 1 << LOG2S;
   uint32_t h = hash_slot(key, LOG2S);
   for (int probe = 0; probe < S; ++probe) {
     const int32_t cur = *reinterpret_cast<volatile int32_t*>(&keys[h]);
-    if (cur == key) { atomicAdd(&vals[h], v); return; }
+    if (cur == key) return static_cast<int>(h);
     if (cur == kEmpty) {
       const int32_t old = atomicCAS(&keys[h], kEmpty, key);
-      if (old == kEmpty || old == key) { atomicAdd(&vals[h], v); return; }
+      if (old == kEmpty || old == key) return static_cast<int>(h);
     }
     h = (h + 1) & (S - 1);
   }
-  set_error(err, kErrHashFull);
+  return -1;
+}
+
+// Adds the partial product a*b into the slot of `key`. kModeF64: one FP64 atomic. kModeF32C: the
+// slot's 8 bytes hold an FP32 sum and its compensation; the error-free product a*b = ph + pl and
+// the sum's own rounding error (TwoSum, rebuilt from the value the atomic returns) go to the
+// compensation, as in the windowed kernel (Dot2 accumulated concurrently).
+template <int LOG2S, int Mode>
+__device__ __forceinline__ void hash_accumulate(int32_t* keys, double* vals, int32_t key, double a, double b,
+                                                uint32_t* err) {
+  const int h = hash_claim<LOG2S>(keys, key);
+  if (h < 0) {
+    set_error(err, kErrHashFull);
+    return;
+  }
+  if constexpr (Mode == kModeF32C) {
+    float* sc = reinterpret_cast<float*>(&vals[h]);
+    const float fa = static_cast<float>(a), fb = static_cast<float>(b);
+    const float ph = fa * fb;
+    const float pl = fmaf(fa, fb, -ph);
+    const float old = atomicAdd(&sc[0], ph);
+    const float nw = old + ph;
+    const float bp = nw - old;
+    const float q = (old - (nw - bp)) + (ph - bp);
+    atomicAdd(&sc[1], q + pl);
+  } else {
+    atomicAdd(&vals[h], a * b);
+  }
+}
+
+// Value of an entry of C from its slot's 8 bytes (an FP64 sum, or an FP32 sum and compensation).
+template <int Mode>
+__device__ __forceinline__ void store_value(void* cval, int64_t at, double slot) {
+  if constexpr (Mode == kModeF32C) {
+    const float2 sc = *reinterpret_cast<const float2*>(&slot);
+    static_cast<float*>(cval)[at] = sc.x + sc.y;
+  } else {
+    static_cast<double*>(cval)[at] = slot;
+  }
+}
+
+// kModeF32C rows of the hash kernels: every partial product must be non-negative (no negative value
+// in A or B, *negflag == 0) and the row's A length must pass the term-count bound, so that no
+// entry can exceed Dot2's bound; otherwise the row is listed for the FP64 recomputation.
+__device__ __forceinline__ bool f32c_hash_row_ok(const int32_t* negflag, int64_t na) {
+  return negflag != nullptr && *negflag == 0 &&
+         f32c_within_count(na < (int64_t(1) << 30) ? static_cast<int>(na) : (1 << 30));
 }
 
 // In-warp bitonic sort of keys/vals[0, N), N a power of two.
@@ -243,28 +296,29 @@ __device__ __forceinline__ int pow2_ceil(int x) {
   return x <= 1 ? 1 : 1 << (32 - __clz(x - 1));
 }
 
-template <int LOG2S>
+template <int LOG2S, int Mode>
 __global__ void __launch_bounds__(256) k_num_warp(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
                                                   int64_t count, const int64_t* __restrict__ c_off,
-                                                  int32_t* __restrict__ ccol, double* __restrict__ cval,
-                                                  const int32_t* __restrict__ abase, uint32_t* err) {
+                                                  int32_t* __restrict__ ccol, void* __restrict__ cval,
+                                                  const int32_t* __restrict__ abase, int32_t* __restrict__ row_flag,
+                                                  const int32_t* __restrict__ negflag, uint32_t* err) {
   constexpr int S = 1 << LOG2S;
   extern __shared__ double smem_f64[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double* vals = smem_f64 + wid * S;
   int32_t* keys = reinterpret_cast<int32_t*>(smem_f64 + 8 * S) + wid * S;
-  const double* av_ = static_cast<const double*>(A.val);
-  const double* bv_ = static_cast<const double*>(B.val);
   const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t r = gw; r < count; r += nw) {
     const int32_t i = perm[r];
     const int64_t a0 = A.rp[i];
     const int64_t na = A.rp[i + 1] - a0;
+    if (Mode == kModeF32C && lane == 0 && !f32c_hash_row_ok(negflag, na)) row_flag[i] = 1;
     for (int s = lane; s < S; s += 32) { keys[s] = kEmpty; vals[s] = 0.0; }
     __syncwarp();
     warp_for_each_product(A, B, a0, na, [&](int64_t j, int64_t e) {
-      hash_accumulate<LOG2S>(keys, vals, B.col[j], av_[a0 + e] * bv_[j], err);
+      hash_accumulate<LOG2S, Mode>(keys, vals, B.col[j], value_at<Mode>(A.val, a0 + e), value_at<Mode>(B.val, j),
+                                   err);
     });
     __syncwarp();
     // compact in place (a write position never passes the slot being read)
@@ -291,17 +345,18 @@ __global__ void __launch_bounds__(256) k_num_warp(DevCsr A, DevCsr B, const int3
     const int32_t cb = abase ? abase[i] : 0;
     for (int t = lane; t < nw_out; t += 32) {
       ccol[off + t] = keys[t] - cb;
-      cval[off + t] = vals[t];
+      store_value<Mode>(cval, off + t, vals[t]);
     }
     __syncwarp();
   }
 }
 
-template <int LOG2S, int NT>
+template <int LOG2S, int NT, int Mode>
 __global__ void __launch_bounds__(NT) k_num_block(DevCsr A, DevCsr B, const int32_t* __restrict__ perm,
                                                   int64_t count, const int64_t* __restrict__ c_off,
-                                                  int32_t* __restrict__ ccol, double* __restrict__ cval,
-                                                  const int32_t* __restrict__ abase, uint32_t* err) {
+                                                  int32_t* __restrict__ ccol, void* __restrict__ cval,
+                                                  const int32_t* __restrict__ abase, int32_t* __restrict__ row_flag,
+                                                  const int32_t* __restrict__ negflag, uint32_t* err) {
   constexpr int S = 1 << LOG2S;
   extern __shared__ double smem_f64[];
   double* vals = smem_f64;
@@ -309,16 +364,16 @@ __global__ void __launch_bounds__(NT) k_num_block(DevCsr A, DevCsr B, const int3
   __shared__ int32_t s_excl[NT];
   __shared__ int64_t s_bs[NT];
   __shared__ int32_t s_scan[33];
-  const double* av_ = static_cast<const double*>(A.val);
-  const double* bv_ = static_cast<const double*>(B.val);
   for (int64_t r = blockIdx.x; r < count; r += gridDim.x) {
     const int32_t i = perm[r];
     const int64_t a0 = A.rp[i];
     const int64_t na = A.rp[i + 1] - a0;
+    if (Mode == kModeF32C && threadIdx.x == 0 && !f32c_hash_row_ok(negflag, na)) row_flag[i] = 1;
     for (int s = threadIdx.x; s < S; s += NT) { keys[s] = kEmpty; vals[s] = 0.0; }
     __syncthreads();
     block_for_each_product<NT>(A, B, a0, na, s_excl, s_bs, s_scan, [&](int64_t j, int64_t e) {
-      hash_accumulate<LOG2S>(keys, vals, B.col[j], av_[a0 + e] * bv_[j], err);
+      hash_accumulate<LOG2S, Mode>(keys, vals, B.col[j], value_at<Mode>(A.val, a0 + e), value_at<Mode>(B.val, j),
+                                   err);
     });
     // compact in place, one block-wide chunk at a time
     int cnt = 0;
@@ -343,7 +398,7 @@ __global__ void __launch_bounds__(NT) k_num_block(DevCsr A, DevCsr B, const int3
     const int32_t cb = abase ? abase[i] : 0;
     for (int t = threadIdx.x; t < nb_out; t += NT) {
       ccol[off + t] = keys[t] - cb;
-      cval[off + t] = vals[t];
+      store_value<Mode>(cval, off + t, vals[t]);
     }
     __syncthreads();
   }
@@ -377,36 +432,41 @@ int launch_num_micro(const DevCsr& A, const DevCsr& B, const int32_t* perm, int6
   return 1;
 }
 
-int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
-                     int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
-                     const int32_t* abase, uint32_t* err, int num_sms, cudaStream_t s) {
+int launch_num_warp(int log2S, int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                    const int64_t* c_off, int32_t* ccol, void* cval, const int32_t* abase, int32_t* row_flag,
+                    const int32_t* negflag, uint32_t* err, int num_sms, cudaStream_t s) {
   if (count <= 0) return 0;
   const unsigned g = grid_rows(count, 8, num_sms * 32);
   const size_t sm = size_t(8) * (size_t(1) << log2S) * 12;
+  auto go = [&](auto kernel) {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    kernel<<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, abase, row_flag, negflag, err);
+  };
+  const bool f32c = mode == kModeF32C;
   switch (log2S) {
-    case 6: k_num_warp<6><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, abase, err); break;
-    case 8: k_num_warp<8><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, abase, err); break;
-    case 10:
-      cudaFuncSetAttribute(k_num_warp<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-      k_num_warp<10><<<g, 256, sm, s>>>(A, B, perm, count, c_off, ccol, cval, abase, err);
-      break;
+    case 6: f32c ? go(k_num_warp<6, kModeF32C>) : go(k_num_warp<6, kModeF64>); break;
+    case 8: f32c ? go(k_num_warp<8, kModeF32C>) : go(k_num_warp<8, kModeF64>); break;
+    case 10: f32c ? go(k_num_warp<10, kModeF32C>) : go(k_num_warp<10, kModeF64>); break;
     default: break;
   }
   return 1;
 }
 
-int launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
-                      int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
-                      const int32_t* abase, uint32_t* err, int num_sms, cudaStream_t s) {
+int launch_num_block(int log2S, int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                     const int64_t* c_off, int32_t* ccol, void* cval, const int32_t* abase, int32_t* row_flag,
+                     const int32_t* negflag, uint32_t* err, int num_sms, cudaStream_t s) {
   if (count <= 0) return 0;
   const size_t sm = (size_t(1) << log2S) * 12;
+  const bool f32c = mode == kModeF32C;
+  auto go = [&](auto kernel, int nt, int per_sm) {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    kernel<<<grid_rows(count, 1, num_sms * per_sm), nt, sm, s>>>(A, B, perm, count, c_off, ccol, cval, abase, row_flag,
+                                                                 negflag, err);
+  };
   if (log2S == 11) {
-    k_num_block<11, 256><<<grid_rows(count, 1, num_sms * 8), 256, sm, s>>>(A, B, perm, count, c_off, ccol,
-                                                                       cval, abase, err);
+    f32c ? go(k_num_block<11, 256, kModeF32C>, 256, 8) : go(k_num_block<11, 256, kModeF64>, 256, 8);
   } else if (log2S == 13) {
-    cudaFuncSetAttribute(k_num_block<13, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_num_block<13, 512><<<grid_rows(count, 1, num_sms * 4), 512, sm, s>>>(A, B, perm, count, c_off, ccol,
-                                                                       cval, abase, err);
+    f32c ? go(k_num_block<13, 512, kModeF32C>, 512, 4) : go(k_num_block<13, 512, kModeF64>, 512, 4);
   }
   return 1;
 }

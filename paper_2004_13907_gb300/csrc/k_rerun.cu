@@ -1,4 +1,5 @@
-// FP64 recomputation of the windowed FP32 rows whose compensated sums exceeded their bound.
+// FP64 recomputation of the FP32 rows (windowed, block or warp hash rows) whose compensated sums
+// may exceed their bound.
 //
 // These rows are few and long (R-MAT 2^20: 21 rows, the heaviest of the matrix), so instead of
 // one block per row the whole GPU works on a group of them at once: every partial product

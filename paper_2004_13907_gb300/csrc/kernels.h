@@ -116,12 +116,14 @@ int launch_num_tiny(int mode, const DevCsr& A, const DevCsr& B, const int32_t* p
 int launch_num_micro(const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                      const int64_t* c_off, int32_t* ccol, double* cval, const int32_t* abase, uint32_t* err,
                      int num_sms, cudaStream_t s);
-int launch_num_warp(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
-                     int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
-                     const int32_t* abase, uint32_t* err, int num_sms, cudaStream_t s);
-int launch_num_block(int log2S, const DevCsr& A, const DevCsr& B, const int32_t* perm,
-                      int64_t count, const int64_t* c_off, int32_t* ccol, double* cval,
-                      const int32_t* abase, uint32_t* err, int num_sms, cudaStream_t s);
+// Warp and block hash kernels, kModeF64 or kModeF32C (row_flag lists kModeF32C rows for the FP64
+// recomputation; negflag is the device flag of launch_negative_check).
+int launch_num_warp(int log2S, int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                    const int64_t* c_off, int32_t* ccol, void* cval, const int32_t* abase, int32_t* row_flag,
+                    const int32_t* negflag, uint32_t* err, int num_sms, cudaStream_t s);
+int launch_num_block(int log2S, int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
+                     const int64_t* c_off, int32_t* ccol, void* cval, const int32_t* abase, int32_t* row_flag,
+                     const int32_t* negflag, uint32_t* err, int num_sms, cudaStream_t s);
 
 // ---- windowed numeric pass and the column-block split table of B (k_window.cu)
 // Columns of C for the windowed rows with a stored bitmap (k_window.cu); rows without one get

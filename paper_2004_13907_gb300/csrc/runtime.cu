@@ -206,6 +206,17 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   if (st) return st;
   cudaMemsetAsync(p->summary, 0, sizeof(Summary), s);
   cudaMemsetAsync(p->c_off, 0, sizeof(int64_t), s);
+  if (p->prec == SPGEMM_F32_COMPENSATED && m > 0) {
+    // FP32 compensated: the short rows take the block and warp hash kernels when no value of A or
+    // B is negative (their bound then needs only the row length); otherwise every non-tiny row
+    // takes the windowed kernel, which keeps the full bound
+    launch_negative_check(p->A.val, A->nnz, p->B.val, B->nnz, p->counters + 8, p->num_sms, s);
+    int32_t neg = 1;
+    cudaError_t e = cudaMemcpyAsync(&neg, p->counters + 8, sizeof(neg), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "reading the sign check of the FP32 values");
+    p->cp.window_all = neg ? 1 : 0;
+  }
 
   Summary h;
   if (o.validate) {
@@ -377,7 +388,8 @@ int64_t numeric_extra_bytes(const spgemm_plan_s* p) {
   const int64_t nwin = p->num_off[kNumWin3 + 1] - p->num_off[kNumWin0];
   if (p->prec == SPGEMM_F32_COMPENSATED && !p->rerun_flag) {
     extra += 2 * ws_rounded(4 * m);
-    if (nwin > 0) extra += ws_rounded(8 * rerun_group_rows(p->width, kRerunScratchBytes) * p->width);
+    const int64_t nwh = p->num_off[kNumWarp1 + 1] - p->num_off[kNumWin0];
+    if (nwh > 0) extra += ws_rounded(8 * rerun_group_rows(p->width, kRerunScratchBytes) * p->width);
   }
   if (p->prec == SPGEMM_F64 && p->opts.fp64_accumulate != 0 && nwin > 0) {
     if (!p->rerun_flag) extra += 2 * ws_rounded(4 * m);   // flags and list of FP64 reruns
@@ -419,14 +431,13 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
     uint32_t* err = &p->summary->err;
     const int64_t nwin = p->num_off[kNumWin3 + 1] - p->num_off[kNumWin0];
     const int64_t nslots = p->sym_off[kSymWin3 + 1] - p->sym_off[kSymWin0];
+    // windowed, block and warp rows (consecutive classes): the FP32 rows the dense FP64 rerun takes
+    const int64_t nwh = p->num_off[kNumWarp1 + 1] - p->num_off[kNumWin0];
     if (f32c) {
-      for (int c = kNumBlock2; c <= kNumWarp1; ++c)
-        if (cnt(c)) return set_error_msg(SPGEMM_ERR_INTERNAL, "FP32-compensated rows outside the windowed path");
-      if (cnt(kNumMicro)) return set_error_msg(SPGEMM_ERR_INTERNAL, "FP32-compensated rows in the FP64 micro path");
       if (!p->rerun_flag) {
         p->rerun_flag = ws_get<int32_t>(p, m, &st);
         p->rerun_list = ws_get<int32_t>(p, m, &st);
-        if (nwin > 0) {
+        if (nwh > 0) {
           p->rerun_group = rerun_group_rows(p->width, kRerunScratchBytes);
           p->rerun_dense = ws_get<double>(p, p->rerun_group * p->width, &st);
         }
@@ -449,8 +460,8 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
     if (fx && nwin > 0) nl += launch_brow_exponent(p->B, p->bexp, p->num_sms, s);
     // FP32 compensated: whether every value of A and B is non-negative (then the windowed rows'
     // error bound needs no sum of |p|), read by the window kernel on the device
-    if (f32c && nwin > 0) nl += launch_negative_check(p->A.val, p->A.nnz, p->B.val, p->B.nnz, p->counters + 8,
-                                                      p->num_sms, s);
+    if (f32c && nwh > 0) nl += launch_negative_check(p->A.val, p->A.nnz, p->B.val, p->B.nnz, p->counters + 8,
+                                                     p->num_sms, s);
     if (nwin > 0 && !p->split_tried) {
       // split table of B, once per plan, when it fits the budget (else the kernel searches)
       p->split_tried = true;
@@ -479,21 +490,22 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
     nl = launch_expand_cols(seg(kNumWin0), nwin, p->win_slot, p->woff, p->wbits, p->blockcnt, p->nblocks, p->c_off,
                             p->awidth, p->width, C->col, p->num_sms, err, s);
     stage_end(p, SPGEMM_STAGE_NUM_EXPAND, nl, s);
-    if (!f32c) {
-      double* cval = static_cast<double*>(C->val);
+    {
+      int32_t* flag = f32c ? p->rerun_flag : nullptr;
+      const int32_t* neg = f32c ? p->counters + 8 : nullptr;
       stage_begin(p, SPGEMM_STAGE_NUM_BLOCK, s);
-      nl = launch_num_block(13, p->A, p->B, seg(kNumBlock2), cnt(kNumBlock2), p->c_off, C->col, cval, p->abase,
-                            err, p->num_sms, s);
-      nl += launch_num_block(11, p->A, p->B, seg(kNumBlock1), cnt(kNumBlock1), p->c_off, C->col, cval, p->abase,
-                             err, p->num_sms, s);
+      nl = launch_num_block(13, mode, p->A, p->B, seg(kNumBlock2), cnt(kNumBlock2), p->c_off, C->col, C->val,
+                            p->abase, flag, neg, err, p->num_sms, s);
+      nl += launch_num_block(11, mode, p->A, p->B, seg(kNumBlock1), cnt(kNumBlock1), p->c_off, C->col, C->val,
+                             p->abase, flag, neg, err, p->num_sms, s);
       stage_end(p, SPGEMM_STAGE_NUM_BLOCK, nl, s);
       stage_begin(p, SPGEMM_STAGE_NUM_WARP, s);
-      nl = launch_num_warp(10, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, cval, p->abase, err,
-                           p->num_sms, s);
-      nl += launch_num_warp(8, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, cval, p->abase, err,
-                            p->num_sms, s);
-      nl += launch_num_warp(6, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, cval, p->abase, err,
-                            p->num_sms, s);
+      nl = launch_num_warp(10, mode, p->A, p->B, seg(kNumWarp3), cnt(kNumWarp3), p->c_off, C->col, C->val, p->abase,
+                           flag, neg, err, p->num_sms, s);
+      nl += launch_num_warp(8, mode, p->A, p->B, seg(kNumWarp2), cnt(kNumWarp2), p->c_off, C->col, C->val, p->abase,
+                            flag, neg, err, p->num_sms, s);
+      nl += launch_num_warp(6, mode, p->A, p->B, seg(kNumWarp1), cnt(kNumWarp1), p->c_off, C->col, C->val, p->abase,
+                            flag, neg, err, p->num_sms, s);
       stage_end(p, SPGEMM_STAGE_NUM_WARP, nl, s);
     }
     stage_begin(p, SPGEMM_STAGE_NUM_TINY, s);
@@ -508,10 +520,10 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       // rows with an entry over the compensated bound are recomputed in FP64 and rounded once
       stage_begin(p, SPGEMM_STAGE_NUM_RERUN, s);
       int32_t* list_w = p->rerun_list;
-      int32_t* list_t = p->rerun_list + nwin;
+      int32_t* list_t = p->rerun_list + nwh;
       cudaMemsetAsync(p->counters + 4, 0, 2 * sizeof(int32_t), s);
       const int all = p->opts.f32c_rerun_all ? 1 : 0;
-      nl = launch_collect_flagged(seg(kNumWin0), nwin, p->rerun_flag, all, list_w, p->counters + 4, s);
+      nl = launch_collect_flagged(seg(kNumWin0), nwh, p->rerun_flag, all, list_w, p->counters + 4, s);
       nl += launch_collect_flagged(seg(kNumTiny), cnt(kNumTiny), p->rerun_flag, all, list_t, p->counters + 5, s);
       int32_t hc[2] = {0, 0};
       cudaError_t e = cudaMemcpyAsync(hc, p->counters + 4, sizeof(hc), cudaMemcpyDeviceToHost, s);

@@ -197,3 +197,34 @@ def test_term_count_bound_of_nonnegative_products(t, sign, rerun):
     assert info["f32c_rerun_rows"] == rerun
     assert val.tolist() == [float(t - 1 + sign)]
     _check(A, B, rp, col, val)
+
+
+def test_sign_change_after_the_plan_reruns_hash_rows():
+    """A plan made on non-negative values sends the short FP32 rows to the hash kernels, whose bound
+    needs non-negative products. When a value turns negative before a later numeric pass, those
+    rows are recomputed in FP64 and every entry still meets the final bound."""
+    import paper_2004_13907_gb300 as sp
+    A = _f32(synth.rmat(13, 16, seed=43))
+    dA = sp.DeviceCSR.from_host(A, "cuda", dtype=torch.float32)
+    plan = sp.spgemm_plan(dA, dA, "f32c")
+    sp.spgemm_symbolic(plan)
+    C = sp.alloc_output(plan)
+    sp.spgemm_numeric(plan, C)
+    sp.spgemm_plan_check(plan)
+    info = sp.spgemm_plan_get_info(plan)
+    cls = dict(zip(sp._native.NUM_CLASSES, info["num_class_rows"]))
+    assert cls["block2048"] + cls["warp1024"] + cls["warp256"] > 0
+    H = C.to_host()
+    _check(A, A, H.row_ptr.numpy().astype(np.int64), H.col.numpy(), H.val.numpy())
+    val = A.val.copy()
+    val[::97] *= -1.0
+    dA.val.copy_(torch.from_numpy(val))
+    sp.spgemm_numeric(plan, C)
+    sp.spgemm_plan_check(plan)
+    reruns = sp.spgemm_plan_get_info(plan)["f32c_rerun_rows"]
+    torch.cuda.synchronize()
+    sp.spgemm_plan_destroy(plan)
+    assert reruns >= cls["block8192"] + cls["block2048"] + cls["warp1024"] + cls["warp256"] + cls["warp64"]
+    A2 = synth.CSR(A.rows, A.cols, A.row_ptr, A.col, val)
+    H = C.to_host()
+    _check(A2, A2, H.row_ptr.numpy().astype(np.int64), H.col.numpy(), H.val.numpy())
