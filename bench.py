@@ -845,7 +845,17 @@ def _pinned(n: int, dtype, torch, registered: list):
     """Page-locked host array of exactly n elements (numpy memory registered with CUDA); the
     registered pointers are appended to `registered`, to be unregistered before the memory is
     freed (a stale registration over reused host memory breaks later copies)."""
-    a = np.empty(max(n, 1), dtype=dtype)
+    import mmap
+    nbytes = max(n, 1) * np.dtype(dtype).itemsize
+    try:
+        # anonymous memory advised for transparent huge pages: after other work has fragmented
+        # the host's memory, 4 KB pages slowed the copy of C to the host several times over
+        buf = mmap.mmap(-1, nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+        if hasattr(mmap, "MADV_HUGEPAGE"):
+            buf.madvise(mmap.MADV_HUGEPAGE)
+        a = np.frombuffer(buf, dtype=dtype, count=max(n, 1))
+    except (OSError, ValueError, AttributeError):
+        a = np.empty(max(n, 1), dtype=dtype)
     t = torch.from_numpy(a)
     rc = torch.cuda.cudart().cudaHostRegister(t.data_ptr(), t.numel() * t.element_size(), 0)
     if int(rc) == 0:

@@ -207,11 +207,13 @@ void spgemm_opts_default(spgemm_opts* opts);
  * Blocks `stream` once to read back the class sizes and sum_i P_i.
  * Small products take a path of their own: F64, 1 <= A.rows <= 65,536, B.cols <= 32,768, the
  * default class options (tiny_max 32, warp_max 1024, block_max 2048, window_hash_fill 4096,
- * force_window 0, fp64_accumulate 0) and general_path 0. There the plan does not block: one
- * warp per row of A counts and then computes its row over a bitmap of all columns of C, and
- * INVALID_CSR in A, sum_i P_i and the class counters (every row in the 1024-slot warp class)
- * come with spgemm_symbolic, which reads them back in its one host read. A row of C over
- * 1,024 entries sends spgemm_symbolic back through the general plan (one more host read).
+ * force_window 0, fp64_accumulate 0) and general_path 0. There the plan does not block and
+ * already launches the symbolic kernel on `stream` (one warp per row of A counts its row over a
+ * bitmap of all columns of C; the numeric kernel later computes it the same way); INVALID_CSR in
+ * A or B, sum_i P_i and the class counters (every row in the 1024-slot warp class) come with
+ * spgemm_symbolic, which reads them back in its one host read (waiting for the plan's stream).
+ * A row of C over 1,024 entries sends spgemm_symbolic back through the general plan (one more
+ * host read).
  * Errors: INVALID_ARG (NULL pointers, A.cols != B.rows, negative sizes, prec mismatch),
  * INVALID_CSR, OOM, CUDA, UNSUPPORTED (sizes beyond int32 column indices). */
 spgemm_status spgemm_plan(const spgemm_csr_in* A, const spgemm_csr_in* B, spgemm_prec prec,

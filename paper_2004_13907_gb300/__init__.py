@@ -36,6 +36,8 @@ def lib() -> ctypes.CDLL:
 
 
 def _prec(p) -> int:
+    if p is F64 or p is F32_COMPENSATED:
+        return p
     if p in (F64, "f64", "fp64", torch.float64):
         return F64
     if p in (F32_COMPENSATED, "f32c", "fp32c", "f32", torch.float32):

@@ -166,6 +166,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     """Loads libspgemm.so (built in-tree by ``build.py``). There is no fallback: without
     the library no product can be computed, and this raises."""
     global _lib
+    if _lib is not None and path is None:   # loaded already (no lock on this path)
+        return _lib
     with _lock:
         if _lib is not None and path is None:
             return _lib

@@ -141,6 +141,12 @@ spgemm_status plan_small(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_
   cudaMemsetAsync(p->summary, 0, sizeof(Summary), s);
   stage_end(p, SPGEMM_STAGE_VALIDATE, 0, s);
   if ((st = cuda_status(cudaGetLastError(), "clearing the plan summary")) != SPGEMM_OK) return st;
+  // the symbolic kernel starts now, on the plan's stream: spgemm_symbolic only reads its summary
+  stage_begin(p, SPGEMM_STAGE_SYM_WARP, s);
+  const int nl = launch_small_symbolic(small_csr(p->a_in), small_csr(p->b_in), p->small_grid, p->opts.validate,
+                                       p->nnz_row, p->small_loc, p->small_blk, p->summary, s);
+  stage_end(p, SPGEMM_STAGE_SYM_WARP, nl, s);
+  if ((st = cuda_status(cudaGetLastError(), "launching the small-product symbolic pass")) != SPGEMM_OK) return st;
   p->state = 0;
   return SPGEMM_OK;
 }
@@ -278,13 +284,10 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
   spgemm_status st;
   const int64_t m = p->A.rows;
   if (p->small) {
-    stage_begin(p, SPGEMM_STAGE_SYM_WARP, s);
-    const int nl = launch_small_symbolic(small_csr(p->a_in), small_csr(p->b_in), p->small_grid, p->opts.validate,
-                                         p->nnz_row, p->small_loc, p->small_blk, p->summary, s);
-    stage_end(p, SPGEMM_STAGE_SYM_WARP, nl, s);
-    if ((st = cuda_status(cudaGetLastError(), "launching the small-product symbolic pass")) != SPGEMM_OK) return st;
+    // the plan launched the symbolic kernel on its own stream; read its summary there (the host
+    // wait orders every later stream after it)
     Summary h;
-    if ((st = read_summary(p, &h, s)) != SPGEMM_OK) return st;
+    if ((st = read_summary(p, &h, static_cast<cudaStream_t>(p->ws.stream))) != SPGEMM_OK) return st;
     if (h.err) return error_bits_status(h.err);
     if (h.small_flags) {
       // a row of C is too long for the small path: plan and count again through the row classes
