@@ -321,8 +321,8 @@ __device__ __forceinline__ void write_row(uint32_t* bm, const uint16_t* pre, con
 // enumerates their partial products as one flat list, 32 entries of A at a time, so the memory
 // round trips of the group's rows overlap.
 template <int PER>
-__global__ void __launch_bounds__(kSymWarps * 32) k_small_sym(SmallCsr A, SmallCsr B, int check, int64_t run, int G,
-                                                              int32_t* __restrict__ nnz_row,
+__global__ void __launch_bounds__(kSymWarps * 32) k_small_sym(SmallCsr A, SmallCsr B, int32_t width, int check,
+                                                              int64_t run, int G, int32_t* __restrict__ nnz_row,
                                                               int32_t* __restrict__ loc,
                                                               int64_t* __restrict__ blk, Summary* sum) {
   extern __shared__ __align__(16) unsigned char small_smem[];
@@ -343,6 +343,8 @@ __global__ void __launch_bounds__(kSymWarps * 32) k_small_sym(SmallCsr A, SmallC
   for (int64_t gs = r0 + wid * G; gs < r1; gs += int64_t(kSymWarps) * G) {
     const int ng = r1 - gs < G ? static_cast<int>(r1 - gs) : G;
     const RowGroup gr = group_rows(A, gs, ng, chk, bad);
+    // lane g < ng: the first column of row gs + g's column space (a stacked batch's job)
+    const int32_t cb_lane = A.cbase && lane < ng ? A.cbase[gs + lane] : 0;
     for (int32_t c0 = 0; c0 < gr.E; c0 += 32) {
       int g;
       int64_t bs;
@@ -357,10 +359,13 @@ __global__ void __launch_bounds__(kSymWarps * 32) k_small_sym(SmallCsr A, SmallC
         for (int u = 0; u < kSlots; ++u) {
           c[u] = ok[u] ? B.col[j[u]] : -1;
           go[u] = __shfl_sync(kFull, g, own[u]);
+          const int32_t cb = __shfl_sync(kFull, cb_lane, go[u]);
+          c[u] = c[u] >= 0 ? c[u] - cb : -1;
         }
 #pragma unroll
         for (int u = 0; u < kSlots; ++u)
-          if (c[u] >= 0 && c[u] < B.cols) atomicOr(&bm0[go[u] * 32 * PER + (c[u] >> 5)], 1u << (c[u] & 31));
+          if (c[u] >= 0 && c[u] < width) atomicOr(&bm0[go[u] * 32 * PER + (c[u] >> 5)], 1u << (c[u] & 31));
+          else if (ok[u] && chk) bad = true;   // a column outside its row's column space
       });
     }
     __syncwarp();
@@ -452,7 +457,8 @@ __device__ __forceinline__ void a_entry(const SmallCsr& A, const SmallCsr& B, in
 // products keeps the loads of its marking step in registers for the accumulation; longer rows
 // enumerate their products twice.
 template <int PER>
-__global__ void __launch_bounds__(kNumWarpsB * 32) k_small_num(SmallCsr A, SmallCsr B, int cap, int64_t run,
+__global__ void __launch_bounds__(kNumWarpsB * 32) k_small_num(SmallCsr A, SmallCsr B, int32_t width, int cap,
+                                                               int64_t run,
                                                                const int32_t* __restrict__ nnz_row,
                                                                const int32_t* __restrict__ loc,
                                                                const int64_t* __restrict__ blk, int64_t nblk,
@@ -486,6 +492,7 @@ __global__ void __launch_bounds__(kNumWarpsB * 32) k_small_num(SmallCsr A, Small
         else static_cast<int32_t*>(crp)[m] = static_cast<int32_t>(total);
       }
     }
+    const int32_t cb = A.cbase ? A.cbase[i] : 0;   // the row's column space (a stacked batch's job)
     int64_t bs;
     int32_t blen;
     double a;
@@ -503,23 +510,23 @@ __global__ void __launch_bounds__(kNumWarpsB * 32) k_small_num(SmallCsr A, Small
       for_slots(blen, bs, a, [&](const bool* ok, const int64_t* j, const int32_t*, const double* av, const int*) {
 #pragma unroll
         for (int u = 0; u < kSlots; ++u) {
-          fc[u] = ok[u] ? B.col[j[u]] : -1;
+          fc[u] = ok[u] ? B.col[j[u]] - cb : -1;
           fv[u] = ok[u] ? av[u] * bv[j[u]] : 0.0;
         }
       });
 #pragma unroll
       for (int u = 0; u < kSlots; ++u)
-        if (fc[u] >= 0 && fc[u] < B.cols) atomicOr(&bm[fc[u] >> 5], 1u << (fc[u] & 31));
+        if (fc[u] >= 0 && fc[u] < width) atomicOr(&bm[fc[u] >> 5], 1u << (fc[u] & 31));
     } else {
       for (int64_t b0 = 0; b0 < na; b0 += 32) {
         a_entry(A, B, a0, na, b0, bs, blen, a);
         for_slots(blen, bs, a, [&](const bool* ok, const int64_t* j, const int32_t*, const double*, const int*) {
           int32_t c[kSlots];
 #pragma unroll
-          for (int u = 0; u < kSlots; ++u) c[u] = ok[u] ? B.col[j[u]] : -1;
+          for (int u = 0; u < kSlots; ++u) c[u] = ok[u] ? B.col[j[u]] - cb : -1;
 #pragma unroll
           for (int u = 0; u < kSlots; ++u)
-            if (c[u] >= 0 && c[u] < B.cols) atomicOr(&bm[c[u] >> 5], 1u << (c[u] & 31));
+            if (c[u] >= 0 && c[u] < width) atomicOr(&bm[c[u] >> 5], 1u << (c[u] & 31));
         });
       }
     }
@@ -530,7 +537,7 @@ __global__ void __launch_bounds__(kNumWarpsB * 32) k_small_num(SmallCsr A, Small
     for (int r = lane; r < n_out; r += 32) vals[r] = 0.0;
     __syncwarp();
     auto add = [&](int32_t col, double v) {
-      if (col < 0 || col >= B.cols) return;
+      if (col < 0 || col >= width) return;
       const int r = rank_of(bm, pre, col);
       if (r < n_out) atomicAdd(&vals[r], v);
     };
@@ -545,7 +552,7 @@ __global__ void __launch_bounds__(kNumWarpsB * 32) k_small_num(SmallCsr A, Small
           double vv[kSlots];
 #pragma unroll
           for (int u = 0; u < kSlots; ++u) {
-            cc[u] = ok[u] ? B.col[j[u]] : -1;
+            cc[u] = ok[u] ? B.col[j[u]] - cb : -1;
             vv[u] = ok[u] ? av[u] * bv[j[u]] : 0.0;
           }
 #pragma unroll
@@ -572,17 +579,24 @@ constexpr int kPerCount = 6;
 int per_index(int per) { return __builtin_ctz(static_cast<unsigned>(per)); }
 
 template <int PER>
-void sym_launch(dim3 g, size_t smem, cudaStream_t s, const SmallCsr& A, const SmallCsr& B, int check, int64_t run,
-                int G, int32_t* nnz_row, int32_t* loc, int64_t* blk, Summary* sum) {
-  k_small_sym<PER><<<g, kSymWarps * 32, smem, s>>>(A, B, check, run, G, nnz_row, loc, blk, sum);
+void sym_launch(dim3 g, size_t smem, cudaStream_t s, const SmallCsr& A, const SmallCsr& B, int32_t width, int check,
+                int64_t run, int G, int32_t* nnz_row, int32_t* loc, int64_t* blk, Summary* sum) {
+  k_small_sym<PER><<<g, kSymWarps * 32, smem, s>>>(A, B, width, check, run, G, nnz_row, loc, blk, sum);
 }
 
 template <int PER>
-void num_launch(dim3 g, size_t smem, cudaStream_t s, const SmallCsr& A, const SmallCsr& B, int cap, int64_t run,
-                const int32_t* nnz_row, const int32_t* loc, const int64_t* blk, int64_t nblk, void* crp, int crp64,
-                int32_t* ccol, double* cval, uint32_t* err) {
-  k_small_num<PER><<<g, kNumWarpsB * 32, smem, s>>>(A, B, cap, run, nnz_row, loc, blk, nblk, crp, crp64, ccol, cval,
-                                                     err);
+void num_launch(dim3 g, size_t smem, cudaStream_t s, const SmallCsr& A, const SmallCsr& B, int32_t width, int cap,
+                int64_t run, const int32_t* nnz_row, const int32_t* loc, const int64_t* blk, int64_t nblk, void* crp,
+                int crp64, int32_t* ccol, double* cval, uint32_t* err) {
+  k_small_num<PER><<<g, kNumWarpsB * 32, smem, s>>>(A, B, width, cap, run, nnz_row, loc, blk, nblk, crp, crp64, ccol,
+                                                     cval, err);
+}
+
+// c_off[i] = blk[i / run] + loc[i]; c_off[m] = blk[blocks].
+__global__ void __launch_bounds__(256) k_small_offsets(const int32_t* __restrict__ loc, const int64_t* __restrict__ blk,
+                                                       int64_t run, int64_t nblk, int64_t m, int64_t* __restrict__ c_off) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i <= m; i += int64_t(gridDim.x) * blockDim.x)
+    c_off[i] = i < m ? blk[i / run] + loc[i] : blk[nblk];
 }
 
 const void* sym_fn(int k) {
@@ -669,8 +683,8 @@ size_t num_smem(int per, int cap) { return num_warp_bytes(per, cap) * kNumWarpsB
 
 bool small_path_fits(int64_t m, int64_t n) { return m <= kSmallMaxRows && n <= kSmallMaxCols && n > 0; }
 
-SmallGrid small_sym_grid(const SmallCsr& A, int64_t n, int num_sms) {
-  const int per = small_per(n);
+SmallGrid small_sym_grid(const SmallCsr& A, int64_t width, int num_sms) {
+  const int per = small_per(width);
   const int G = small_groups(avg_row(A), static_cast<size_t>(128) * per, kSymWarpBytes);
   const int regs = small_info().sym_regs[per_index(per)];
   const int64_t m = A.rows;
@@ -682,28 +696,39 @@ SmallGrid small_sym_grid(const SmallCsr& A, int64_t n, int num_sms) {
   return SmallGrid{(m + run - 1) / run, run, G};
 }
 
-int launch_small_symbolic(const SmallCsr& A, const SmallCsr& B, SmallGrid g, int check, int32_t* nnz_row,
-                          int32_t* loc, int64_t* blk, Summary* sum, cudaStream_t s) {
-  const int per = small_per(B.cols);
+int launch_small_symbolic(const SmallCsr& A, const SmallCsr& B, int64_t width, SmallGrid g, int check,
+                          int32_t* nnz_row, int32_t* loc, int64_t* blk, Summary* sum, cudaStream_t s) {
+  const int per = small_per(width);
   const dim3 grid(static_cast<unsigned>(g.blocks));
   const size_t smem = sym_smem(per, g.groups);
   const int G = g.groups;
+  const int32_t w = static_cast<int32_t>(width);
+#define SPG_SYM(P) sym_launch<P>(grid, smem, s, A, B, w, check, g.run, G, nnz_row, loc, blk, sum)
   switch (per) {
-    case 1: sym_launch<1>(grid, smem, s, A, B, check, g.run, G, nnz_row, loc, blk, sum); break;
-    case 2: sym_launch<2>(grid, smem, s, A, B, check, g.run, G, nnz_row, loc, blk, sum); break;
-    case 4: sym_launch<4>(grid, smem, s, A, B, check, g.run, G, nnz_row, loc, blk, sum); break;
-    case 8: sym_launch<8>(grid, smem, s, A, B, check, g.run, G, nnz_row, loc, blk, sum); break;
-    case 16: sym_launch<16>(grid, smem, s, A, B, check, g.run, G, nnz_row, loc, blk, sum); break;
-    default: sym_launch<32>(grid, smem, s, A, B, check, g.run, G, nnz_row, loc, blk, sum); break;
+    case 1: SPG_SYM(1); break;
+    case 2: SPG_SYM(2); break;
+    case 4: SPG_SYM(4); break;
+    case 8: SPG_SYM(8); break;
+    case 16: SPG_SYM(16); break;
+    default: SPG_SYM(32); break;
   }
+#undef SPG_SYM
   return 1;
 }
 
-int launch_small_numeric(const SmallCsr& A, const SmallCsr& B, SmallGrid g, int cap, const int32_t* nnz_row,
-                         const int32_t* loc, const int64_t* blk, void* crp, int crp64, int32_t* ccol, double* cval,
-                         uint32_t* err, int num_sms, cudaStream_t s) {
+int launch_small_offsets(const int32_t* loc, const int64_t* blk, SmallGrid g, int64_t m, int64_t* c_off,
+                         cudaStream_t s) {
+  int64_t nb = (m + 1 + 255) / 256;
+  nb = nb < 4096 ? nb : 4096;
+  k_small_offsets<<<static_cast<unsigned>(nb), 256, 0, s>>>(loc, blk, g.run, g.blocks, m, c_off);
+  return 1;
+}
+
+int launch_small_numeric(const SmallCsr& A, const SmallCsr& B, int64_t width, SmallGrid g, int cap,
+                         const int32_t* nnz_row, const int32_t* loc, const int64_t* blk, void* crp, int crp64,
+                         int32_t* ccol, double* cval, uint32_t* err, int num_sms, cudaStream_t s) {
   if (A.rows <= 0) return 0;
-  const int per = small_per(B.cols);
+  const int per = small_per(width);
   cap = cap < 1 ? 1 : (cap > kSmallCap ? kSmallCap : cap);
   const size_t smem = num_smem(per, cap);
   const int regs = small_info().num_regs[per_index(per)];
@@ -711,7 +736,9 @@ int launch_small_numeric(const SmallCsr& A, const SmallCsr& B, SmallGrid g, int 
   int64_t nb = (A.rows + kNumWarpsB - 1) / kNumWarpsB;
   nb = nb < most ? nb : most;
   const dim3 grid(static_cast<unsigned>(nb > 0 ? nb : 1));
-#define SPG_NUM(P) num_launch<P>(grid, smem, s, A, B, cap, g.run, nnz_row, loc, blk, g.blocks, crp, crp64, ccol, cval, err)
+  const int32_t w = static_cast<int32_t>(width);
+#define SPG_NUM(P) \
+  num_launch<P>(grid, smem, s, A, B, w, cap, g.run, nnz_row, loc, blk, g.blocks, crp, crp64, ccol, cval, err)
   switch (per) {
     case 1: SPG_NUM(1); break;
     case 2: SPG_NUM(2); break;

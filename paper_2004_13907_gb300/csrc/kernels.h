@@ -30,11 +30,13 @@ struct Summary {
   uint32_t small_done;    // small-product path: blocks of the symbolic kernel that have finished
 };
 
-// ---- small products of narrow matrices (k_small.cu): a warp per row with a bitmap of all n
-// columns; taken for F64 plans with m <= kSmallMaxRows and n <= kSmallMaxCols, left for the
+// ---- small products of narrow matrices (k_small.cu): a warp per row with a bitmap of all the
+// row's columns (n, or a stacked batch's widest job); taken for F64 plans with m <=
+// kSmallMaxRows (kSmallMaxBatchRows for batches) and a width <= kSmallMaxCols, left for the
 // general path when a row of C has more than kSmallCap entries.
 constexpr int64_t kSmallMaxRows = 65536;
 constexpr int64_t kSmallMaxCols = 32768;
+constexpr int64_t kSmallMaxBatchRows = int64_t(1) << 24;
 constexpr int kSmallCap = 1024;
 // A CSR input with its row pointers as the caller stores them.
 struct SmallCsr {
@@ -43,6 +45,7 @@ struct SmallCsr {
   int32_t rp64;
   const int32_t* col;
   const void* val;
+  const int32_t* cbase;  // A of a stacked batch: the first column of each row's job (else null)
 };
 bool small_path_fits(int64_t m, int64_t n);
 // The symbolic kernel's grid: `blocks` blocks, each a contiguous run of `run` rows, its warps
@@ -51,16 +54,20 @@ struct SmallGrid {
   int64_t blocks, run;
   int groups;
 };
-SmallGrid small_sym_grid(const SmallCsr& A, int64_t n, int num_sms);
+SmallGrid small_sym_grid(const SmallCsr& A, int64_t width, int num_sms);
 // Symbolic pass, validation of A and B (when `check`) and the offsets of C's rows, in one kernel:
 // nnz_row[i], loc[i] (row i's offset within its block's run), blk[b] (run b's offset, b <= blocks,
 // blk[blocks] = nnz(C)), summary->total (nnz(C)), max_row (longest row of C), small_products,
 // small_flags, err. The summary must start zeroed.
-int launch_small_symbolic(const SmallCsr& A, const SmallCsr& B, SmallGrid g, int check, int32_t* nnz_row,
-                          int32_t* loc, int64_t* blk, Summary* sum, cudaStream_t s);
+int launch_small_symbolic(const SmallCsr& A, const SmallCsr& B, int64_t width, SmallGrid g, int check,
+                          int32_t* nnz_row, int32_t* loc, int64_t* blk, Summary* sum, cudaStream_t s);
+// c_off[i] = offset of row i of C (i <= m) from the symbolic kernel's runs (a stacked batch reads them).
+int launch_small_offsets(const int32_t* loc, const int64_t* blk, SmallGrid g, int64_t m, int64_t* c_off,
+                         cudaStream_t s);
 // Numeric pass: the row pointers (int32 or int64), columns and values of C; `cap` = the longest
 // row of C (at most kSmallCap).
-int launch_small_numeric(const SmallCsr& A, const SmallCsr& B, SmallGrid g, int cap, const int32_t* nnz_row,
+int launch_small_numeric(const SmallCsr& A, const SmallCsr& B, int64_t width, SmallGrid g, int cap,
+                         const int32_t* nnz_row,
                          const int32_t* loc, const int64_t* blk, void* crp, int crp64, int32_t* ccol, double* cval,
                          uint32_t* err, int num_sms, cudaStream_t s);
 

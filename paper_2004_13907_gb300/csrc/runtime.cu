@@ -112,9 +112,13 @@ void destroy_events(spgemm_plan_s* p) {
 
 namespace {
 
-SmallCsr small_csr(const spgemm_csr_in& M) {
-  return SmallCsr{M.rows, M.cols, M.nnz, M.row_ptr, M.idx64_rowptr, static_cast<const int32_t*>(M.col), M.val};
+SmallCsr small_csr(const spgemm_csr_in& M, const int32_t* cbase = nullptr) {
+  return SmallCsr{M.rows, M.cols, M.nnz, M.row_ptr, M.idx64_rowptr, static_cast<const int32_t*>(M.col), M.val,
+                  cbase};
 }
+
+// Width of a small plan's column space: n, or a stacked batch's widest job.
+int64_t small_width(const spgemm_plan_s* p) { return p->abase ? p->width : p->B.cols; }
 
 // The small-product path's plan: one workspace block for the summary, the row counts, their
 // offsets within the symbolic kernel's runs of rows and the runs' offsets; nothing is launched
@@ -124,7 +128,7 @@ spgemm_status plan_small(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_
   spgemm_status st = SPGEMM_OK;
   const int64_t m = A->rows;
   auto r256 = [](int64_t b) { return static_cast<size_t>((b + 255) & ~int64_t(255)); };
-  p->small_grid = small_sym_grid(small_csr(*A), B->cols, p->num_sms);
+  p->small_grid = small_sym_grid(small_csr(*A), p->abase ? p->width : B->cols, p->num_sms);
   const size_t sum_bytes = r256(sizeof(Summary));
   const size_t blk_bytes = r256(8 * (p->small_grid.blocks + 1));
   const size_t row_bytes = r256(4 * m);
@@ -143,8 +147,9 @@ spgemm_status plan_small(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_
   if ((st = cuda_status(cudaGetLastError(), "clearing the plan summary")) != SPGEMM_OK) return st;
   // the symbolic kernel starts now, on the plan's stream: spgemm_symbolic only reads its summary
   stage_begin(p, SPGEMM_STAGE_SYM_WARP, s);
-  const int nl = launch_small_symbolic(small_csr(p->a_in), small_csr(p->b_in), p->small_grid, p->opts.validate,
-                                       p->nnz_row, p->small_loc, p->small_blk, p->summary, s);
+  const int nl = launch_small_symbolic(small_csr(p->a_in, p->abase), small_csr(p->b_in), small_width(p),
+                                       p->small_grid, p->opts.validate, p->nnz_row, p->small_loc, p->small_blk,
+                                       p->summary, s);
   stage_end(p, SPGEMM_STAGE_SYM_WARP, nl, s);
   if ((st = cuda_status(cudaGetLastError(), "launching the small-product symbolic pass")) != SPGEMM_OK) return st;
   p->state = 0;
@@ -168,9 +173,12 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
   const spgemm_opts& o = p->opts;
   // small narrow F64 products with the default class options: a warp per row over a bitmap of all
   // columns (k_small.cu), one host read in all
-  p->small = p->prec == SPGEMM_F64 && !p->abase && !p->awidth && !o.general_path && !o.force_window &&
-             o.fp64_accumulate == 0 && o.tiny_max == 32 && o.warp_max == 1024 && o.block_max == 2048 &&
-             o.window_hash_fill == 4096 && m > 0 && small_path_fits(m, n);
+  // (also a stacked batch whose widest job has at most kSmallMaxCols columns)
+  p->small = p->prec == SPGEMM_F64 && !o.general_path && !o.force_window && o.fp64_accumulate == 0 &&
+             o.tiny_max == 32 && o.warp_max == 1024 && o.block_max == 2048 && o.window_hash_fill == 4096 &&
+             m > 0 &&
+             (p->abase ? m <= kSmallMaxBatchRows && p->width > 0 && p->width <= kSmallMaxCols
+                       : small_path_fits(m, n));
   if (p->small) return plan_small(p, A, B, s);
   if (!A->idx64_rowptr) {
     int64_t* t = ws_get<int64_t>(p, m + 1, &st);
@@ -300,6 +308,12 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
     p->total_products = static_cast<int64_t>(h.small_products);
     p->nnz_c = h.total;
     p->small_cap = static_cast<int>(h.max_row);
+    if (p->abase) {
+      // a stacked batch reads its jobs' offsets from the row offsets of C
+      p->c_off = ws_get<int64_t>(p, m + 1, &st);
+      if (st) return st;
+      launch_small_offsets(p->small_loc, p->small_blk, p->small_grid, m, p->c_off, s);
+    }
     // every row counts as one warp-table row in the plan's class counters
     for (int c = 0; c <= kMaxClasses; ++c) {
       p->sym_off[c] = c <= kSymWarp3 ? 0 : m;
@@ -417,7 +431,8 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
   if (p->small) {
     // the numeric kernel writes C's row pointers as well
     stage_begin(p, SPGEMM_STAGE_NUM_WARP, s);
-    nl = launch_small_numeric(small_csr(p->a_in), small_csr(p->b_in), p->small_grid, p->small_cap, p->nnz_row,
+    nl = launch_small_numeric(small_csr(p->a_in, p->abase), small_csr(p->b_in), small_width(p), p->small_grid,
+                              p->small_cap, p->nnz_row,
                               p->small_loc, p->small_blk, C->row_ptr, C->idx64_rowptr, C->col,
                               static_cast<double*>(C->val), &p->summary->err, p->num_sms, s);
     stage_end(p, SPGEMM_STAGE_NUM_WARP, nl, s);

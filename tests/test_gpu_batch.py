@@ -181,3 +181,29 @@ def test_batch_deterministic_mode_equals_exactly_rounded_oracle():
         assert np.array_equal(C.col.cpu().numpy(), ref.col)
         assert np.array_equal(C.val.cpu().numpy(), ref.val), f"job {j}"
     batch.destroy()
+
+
+def test_small_job_batch_takes_the_small_path():
+    """A batch whose widest job has at most 32,768 columns runs as two kernels over every job's rows
+    (each row's bitmap in its own job's column space): every job matches the oracle, and equals
+    the same batch through the general row classes column for column."""
+    import paper_2004_13907_gb300 as sp
+    jobs = _jobs(64, seed=5, n_hi=1000)   # rows of C below 1,024 entries
+    jobs.append((synth.random_small(0, 5, 0.5, seed=1), synth.random_small(5, 7, 0.5, seed=2)))
+    jobs.append((synth.uniform_random(50, 40, 0.3, seed=9), synth.uniform_random(40, 32_768, 0.001, seed=10)))
+    dA = [sp.DeviceCSR.from_host(A, "cuda") for A, _ in jobs]
+    dB = [sp.DeviceCSR.from_host(B, "cuda", idx64=(j % 2 == 1)) for j, (_, B) in enumerate(jobs)]
+    batch = sp.spgemm_batch(dA, dB)
+    batch.check()
+    info = batch.info()
+    cls = dict(zip(sp._native.NUM_CLASSES, info["num_class_rows"]))
+    assert cls["warp1024"] == sum(A.rows for A, _ in jobs)
+    ref = sp.spgemm_batch(dA, dB, opts=sp.spgemm_opts_default(general_path=1))
+    ref.check()
+    torch.cuda.synchronize()
+    for j, (A, B) in enumerate(jobs):
+        got = batch.result(j)
+        _check_job(A, B, got)
+        assert torch.equal(got.col, ref.result(j).col)
+    batch.destroy()
+    ref.destroy()
