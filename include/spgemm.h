@@ -143,7 +143,12 @@ typedef struct spgemm_opts {
                                  (one symbolic kernel, a scan, one numeric kernel around the single
                                  host read of nnz(C)); a row of C with more than 1,024 entries, or
                                  this flag, sends it through the general row classes */
-  int32_t reserved[9];
+  int32_t host_panels;        /* spgemm_multiply_host: row panels of A multiplied one after another
+                                 while the previous panels' C is copied to the host, each with an
+                                 equal share of the partial products. 0: 4 panels when A's entries
+                                 times B's mean row length reach 1e8, else one; N >= 1: N panels
+                                 (at most 64) */
+  int32_t reserved[8];
 } spgemm_opts;
 
 /* Opaque plan: the work description of one product (row counts, row classes, row
@@ -255,9 +260,12 @@ spgemm_status spgemm_plan_destroy(spgemm_plan_t* plan);
 /* One product through HOST buffers: copies A and B (host pointers) to the device, runs
  * plan, symbolic and numeric, and copies C back into the caller's host arrays C->row_ptr
  * (rows+1), C->col and C->val, which must hold nnz_capacity entries. When nnz(C) exceeds
- * nnz_capacity nothing is copied, *nnz_c is set and INVALID_ARG is returned, so the caller
- * can grow its buffers and call again. Synchronous. C->idx64_rowptr selects the row_ptr
- * type. Device staging comes from `alloc` (cudaMallocAsync when NULL). */
+ * nnz_capacity, *nnz_c is set and INVALID_ARG is returned (the host arrays' contents are then
+ * unspecified), so the caller can grow its buffers and call again. Large products run in row
+ * panels of A (opts->host_panels): each panel is planned and multiplied while the previous ones'
+ * rows of C are copied to the host on a second stream. Synchronous. C->idx64_rowptr selects the
+ * row_ptr type (INDEX_OVERFLOW when nnz(C) needs int64 and it is int32). Device staging comes
+ * from `alloc` (cudaMallocAsync when NULL); panels of C come from the library's pool. */
 spgemm_status spgemm_multiply_host(const spgemm_csr_in* A_host, const spgemm_csr_in* B_host,
                                    spgemm_prec prec, const spgemm_opts* opts,
                                    const spgemm_allocator* alloc, void* stream,

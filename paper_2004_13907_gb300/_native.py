@@ -50,7 +50,7 @@ class Opts(ctypes.Structure):
                 ("f32c_rerun_all", c_i32), ("f32c_rerun_none", c_i32), ("num_streams", c_i32),
                 ("record_timings", c_i32), ("window_split_max_mb", c_i32), ("max_sms", c_i32),
                 ("window_cols_max_mb", c_i32), ("fp64_accumulate", c_i32), ("general_path", c_i32),
-                ("reserved", c_i32 * 9)]
+                ("host_panels", c_i32), ("reserved", c_i32 * 8)]
 
 
 class PlanInfo(ctypes.Structure):

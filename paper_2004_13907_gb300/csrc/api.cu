@@ -251,10 +251,9 @@ spgemm_status spgemm_plan_check(spgemm_plan_t* plan, void* stream) {
   const spgemm_status st = read_device_error(plan, static_cast<cudaStream_t>(stream));
   if (st == SPGEMM_OK && plan->fx_rerun_pending) {
     int32_t n = 0;
-    cudaError_t e = cudaMemcpyAsync(&n, plan->counters + 6, sizeof(n), cudaMemcpyDeviceToHost,
-                                    static_cast<cudaStream_t>(stream));
-    if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_status(e, "reading the FP64 rerun count");
+    const spgemm_status rs = read_small(&n, plan->counters + 6, sizeof(n), static_cast<cudaStream_t>(stream),
+                                        &plan->launches, "reading the FP64 rerun count");
+    if (rs != SPGEMM_OK) return rs;
     plan->f32c_rerun_rows = n;
   }
   return st;

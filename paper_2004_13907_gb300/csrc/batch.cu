@@ -252,9 +252,8 @@ spgemm_status batch_prepare(int64_t n_jobs, const spgemm_csr_in* A, const spgemm
     b->launches += (na > 0) + (nb > 0);
   }
   uint32_t herr = 0;
-  e = cudaMemcpyAsync(&herr, b->err, sizeof(herr), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) { cuda_status(e, "stacking the batch"); return fail(SPGEMM_ERR_CUDA); }
+  if ((st = read_small(&herr, b->err, sizeof(herr), s, &b->launches, "stacking the batch")) != SPGEMM_OK)
+    return fail(st);
   if (herr) {
     set_error_msg(SPGEMM_ERR_INVALID_CSR, "a job has a column index outside its matrix");
     return fail(SPGEMM_ERR_INVALID_CSR);

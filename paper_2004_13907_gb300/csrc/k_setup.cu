@@ -23,6 +23,13 @@ __global__ void k_rowptr_rebase(const void* __restrict__ in, int idx64, int64_t 
   }
 }
 
+// Small reads of device state: a grid of SMs stores the words into mapped page-locked host
+// memory, so the read never queues on the copy engine behind bulk copies to the host.
+__global__ void k_fetch(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, int64_t words) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < words; i += int64_t(gridDim.x) * blockDim.x)
+    dst[i] = src[i];
+}
+
 __global__ void k_rowptr_to64(const int32_t* __restrict__ in, int64_t* __restrict__ out, int64_t n1) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n1;
        i += int64_t(gridDim.x) * blockDim.x)
@@ -390,6 +397,13 @@ int launch_rowptr_rebase(const void* in, int idx64, int64_t r0, int64_t n1, int6
                          cudaStream_t s) {
   if (n1 <= 0) return 0;
   k_rowptr_rebase<<<grid_for(n1, 256), 256, 0, s>>>(in, idx64, r0, n1, base, out);
+  return 1;
+}
+
+int launch_fetch(const void* src, void* dst, int64_t bytes, cudaStream_t s) {
+  const int64_t words = bytes / 4;
+  if (words <= 0) return 0;
+  k_fetch<<<grid_for(words, 256), 256, 0, s>>>(static_cast<const uint32_t*>(src), static_cast<uint32_t*>(dst), words);
   return 1;
 }
 

@@ -73,6 +73,8 @@ int launch_small_numeric(const SmallCsr& A, const SmallCsr& B, int64_t width, Sm
 
 // ---- setup / scan kernels (k_setup.cu)
 int launch_rowptr_to64(const int32_t* in, int64_t* out, int64_t n1, cudaStream_t s);
+// dst (mapped page-locked host memory, as a device pointer) = src[0 .. bytes), bytes a multiple of 4.
+int launch_fetch(const void* src, void* dst, int64_t bytes, cudaStream_t s);
 // out[t] = in[r0 + t] - base for t < n1 (in: int32 or int64 row pointers).
 int launch_rowptr_rebase(const void* in, int idx64, int64_t r0, int64_t n1, int64_t base, int64_t* out,
                          cudaStream_t s);

@@ -28,43 +28,8 @@ template <typename T>
 T* ws_get(spgemm_plan_s* p, int64_t count, spgemm_status* st) { return ws_alloc<T>(p, count, st); }
 
 
-// Page-locked host copies of the summary, shared by all plans: a read takes one from the free
-// list (allocating one on first need) and returns it, so the copy runs as a direct DMA.
-std::mutex g_pinned_mu;
-std::vector<Summary*> g_pinned_free;
-
-Summary* pinned_take() {
-  {
-    std::lock_guard<std::mutex> lk(g_pinned_mu);
-    if (!g_pinned_free.empty()) {
-      Summary* h = g_pinned_free.back();
-      g_pinned_free.pop_back();
-      return h;
-    }
-  }
-  void* h = nullptr;
-  if (cudaMallocHost(&h, sizeof(Summary)) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return static_cast<Summary*>(h);
-}
-
-void pinned_give(Summary* h) {
-  std::lock_guard<std::mutex> lk(g_pinned_mu);
-  g_pinned_free.push_back(h);
-}
-
 spgemm_status read_summary(spgemm_plan_s* p, Summary* h, cudaStream_t s) {
-  Summary* hp = pinned_take();
-  cudaError_t e = cudaMemcpyAsync(hp ? hp : h, p->summary, sizeof(Summary), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (hp) {
-    if (e == cudaSuccess) *h = *hp;
-    pinned_give(hp);
-  }
-  if (e != cudaSuccess) return cuda_status(e, "reading the pass summary");
-  return SPGEMM_OK;
+  return read_small(h, p->summary, sizeof(Summary), s, &p->launches, "reading the pass summary");
 }
 
 spgemm_status error_bits_status(uint32_t err) {
@@ -77,6 +42,58 @@ spgemm_status error_bits_status(uint32_t err) {
 int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 }  // namespace
+
+namespace {
+
+// Page-locked, mapped staging blocks shared by all reads: a read takes one from the free list
+// (allocating it on first need) and gives it back.
+constexpr size_t kStageBytes = 4096;
+std::mutex g_stage_mu;
+std::vector<void*> g_stage_free;
+
+void* stage_take() {
+  {
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    if (!g_stage_free.empty()) {
+      void* h = g_stage_free.back();
+      g_stage_free.pop_back();
+      return h;
+    }
+  }
+  void* h = nullptr;
+  if (cudaHostAlloc(&h, kStageBytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return h;
+}
+
+void stage_give(void* h) {
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  g_stage_free.push_back(h);
+}
+
+}  // namespace
+
+spgemm_status read_small(void* dst, const void* src, size_t bytes, cudaStream_t s, int64_t* launches,
+                         const char* what) {
+  void* hp = bytes <= kStageBytes && bytes % 4 == 0 ? stage_take() : nullptr;
+  void* dp = nullptr;
+  cudaError_t e;
+  if (hp && cudaHostGetDevicePointer(&dp, hp, 0) == cudaSuccess) {
+    const int n = launch_fetch(src, dp, static_cast<int64_t>(bytes), s);
+    if (launches) *launches += n;
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) std::memcpy(dst, hp, bytes);
+  } else {
+    cudaGetLastError();
+    e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (hp) stage_give(hp);
+  if (e != cudaSuccess) return cuda_status(e, what);
+  return SPGEMM_OK;
+}
 
 spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s) {
   Summary h;
@@ -226,9 +243,8 @@ spgemm_status plan_run(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_cs
     // takes the windowed kernel, which keeps the full bound
     launch_negative_check(p->A.val, A->nnz, p->B.val, B->nnz, p->counters + 8, p->num_sms, s);
     int32_t neg = 1;
-    cudaError_t e = cudaMemcpyAsync(&neg, p->counters + 8, sizeof(neg), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(e, "reading the sign check of the FP32 values");
+    st = read_small(&neg, p->counters + 8, sizeof(neg), s, &p->launches, "reading the sign check of the FP32 values");
+    if (st) return st;
     p->cp.window_all = neg ? 1 : 0;
   }
 
@@ -544,9 +560,8 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       nl = launch_collect_flagged(seg(kNumWin0), nwh, p->rerun_flag, all, list_w, p->counters + 4, s);
       nl += launch_collect_flagged(seg(kNumTiny), cnt(kNumTiny), p->rerun_flag, all, list_t, p->counters + 5, s);
       int32_t hc[2] = {0, 0};
-      cudaError_t e = cudaMemcpyAsync(hc, p->counters + 4, sizeof(hc), cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) return cuda_status(e, "reading the FP64 rerun counts");
+      spgemm_status rs = read_small(hc, p->counters + 4, sizeof(hc), s, &p->launches, "reading the FP64 rerun counts");
+      if (rs) return rs;
       if (hc[0] > 0)
         nl += launch_rerun_dense(p->A, p->B, list_w, hc[0], p->c_off, C->col, static_cast<float*>(C->val), p->abase,
                                  p->width, p->rerun_dense, p->rerun_group, p->num_sms, err, s);

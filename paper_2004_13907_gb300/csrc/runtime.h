@@ -27,6 +27,7 @@ spgemm_status set_error_msg(spgemm_status st, const char* fmt, ...);
 void clear_error_msg();
 spgemm_status cuda_status(cudaError_t e, const char* what);
 int device_sm_count();
+cudaMemPool_t library_pool();   // the library's stream-ordered pool on the current device (null if none)
 spgemm_status check_csr_in(const spgemm_csr_in* M, const char* name, spgemm_prec prec);
 
 }  // namespace spg
@@ -105,6 +106,11 @@ T* ws_alloc(spgemm_plan_s* p, int64_t count, spgemm_status* st);
 spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s);
 spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s);
 spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s);
+// Synchronous read of a few bytes of device state (a multiple of 4, at most 4 KB) on stream s,
+// by a kernel storing into mapped page-locked memory (copies to the host queue behind every bulk
+// copy in flight); `launches` (may be null) counts the kernel.
+spgemm_status read_small(void* dst, const void* src, size_t bytes, cudaStream_t s, int64_t* launches,
+                         const char* what);
 // Below this many micro rows (at most 8 A entries and 32 partial products) the rows take the
 // warp-per-row tiny kernels instead of the thread-per-row merge, whose dependent loads make it
 // pay only when many rows run at once.

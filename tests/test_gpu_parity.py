@@ -373,3 +373,45 @@ def test_galerkin_triple_product(g):
     assert np.array_equal(Ac.val.cpu().numpy(), 6.0 * L.val)
     sp.spgemm_plan_destroy(p1)
     sp.spgemm_plan_destroy(p2)
+
+
+@pytest.mark.parametrize("panels,idx64", [(2, False), (5, True), (64, False)])
+def test_host_entry_in_row_panels(panels, idx64):
+    """spgemm_multiply_host in row panels of A (each multiplied while the previous panels' C is
+    copied back on a second stream): the same C as the oracle, with int32 or int64 row pointers,
+    and a capacity too small reports nnz(C) for a second call."""
+    import paper_2004_13907_gb300 as sp
+    for A in (synth.uniform_random(3000, 2500, 3e-3, seed=21), synth.rmat(12, 16, seed=22)):
+        B = A if A.rows == A.cols else synth.uniform_random(A.cols, 1800, 4e-3, seed=23)
+        pin = lambda M: sp.DeviceCSR(M.rows, M.cols, torch.from_numpy(M.row_ptr.astype(np.int32)).pin_memory(),
+                                     torch.from_numpy(M.col).pin_memory(), torch.from_numpy(M.val).pin_memory())
+        o = opts(host_panels=panels)
+        C = sp.spgemm_multiply_host(pin(A), pin(B), opts=o, idx64=idx64)
+        assert C.row_ptr.dtype == (torch.int64 if idx64 else torch.int32)
+        assert_parity(A, B, C.row_ptr.numpy().astype(np.int64), C.col.numpy(), C.val.numpy())
+        ref = oracle.spgemm(A, B)
+        small = sp.DeviceCSR(A.rows, B.cols, torch.empty(A.rows + 1, dtype=torch.int32).pin_memory(),
+                             torch.empty(max(ref.nnz // 2, 1), dtype=torch.int32).pin_memory(),
+                             torch.empty(max(ref.nnz // 2, 1), dtype=torch.float64).pin_memory())
+        C2 = sp.spgemm_multiply_host(pin(A), pin(B), opts=o, out=small)
+        assert np.array_equal(C2.col.numpy(), ref.col)
+
+
+def test_host_entry_default_panels_on_a_large_product():
+    """spgemm_multiply_host with default options on a product large enough to run in the default
+    row panels (A's entries times B's mean row length above 1e8): every row against the oracle."""
+    import paper_2004_13907_gb300 as sp
+    A = synth.uniform_random(260_000, 260_000, 8e-5, seed=24)
+    assert A.nnz * (A.nnz / A.rows) > 1e8
+    hA = sp.DeviceCSR(A.rows, A.cols, torch.from_numpy(A.row_ptr.astype(np.int32)).pin_memory(),
+                      torch.from_numpy(A.col).pin_memory(), torch.from_numpy(A.val).pin_memory())
+    C = sp.spgemm_multiply_host(hA, hA)
+    seen = [0]
+
+    def check(ref, rp, col, val, r0, r1):
+        assert np.array_equal(rp, ref.row_ptr) and np.array_equal(col, ref.col), f"rows [{r0}, {r1})"
+        assert np.all(np.abs(val - ref.val) <= 1e-12 * ref.mag), f"values in rows [{r0}, {r1})"
+        seen[0] += len(col)
+
+    compare_all_rows(A, A, C, check)
+    assert seen[0] == C.nnz
