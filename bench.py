@@ -215,14 +215,18 @@ def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: 
     precs = {name: prec for name, _, prec in specs}
     dev = [(name, M, sp.DeviceCSR.from_host(M, "cuda")) for name, M in mats]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    opts = sp.spgemm_opts_default(record_timings=1)
+    # the timed steps run the product as a caller does (default options); the stage breakdown
+    # comes from as many steps again with stage events, which cost microseconds per plan (a tenth
+    # of a small product)
+    opts = sp.spgemm_opts_default()
+    opts_staged = sp.spgemm_opts_default(record_timings=1)
     stream = torch.cuda.current_stream()
     peak, _ = _peaks()
 
-    def step(keep=False):
+    def step(o):
         out = []
         for name, M, dM in dev:
-            plan = sp.spgemm_plan(dM, dM, precs[name], opts)
+            plan = sp.spgemm_plan(dM, dM, precs[name], o)
             sp.spgemm_symbolic(plan)
             C = sp.alloc_output(plan)
             sp.spgemm_numeric(plan, C)
@@ -230,34 +234,37 @@ def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: 
         return out
 
     for _ in range(warmup):
-        for name, plan, C in step():
+        for name, plan, C in step(opts):
             sp.spgemm_plan_destroy(plan)
         flush.zero_()
     torch.cuda.synchronize()
     times, stages, products, launches, infos = [], {}, 0, 0, {}
-    for _ in range(steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        products = 0
-        for name, plan, C in res:
-            sp.spgemm_plan_check(plan)
-            info = sp.spgemm_plan_get_info(plan)
-            infos[name] = info
-            products += info["products"]
-            launches += info["kernel_launches"]
-            step_st = {}
-            for k, (ms, _) in sp.spgemm_plan_get_timings(plan).items():
-                key = (name, "num_window" if k == "num_expand" else k)   # the expansion completes the pass
-                step_st[key] = step_st.get(key, 0.0) + ms
-            for key, ms in step_st.items():
-                stages.setdefault(key, []).append(ms)
-            sp.spgemm_plan_destroy(plan)
-        del res
+    for staged in (False, True):
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = step(opts_staged if staged else opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if not staged:
+                times.append(e0.elapsed_time(e1))
+            products = 0
+            for name, plan, C in res:
+                sp.spgemm_plan_check(plan)
+                info = sp.spgemm_plan_get_info(plan)
+                infos[name] = info
+                products += info["products"]
+                if not staged:
+                    launches += info["kernel_launches"]
+                step_st = {}
+                for k, (ms, _) in sp.spgemm_plan_get_timings(plan).items():
+                    key = (name, "num_window" if k == "num_expand" else k)   # the expansion completes the pass
+                    step_st[key] = step_st.get(key, 0.0) + ms
+                for key, ms in step_st.items():
+                    stages.setdefault(key, []).append(ms)
+                sp.spgemm_plan_destroy(plan)
+            del res
     ms = float(np.mean(times))
     st = {k: float(np.mean(v)) for k, v in stages.items()}
     (dom_name, dom_stage), dom_ms = max(st.items(), key=lambda kv: kv[1])
@@ -270,7 +277,8 @@ def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: 
            "numeric": {"ms": round(numeric_ms, 4), "alg_bytes": nbytes,
                        "GBps": round(nbytes / (numeric_ms * 1e-3) / 1e9, 1),
                        "frac_of_peak": round(nbytes / (numeric_ms * 1e-3) / 1e9 / peak, 4)},
-           "stage_ms": {f"{n}:{k}": round(v, 4) for (n, k), v in st.items() if v > 0.001}}
+           "stage_ms": {f"{n}:{k}": round(v, 4) for (n, k), v in st.items() if v > 0.001},
+           "stage_timing": "stage events in as many further steps (the timed steps run default options)"}
     if dom_stage == "num_window":
         wb, _ = _window_bytes(infos[dom_name])
         out["roofline"] = {"bound": "hbm", "kernel": f"k_num_window + k_expand_cols ({dom_name})",
@@ -282,7 +290,7 @@ def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: 
     if cpu_err:
         # CPU-baseline leg: the oracle on a bounded row sample of the product, its rate, and the
         # GPU result's error on those rows (FP32 results against the FP64 oracle)
-        res = step()
+        res = step(opts)
         torch.cuda.synchronize()
         out["cpu_baseline"], out["max_rel_err"] = cpu_baseline_error(mats, res, args.cpu_seconds, sp)
         for name, plan, C in res:

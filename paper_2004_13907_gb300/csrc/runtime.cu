@@ -5,6 +5,7 @@
 // allocate C); one, after the symbolic pass, on the small-product path.
 #include <cstring>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "runtime.h"
@@ -102,19 +103,49 @@ spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s) {
   return error_bits_status(h.err);
 }
 
+namespace {
+
+// Timing events come from a process-wide free list (per device) and go back to it when the plan
+// is destroyed: an instrumented plan pays two event records per stage it runs, not the creation
+// of events.
+std::mutex g_ev_mu;
+std::vector<std::pair<int, cudaEvent_t>> g_ev_free;
+
+cudaEvent_t event_take(int dev) {
+  {
+    std::lock_guard<std::mutex> lk(g_ev_mu);
+    for (size_t i = g_ev_free.size(); i-- > 0;)
+      if (g_ev_free[i].first == dev) {
+        const cudaEvent_t e = g_ev_free[i].second;
+        g_ev_free[i] = g_ev_free.back();
+        g_ev_free.pop_back();
+        return e;
+      }
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+}  // namespace
+
 void stage_begin(spgemm_plan_s* p, int stage, cudaStream_t s) {
   if (!p->opts.record_timings) return;
   if (!p->ev_made) {
-    for (int i = 0; i < SPGEMM_NUM_STAGES; ++i)
-      for (int j = 0; j < 2; ++j) cudaEventCreate(&p->ev[i][j]);
+    if (cudaGetDevice(&p->ev_dev) != cudaSuccess) return;
     p->ev_made = true;
   }
-  cudaEventRecord(p->ev[stage][0], s);
+  for (int j = 0; j < 2; ++j)
+    if (!p->ev[stage][j]) p->ev[stage][j] = event_take(p->ev_dev);
+  if (p->ev[stage][0]) cudaEventRecord(p->ev[stage][0], s);
 }
 
 void stage_end(spgemm_plan_s* p, int stage, int launches, cudaStream_t s) {
   p->launches += launches;
-  if (!p->opts.record_timings || !p->ev_made) return;
+  if (!p->opts.record_timings || !p->ev[stage][0] || !p->ev[stage][1]) return;
   cudaEventRecord(p->ev[stage][1], s);
   p->ev_rec[stage] = true;
   p->ev_launches[stage] = launches;
@@ -122,8 +153,13 @@ void stage_end(spgemm_plan_s* p, int stage, int launches, cudaStream_t s) {
 
 void destroy_events(spgemm_plan_s* p) {
   if (!p->ev_made) return;
+  std::lock_guard<std::mutex> lk(g_ev_mu);
   for (int i = 0; i < SPGEMM_NUM_STAGES; ++i)
-    for (int j = 0; j < 2; ++j) cudaEventDestroy(p->ev[i][j]);
+    for (int j = 0; j < 2; ++j)
+      if (p->ev[i][j]) {
+        g_ev_free.emplace_back(p->ev_dev, p->ev[i][j]);
+        p->ev[i][j] = nullptr;
+      }
   p->ev_made = false;
 }
 

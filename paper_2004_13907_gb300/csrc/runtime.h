@@ -92,6 +92,7 @@ struct spgemm_plan_s {
   // stage timing (record_timings)
   cudaEvent_t ev[16][2] = {};
   bool ev_made = false;
+  int ev_dev = 0;                // device of the plan's timing events
   bool ev_rec[16] = {};
   int ev_launches[16] = {};
   int state = 0;

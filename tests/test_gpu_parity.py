@@ -415,3 +415,32 @@ def test_host_entry_default_panels_on_a_large_product():
 
     compare_all_rows(A, A, C, check)
     assert seen[0] == C.nnz
+
+
+def test_stage_timings_per_plan_with_reused_events():
+    """record_timings: every stage a plan ran reports a positive device time and its launches,
+    the small-product path none of the general path's stages, and plans made one after another
+    (whose timing events come back to a shared pool) each their own. Without the option nothing
+    is recorded."""
+    import paper_2004_13907_gb300 as sp
+    big = synth.rmat(12, 16, seed=25)                    # general row classes
+    small = synth.uniform_random(2000, 2000, 2e-3, seed=26)   # small-product path
+    for rep in range(3):
+        for M, expect in ((big, {"count", "num_rowptr"}), (small, {"sym_warp", "num_warp"})):
+            dM = sp.DeviceCSR.from_host(M, "cuda")
+            plan = sp.spgemm_plan(dM, dM, opts=opts(record_timings=1))
+            sp.spgemm_symbolic(plan)
+            C = sp.alloc_output(plan)
+            sp.spgemm_numeric(plan, C)
+            t = sp.spgemm_plan_get_timings(plan)
+            ran = {k for k, (ms, nl) in t.items() if nl > 0}
+            assert expect <= ran, (expect, t)
+            assert all(ms > 0 for k, (ms, nl) in t.items() if k in ran)
+            if M is small:
+                assert not ran & {"count", "num_rowptr", "num_window"}
+            sp.spgemm_plan_destroy(plan)
+    dM = sp.DeviceCSR.from_host(small, "cuda")
+    plan = sp.spgemm_plan(dM, dM)
+    sp.spgemm_symbolic(plan)
+    assert all(ms == 0 and nl == 0 for ms, nl in sp.spgemm_plan_get_timings(plan).values())
+    sp.spgemm_plan_destroy(plan)
