@@ -172,16 +172,21 @@ def _dist():
     return ws, rank, local
 
 
-def _window_bytes(info: dict) -> tuple:
+def _window_bytes(info: dict, vbytes: int = 8) -> tuple:
     """Algorithmic bytes of the windowed numeric pass (k_num_window, and k_expand_cols for the
     columns of rows whose bitmap the symbolic pass stored): per row 8 (its A row pointers), per
-    A entry 12 (column, value) + 8 (start and end of the named B row), per partial product 12
-    (the gathered B column and value), per entry of C 12 (column, value)."""
+    A entry 4 + v (column, value) + 8 (start and end of the named B row), per partial product
+    4 + v (the gathered B column and value), per entry of C 4 + v (column, value); v = 8 (FP64)
+    or 4 (FP32)."""
     rows = sum(info["num_class_rows"][0:4])
     annz = sum(info["num_class_annz"][0:4])
     prods = sum(info["num_class_products"][0:4])
     cnnz = sum(info["num_class_cnnz"][0:4])
-    return 8 * rows + 20 * annz + 12 * prods + 12 * cnnz, prods
+    return 8 * rows + (12 + vbytes) * annz + (4 + vbytes) * prods + (4 + vbytes) * cnnz, prods
+
+
+def _vbytes(prec: str) -> int:
+    return 4 if prec == "f32c" else 8
 
 
 def _class_bytes(info: dict, vbytes: int = 8) -> dict:
@@ -198,12 +203,13 @@ def _class_bytes(info: dict, vbytes: int = 8) -> dict:
     return out
 
 
-def _numeric_bytes(info: dict, m: int) -> int:
+def _numeric_bytes(info: dict, m: int, vbytes: int = 8) -> int:
     """Algorithmic bytes of a whole numeric pass (all classes): A (row pointers, columns,
     values), the gathered B rows (row bounds, columns, values) and C (row pointers, columns,
-    values)."""
+    values); v = 8 (FP64) or 4 (FP32) bytes per value."""
     annz = sum(info["num_class_annz"])
-    return 4 * (m + 1) + 12 * annz + 8 * annz + 12 * info["products"] + 8 * (m + 1) + 12 * info["nnz_c"]
+    return (4 * (m + 1) + (4 + vbytes) * annz + 8 * annz + (4 + vbytes) * info["products"] + 8 * (m + 1) +
+            (4 + vbytes) * info["nnz_c"])
 
 
 def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: bool = False) -> dict:
@@ -257,12 +263,13 @@ def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: 
                 products += info["products"]
                 if not staged:
                     launches += info["kernel_launches"]
-                step_st = {}
-                for k, (ms, _) in sp.spgemm_plan_get_timings(plan).items():
-                    key = (name, "num_window" if k == "num_expand" else k)   # the expansion completes the pass
-                    step_st[key] = step_st.get(key, 0.0) + ms
-                for key, ms in step_st.items():
-                    stages.setdefault(key, []).append(ms)
+                else:
+                    step_st = {}
+                    for k, (ms, _) in sp.spgemm_plan_get_timings(plan).items():
+                        key = (name, "num_window" if k == "num_expand" else k)   # the expansion completes the pass
+                        step_st[key] = step_st.get(key, 0.0) + ms
+                    for key, ms in step_st.items():
+                        stages.setdefault(key, []).append(ms)
                 sp.spgemm_plan_destroy(plan)
             del res
     ms = float(np.mean(times))
@@ -270,7 +277,7 @@ def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: 
     (dom_name, dom_stage), dom_ms = max(st.items(), key=lambda kv: kv[1])
     name0, M0, _ = dev[0]
     numeric_ms = sum(v for (n_, k), v in st.items() if k.startswith("num_"))
-    nbytes = sum(_numeric_bytes(infos[n], M.rows) for n, M, _ in dev)
+    nbytes = sum(_numeric_bytes(infos[n], M.rows, _vbytes(precs[n])) for n, M, _ in dev)
     out = {"workload": wl, "value": round(_job_gflops(products, 1, ms), 3), "unit": UNIT, "ms_per_step": round(ms, 4),
            "steps": steps, "warmup": warmup, "products_per_step": products, "gpu_launches": int(launches),
            "description": WORKLOAD_DESC.get(wl, wl),
@@ -280,7 +287,7 @@ def _product_config(wl: str, args, sp, torch, steps: int, warmup: int, cpu_err: 
            "stage_ms": {f"{n}:{k}": round(v, 4) for (n, k), v in st.items() if v > 0.001},
            "stage_timing": "stage events in as many further steps (the timed steps run default options)"}
     if dom_stage == "num_window":
-        wb, _ = _window_bytes(infos[dom_name])
+        wb, _ = _window_bytes(infos[dom_name], _vbytes(precs[dom_name]))
         out["roofline"] = {"bound": "hbm", "kernel": f"k_num_window + k_expand_cols ({dom_name})",
                            "achieved": round(wb / (dom_ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                            "frac": round(wb / (dom_ms * 1e-3) / 1e9 / peak, 4), "algorithmic_bytes": wb,
@@ -517,7 +524,7 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     roof = None
     if dom_stage == "num_window":
-        bytes_, wprods = _window_bytes(per[dom_mat]["info"])
+        bytes_, wprods = _window_bytes(per[dom_mat]["info"], _vbytes(precs[dom_mat]))
         achieved = bytes_ / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": f"k_num_window + k_expand_cols ({dom_mat})",
                 "achieved": round(achieved, 1),
@@ -542,7 +549,7 @@ def run_ours(args):
             "numeric_ms": round(sum(float(np.mean(d["stages"][k])) for k in
                                     ("num_rowptr", "num_window", "num_expand", "num_block", "num_warp",
                                      "num_tiny")), 4),
-            "numeric_alg_bytes": _numeric_bytes(info, d["rows"]),
+            "numeric_alg_bytes": _numeric_bytes(info, d["rows"], _vbytes(precs[name])),
             "num_class_rows": {sp._native.NUM_CLASSES[c]: info["num_class_rows"][c]
                                for c in range(len(sp._native.NUM_CLASSES)) if info["num_class_rows"][c]},
             "num_class_alg_bytes": _class_bytes(info, 4 if precs[name] == "f32c" else 8),

@@ -370,11 +370,10 @@ spgemm_status spgemm_coo_to_csr(int64_t rows, int64_t cols, int64_t nnz, const i
  * are not checked here).
  * Scratch: one fixed device array of about 770 KB inside the library, which every GPU that
  * loads the library holds until the process exits. The first call on a device looks up that
- * array's address (cudaGetSymbolAddress, with the device current), so make the first call
- * before any stream capture. Every call uses the same array: calls whose work overlaps on the
- * GPU (from several threads or streams) race and must be serialised by the caller. The call
- * waits for `stream` twice (to read nnz(C) and the device error word) and returns with C
- * written. */
+ * array's address (cudaGetSymbolAddress, with the device current). Every call uses the same
+ * array: calls whose work overlaps on the GPU (from several threads or streams) race and must
+ * be serialised by the caller. The call waits for `stream` twice (to read nnz(C) and the device
+ * error word) and returns with C written. */
 spgemm_status spgemm_multiply_noalloc(const spgemm_csr_in* A, const spgemm_csr_in* B,
                                       spgemm_csr_out* C, int64_t nnz_capacity, int64_t* nnz_c,
                                       void* stream);

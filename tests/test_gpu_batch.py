@@ -207,3 +207,44 @@ def test_small_job_batch_takes_the_small_path():
         assert torch.equal(got.col, ref.result(j).col)
     batch.destroy()
     ref.destroy()
+
+
+def test_batch_jobs_from_the_full_distribution():
+    """Jobs of the 4,096-job workload as it is drawn (seed 0, n up to 50,000, density up to 1e-2):
+    the largest job of all (n = 49,806, about 1.2e10 partial products, 29 GB of C), two jobs near
+    8 GB of C and a seeded spread of the rest, stacked in one batch. Jobs with at most 2e7 partial
+    products are compared on every row, larger ones on their four heaviest rows and 60 seeded
+    others."""
+    import paper_2004_13907_gb300 as sp
+    rng = np.random.default_rng(31)
+    idx = [1313, 2404, 1142] + [int(i) for i in rng.choice(4096, 21, replace=False) if i not in (1313, 2404, 1142)]
+    jobs = [synth.batch_job(i, seed=0) for i in idx]
+    assert jobs[0][0].rows == 49_806
+    dA = [sp.DeviceCSR.from_host(A, "cuda") for A, _ in jobs]
+    dB = [sp.DeviceCSR.from_host(B, "cuda") for _, B in jobs]
+    batch = sp.spgemm_batch(dA, dB)
+    batch.check()
+    torch.cuda.synchronize()
+    assert batch.info()["products"] == sum(int(oracle.products_per_row(A, B).sum()) for A, B in jobs)
+    sampled = 0
+    for j, (A, B) in enumerate(jobs):
+        C = batch.result(j)
+        P = oracle.products_per_row(A, B)
+        if P.sum() <= 2e7:
+            _check_job(A, B, C)
+            continue
+        sampled += 1
+        rows = np.unique(np.concatenate([np.argsort(P)[-4:], rng.choice(A.rows, 60, replace=False)]))
+        ref = oracle.spgemm(A, B, rows)
+        rp = C.row_ptr.cpu().numpy().astype(np.int64)
+        for t, r in enumerate(rows):
+            s, e = int(rp[r]), int(rp[r + 1])
+            rs, re = int(ref.row_ptr[t]), int(ref.row_ptr[t + 1])
+            assert e - s == re - rs, f"job {idx[j]} row {r}: {e - s} entries, oracle {re - rs}"
+            assert np.array_equal(C.col[s:e].cpu().numpy(), ref.col[rs:re]), f"job {idx[j]} row {r}"
+            v = C.val[s:e].cpu().numpy()
+            assert np.all(np.abs(v - ref.val[rs:re]) <= 1e-12 * ref.mag[rs:re]), f"job {idx[j]} row {r}"
+    assert sampled >= 3
+    batch.destroy()
+    del dA, dB
+    torch.cuda.empty_cache()
