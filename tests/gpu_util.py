@@ -82,3 +82,24 @@ def compare_all_rows(A, B, C, check, panel_products=2e8):
             val = C.val[s:e].cpu().numpy().astype(np.float64)
             check(ref, rp[r0:r1 + 1] - s, col, val, r0, r1)
     return len(cuts) - 1
+
+
+def check_job_rows(A, B, C, rng, full_max_products=2e7, sample=60, tol=TOL_F64):
+    """A device (or pinned host) product C = A*B against the oracle: every row when the job has
+    at most ``full_max_products`` partial products, else its four heaviest rows and ``sample``
+    seeded others. Returns True when the rows were sampled."""
+    P = oracle.products_per_row(A, B)
+    rp = C.row_ptr.cpu().numpy().astype(np.int64)
+    if P.sum() <= full_max_products:
+        assert_parity(A, B, rp, C.col.cpu().numpy(), C.val.cpu().numpy().astype(np.float64), tol=tol)
+        return False
+    rows = np.unique(np.concatenate([np.argsort(P)[-4:], rng.choice(A.rows, sample, replace=False)]))
+    ref = oracle.spgemm(A, B, rows)
+    for t, r in enumerate(rows):
+        s, e = int(rp[r]), int(rp[r + 1])
+        rs, re = int(ref.row_ptr[t]), int(ref.row_ptr[t + 1])
+        assert e - s == re - rs, f"row {r}: {e - s} entries, oracle {re - rs}"
+        assert np.array_equal(C.col[s:e].cpu().numpy(), ref.col[rs:re]), f"row {r} columns"
+        v = C.val[s:e].cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(v - ref.val[rs:re]) <= tol * ref.mag[rs:re]), f"row {r} values"
+    return True

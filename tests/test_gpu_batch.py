@@ -13,7 +13,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import gpu_or_skip
+from gpu_util import check_job_rows, gpu_or_skip
 
 pytestmark = pytest.mark.gpu
 
@@ -226,24 +226,7 @@ def test_batch_jobs_from_the_full_distribution():
     batch.check()
     torch.cuda.synchronize()
     assert batch.info()["products"] == sum(int(oracle.products_per_row(A, B).sum()) for A, B in jobs)
-    sampled = 0
-    for j, (A, B) in enumerate(jobs):
-        C = batch.result(j)
-        P = oracle.products_per_row(A, B)
-        if P.sum() <= 2e7:
-            _check_job(A, B, C)
-            continue
-        sampled += 1
-        rows = np.unique(np.concatenate([np.argsort(P)[-4:], rng.choice(A.rows, 60, replace=False)]))
-        ref = oracle.spgemm(A, B, rows)
-        rp = C.row_ptr.cpu().numpy().astype(np.int64)
-        for t, r in enumerate(rows):
-            s, e = int(rp[r]), int(rp[r + 1])
-            rs, re = int(ref.row_ptr[t]), int(ref.row_ptr[t + 1])
-            assert e - s == re - rs, f"job {idx[j]} row {r}: {e - s} entries, oracle {re - rs}"
-            assert np.array_equal(C.col[s:e].cpu().numpy(), ref.col[rs:re]), f"job {idx[j]} row {r}"
-            v = C.val[s:e].cpu().numpy()
-            assert np.all(np.abs(v - ref.val[rs:re]) <= 1e-12 * ref.mag[rs:re]), f"job {idx[j]} row {r}"
+    sampled = sum(check_job_rows(A, B, batch.result(j), rng) for j, (A, B) in enumerate(jobs))
     assert sampled >= 3
     batch.destroy()
     del dA, dB

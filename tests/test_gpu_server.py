@@ -16,7 +16,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import gpu_or_skip
+from gpu_util import check_job_rows, gpu_or_skip
 
 pytestmark = pytest.mark.gpu
 
@@ -297,3 +297,36 @@ def test_job_over_the_cap_runs_as_row_panels():
         srv.release(j)
         srv.release(js)
         assert srv.stats()["bytes_in_use"] == 0
+
+
+def test_serving_the_largest_jobs_of_the_request_stream():
+    """Requests as the 20,000-request workload draws them, under its 32 GB cap: the four largest
+    jobs of the 512 it cycles through (up to n = 47,624 and 24 GB of C), the largest 3D Laplacian
+    (g = 128) and 24 other jobs of the 512, served together. Each result is checked and released
+    as it comes out of the completion queue (the cap holds one large result at a time): every row
+    of a job with at most 2e7 partial products, the four heaviest rows and 60 seeded others of a
+    larger one."""
+    import paper_2004_13907_gb300 as sp
+    rng = np.random.default_rng(91)
+    big = [226, 52, 56, 154]
+    others = [int(i) for i in rng.choice(512, 30, replace=False) if int(i) not in big][:24]
+    jobs = [synth.batch_job(i, seed=0) for i in big + others]
+    jobs.append((synth.laplacian3d(128),) * 2)
+    assert jobs[0][0].rows == 47_624
+    dev = [(sp.DeviceCSR.from_host(A, "cuda"), sp.DeviceCSR.from_host(B, "cuda")) for A, B in jobs]
+    cap = 32 << 30
+    with sp.Server(mem_cap_bytes=cap, start_paused=1) as srv:
+        ids = [srv.submit(dA, dB) for dA, dB in dev]
+        srv.resume()
+        sampled = 0
+        for _ in ids:
+            j = srv.wait_any(timeout=300)
+            assert j is not None, "no job finished for 300 s"
+            assert srv.poll(j)["state"] == "done"
+            A, B = jobs[ids.index(j)]
+            sampled += check_job_rows(A, B, srv.result(j), rng)
+            srv.release(j)
+        st = srv.stats()
+        assert st["completed"] == len(jobs) and st["failed"] == 0 and st["rejected"] == 0
+        assert st["bytes_peak"] <= cap and st["bytes_in_use"] == 0
+    assert sampled >= 4
