@@ -530,9 +530,11 @@ def run_ours(args):
                 "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": bytes_,
-                "launch_ms": round(dom_ms, 4), "traffic": _traffic(bytes_),
-                "traffic_source": "R-MAT 2^17 DRAM bytes per algorithmic byte (profiles/k_num_window_rmat17.md) x "
-                                  "this launch's algorithmic bytes; B fits L2 at 2^17, so a lower bound here"}
+                "launch_ms": round(dom_ms, 4), "traffic": None, "traffic_source": None}
+        if all(p == "f64" for p in precs.values()):
+            roof["traffic"] = _traffic(bytes_)
+            roof["traffic_source"] = ("R-MAT 2^17 DRAM bytes per algorithmic byte (profiles/k_num_window_rmat17.md) x "
+                                      "this launch's algorithmic bytes; B fits L2 at 2^17, so a lower bound here")
         if all(p == "f64" for p in precs.values()):
             roof.update(_fp64_pipe(wprods, dom_ms,
                                    torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count,
