@@ -180,6 +180,7 @@ spgemm_status spgemm_plan(const spgemm_csr_in* A, const spgemm_csr_in* B, spgemm
   if (st != SPGEMM_OK) {
     const std::string msg = g_last_error;
     cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    release_small_host(p);
     destroy_events(p);
     p->ws.release_all();
     delete p;
@@ -278,6 +279,7 @@ spgemm_status spgemm_plan_get_timings(spgemm_plan_t* plan, spgemm_timings* t) {
 
 spgemm_status spgemm_plan_destroy(spgemm_plan_t* plan) {
   if (!plan) return SPGEMM_OK;
+  release_small_host(plan);
   destroy_events(plan);
   plan->ws.release_all();
   delete plan;

@@ -324,7 +324,8 @@ template <int PER>
 __global__ void __launch_bounds__(kSymWarps * 32) k_small_sym(SmallCsr A, SmallCsr B, int32_t width, int check,
                                                               int64_t run, int G, int32_t* __restrict__ nnz_row,
                                                               int32_t* __restrict__ loc,
-                                                              int64_t* __restrict__ blk, Summary* sum) {
+                                                              int64_t* __restrict__ blk, Summary* sum,
+                                                              Summary* hsum) {
   extern __shared__ __align__(16) unsigned char small_smem[];
   __shared__ int64_t s_scan[33];
   __shared__ int32_t s_cnt[kRunShared];
@@ -433,6 +434,16 @@ __global__ void __launch_bounds__(kSymWarps * 32) k_small_sym(SmallCsr A, SmallC
   if (threadIdx.x == 0) {
     blk[gridDim.x] = total;
     sum->total = total;
+    if (hsum) {
+      // every other block's updates of the summary came before its ticket: read them where the
+      // atomics ran (atomics with identity operands) and store what the host reads into mapped
+      // page-locked memory, so the host needs no copy after the kernel
+      hsum->err = atomicOr(&sum->err, 0u);
+      hsum->small_flags = atomicOr(&sum->small_flags, 0u);
+      hsum->small_products = atomicAdd(&sum->small_products, 0ull);
+      hsum->max_row = static_cast<int64_t>(atomicMax(reinterpret_cast<unsigned long long*>(&sum->max_row), 0ull));
+      hsum->total = total;
+    }
   }
 }
 
@@ -580,8 +591,8 @@ int per_index(int per) { return __builtin_ctz(static_cast<unsigned>(per)); }
 
 template <int PER>
 void sym_launch(dim3 g, size_t smem, cudaStream_t s, const SmallCsr& A, const SmallCsr& B, int32_t width, int check,
-                int64_t run, int G, int32_t* nnz_row, int32_t* loc, int64_t* blk, Summary* sum) {
-  k_small_sym<PER><<<g, kSymWarps * 32, smem, s>>>(A, B, width, check, run, G, nnz_row, loc, blk, sum);
+                int64_t run, int G, int32_t* nnz_row, int32_t* loc, int64_t* blk, Summary* sum, Summary* hsum) {
+  k_small_sym<PER><<<g, kSymWarps * 32, smem, s>>>(A, B, width, check, run, G, nnz_row, loc, blk, sum, hsum);
 }
 
 template <int PER>
@@ -697,13 +708,14 @@ SmallGrid small_sym_grid(const SmallCsr& A, int64_t width, int num_sms) {
 }
 
 int launch_small_symbolic(const SmallCsr& A, const SmallCsr& B, int64_t width, SmallGrid g, int check,
-                          int32_t* nnz_row, int32_t* loc, int64_t* blk, Summary* sum, cudaStream_t s) {
+                          int32_t* nnz_row, int32_t* loc, int64_t* blk, Summary* sum, Summary* hsum,
+                          cudaStream_t s) {
   const int per = small_per(width);
   const dim3 grid(static_cast<unsigned>(g.blocks));
   const size_t smem = sym_smem(per, g.groups);
   const int G = g.groups;
   const int32_t w = static_cast<int32_t>(width);
-#define SPG_SYM(P) sym_launch<P>(grid, smem, s, A, B, w, check, g.run, G, nnz_row, loc, blk, sum)
+#define SPG_SYM(P) sym_launch<P>(grid, smem, s, A, B, w, check, g.run, G, nnz_row, loc, blk, sum, hsum)
   switch (per) {
     case 1: SPG_SYM(1); break;
     case 2: SPG_SYM(2); break;

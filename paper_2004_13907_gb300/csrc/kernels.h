@@ -38,6 +38,7 @@ constexpr int64_t kSmallMaxRows = 65536;
 constexpr int64_t kSmallMaxCols = 32768;
 constexpr int64_t kSmallMaxBatchRows = int64_t(1) << 24;
 constexpr int kSmallCap = 1024;
+constexpr uint32_t kSmallUnwritten = 0x80000000u;   // small_flags of a host summary no kernel stored
 // A CSR input with its row pointers as the caller stores them.
 struct SmallCsr {
   int64_t rows, cols, nnz;
@@ -58,9 +59,12 @@ SmallGrid small_sym_grid(const SmallCsr& A, int64_t width, int num_sms);
 // Symbolic pass, validation of A and B (when `check`) and the offsets of C's rows, in one kernel:
 // nnz_row[i], loc[i] (row i's offset within its block's run), blk[b] (run b's offset, b <= blocks,
 // blk[blocks] = nnz(C)), summary->total (nnz(C)), max_row (longest row of C), small_products,
-// small_flags, err. The summary must start zeroed.
+// small_flags, err. The summary must start zeroed. hsum (may be null): mapped page-locked memory
+// (as a device pointer) that receives err, small_flags, small_products, max_row and total once
+// the kernel ends.
 int launch_small_symbolic(const SmallCsr& A, const SmallCsr& B, int64_t width, SmallGrid g, int check,
-                          int32_t* nnz_row, int32_t* loc, int64_t* blk, Summary* sum, cudaStream_t s);
+                          int32_t* nnz_row, int32_t* loc, int64_t* blk, Summary* sum, Summary* hsum,
+                          cudaStream_t s);
 // c_off[i] = offset of row i of C (i <= m) from the symbolic kernel's runs (a stacked batch reads them).
 int launch_small_offsets(const int32_t* loc, const int64_t* blk, SmallGrid g, int64_t m, int64_t* c_off,
                          cudaStream_t s);

@@ -96,6 +96,13 @@ spgemm_status read_small(void* dst, const void* src, size_t bytes, cudaStream_t 
   return SPGEMM_OK;
 }
 
+void release_small_host(spgemm_plan_s* p) {
+  if (!p->small_host) return;
+  cudaStreamSynchronize(static_cast<cudaStream_t>(p->ws.stream));
+  stage_give(p->small_host);
+  p->small_host = nullptr;
+}
+
 spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s) {
   Summary h;
   spgemm_status st = read_summary(p, &h, s);
@@ -198,11 +205,26 @@ spgemm_status plan_small(spgemm_plan_s* p, const spgemm_csr_in* A, const spgemm_
   cudaMemsetAsync(p->summary, 0, sizeof(Summary), s);
   stage_end(p, SPGEMM_STAGE_VALIDATE, 0, s);
   if ((st = cuda_status(cudaGetLastError(), "clearing the plan summary")) != SPGEMM_OK) return st;
+  // the summary's host copy: the symbolic kernel's last block stores it into a mapped staging
+  // block, so spgemm_symbolic reads it after one wait, with no copy; small_flags starts at a value
+  // the kernel never writes, so a summary the kernel did not store is caught
+  Summary* hsum = nullptr;
+  if (!p->small_host) p->small_host = stage_take();
+  if (p->small_host) {
+    if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&hsum), p->small_host, 0) == cudaSuccess) {
+      static_cast<Summary*>(p->small_host)->small_flags = kSmallUnwritten;
+    } else {
+      cudaGetLastError();
+      stage_give(p->small_host);
+      p->small_host = nullptr;
+      hsum = nullptr;
+    }
+  }
   // the symbolic kernel starts now, on the plan's stream: spgemm_symbolic only reads its summary
   stage_begin(p, SPGEMM_STAGE_SYM_WARP, s);
   const int nl = launch_small_symbolic(small_csr(p->a_in, p->abase), small_csr(p->b_in), small_width(p),
                                        p->small_grid, p->opts.validate, p->nnz_row, p->small_loc, p->small_blk,
-                                       p->summary, s);
+                                       p->summary, hsum, s);
   stage_end(p, SPGEMM_STAGE_SYM_WARP, nl, s);
   if ((st = cuda_status(cudaGetLastError(), "launching the small-product symbolic pass")) != SPGEMM_OK) return st;
   p->state = 0;
@@ -347,7 +369,16 @@ spgemm_status symbolic_run(spgemm_plan_s* p, cudaStream_t s) {
     // the plan launched the symbolic kernel on its own stream; read its summary there (the host
     // wait orders every later stream after it)
     Summary h;
-    if ((st = read_summary(p, &h, static_cast<cudaStream_t>(p->ws.stream))) != SPGEMM_OK) return st;
+    if (p->small_host) {
+      const cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(p->ws.stream));
+      if (e != cudaSuccess) return cuda_status(e, "waiting for the small-product symbolic pass");
+      std::memcpy(&h, p->small_host, sizeof(Summary));
+      release_small_host(p);
+      if (h.small_flags == kSmallUnwritten)
+        return set_error_msg(SPGEMM_ERR_INTERNAL, "the small-product symbolic pass left no summary");
+    } else if ((st = read_summary(p, &h, static_cast<cudaStream_t>(p->ws.stream))) != SPGEMM_OK) {
+      return st;
+    }
     if (h.err) return error_bits_status(h.err);
     if (h.small_flags) {
       // a row of C is too long for the small path: plan and count again through the row classes

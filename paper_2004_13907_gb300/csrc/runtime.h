@@ -80,6 +80,7 @@ struct spgemm_plan_s {
   int32_t* small_loc = nullptr;      // small path: row offsets within their run
   int64_t* small_blk = nullptr;      // small path: offsets of the runs (and nnz(C) last)
   spgemm_csr_in a_in{}, b_in{};      // small path: the inputs as the caller gave them
+  void* small_host = nullptr;        // small path: mapped staging block the symbolic kernel writes its summary to
   int32_t* rerun_list = nullptr;
   int64_t sym_off[spg::kMaxClasses + 1] = {};
   int64_t num_off[spg::kMaxClasses + 1] = {};
@@ -112,6 +113,9 @@ spgemm_status read_device_error(spgemm_plan_s* p, cudaStream_t s);
 // copy in flight); `launches` (may be null) counts the kernel.
 spgemm_status read_small(void* dst, const void* src, size_t bytes, cudaStream_t s, int64_t* launches,
                          const char* what);
+// Gives a small plan's summary staging block back (after waiting for the plan's stream while its
+// symbolic kernel may still write to it).
+void release_small_host(spgemm_plan_s* p);
 // Below this many micro rows (at most 8 A entries and 32 partial products) the rows take the
 // warp-per-row tiny kernels instead of the thread-per-row merge, whose dependent loads make it
 // pay only when many rows run at once.
