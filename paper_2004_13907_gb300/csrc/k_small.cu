@@ -435,13 +435,17 @@ __global__ void __launch_bounds__(kSymWarps * 32) k_small_sym(SmallCsr A, SmallC
     blk[gridDim.x] = total;
     sum->total = total;
     if (hsum) {
-      // every other block's updates of the summary came before its ticket: read them where the
-      // atomics ran (atomics with identity operands) and store what the host reads into mapped
-      // page-locked memory, so the host needs no copy after the kernel
-      hsum->err = atomicOr(&sum->err, 0u);
-      hsum->small_flags = atomicOr(&sum->small_flags, 0u);
-      hsum->small_products = atomicAdd(&sum->small_products, 0ull);
-      hsum->max_row = static_cast<int64_t>(atomicMax(reinterpret_cast<unsigned long long*>(&sum->max_row), 0ull));
+      // every other block's updates of the summary came before its ticket (and this block's fence
+      // after it): read them from L2, where the atomics ran, as independent loads, and store what
+      // the host reads into mapped page-locked memory, so the host needs no copy after the kernel
+      const uint32_t e = __ldcg(&sum->err);
+      const uint32_t f = __ldcg(&sum->small_flags);
+      const unsigned long long pr = __ldcg(&sum->small_products);
+      const long long mr = __ldcg(reinterpret_cast<const long long*>(&sum->max_row));
+      hsum->err = e;
+      hsum->small_flags = f;
+      hsum->small_products = pr;
+      hsum->max_row = mr;
       hsum->total = total;
     }
   }
