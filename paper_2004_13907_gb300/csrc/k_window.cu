@@ -35,7 +35,6 @@ namespace spg {
 namespace {
 
 constexpr int kRankCap = 4096;                     // entries of C per window (>= kBlockCols)
-constexpr int kGroupWords = 64;                    // words per prefix group
 constexpr int kNumThreads = 512;                   // threads of the windowed numeric kernel
 constexpr int kCntCache = 1024;                    // block counts kept in shared memory
 constexpr int kMaxWin = 256;                       // windows planned per batch
@@ -54,14 +53,11 @@ struct WinGeom {
   static constexpr int kWordsPerThread = kSpanWords / kNumThreads;
   static constexpr int kSmemBits = kSpanWords * 4;
   static constexpr int kSmemPre = kSpanWords * 2;
-  static constexpr int kSmemGrp = (kSpanWords / kGroupWords) * 4;
   static constexpr int kValBytes = kWide ? 16 : 8;
   static constexpr int kSmemVals = kRankCap * kValBytes;
-  static constexpr int kSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemGrp + kSmemEnt + kCntCache * 2 +
-                                    kMaxWin * 12;
+  static constexpr int kSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemEnt + kCntCache * 2 + kMaxWin * 12;
   static constexpr int kBlocksPerSm = 2;
   static_assert(kWordsPerThread * kNumThreads == kSpanWords, "words per thread");
-  static_assert(kGroupWords % kWordsPerThread == 0, "a thread's words lie in one group");
   static_assert(kWordsPerThread % 4 == 0, "a thread's words are copied as 16-byte vectors");
   static_assert(kSmemVals % 16 == 0, "vector clearing of the values");
   static_assert(2 * (kSmemBytes + 1024 + 512) <= 228 * 1024, "two blocks per SM");
@@ -134,7 +130,6 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
   using G = WinGeom<Mode>;
   constexpr int kSmemBits = G::kSmemBits;
   constexpr int kSmemPre = G::kSmemPre;
-  constexpr int kSmemGrp = G::kSmemGrp;
   constexpr int kSpanBlocks = G::kSpanBlocks;
   constexpr int kWordsPerThread = G::kWordsPerThread;
   constexpr int kSmemVals = WinGeom<Mode>::kSmemVals;
@@ -150,9 +145,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
   int32_t* x_lt = reinterpret_cast<int32_t*>(x_l2 + kRankCap); //   signed top limb
   int32_t* colbuf = reinterpret_cast<int32_t*>(win_smem);
   uint32_t* bm = reinterpret_cast<uint32_t*>(win_smem + kSmemVals);
-  uint16_t* pre = reinterpret_cast<uint16_t*>(win_smem + kSmemVals + kSmemBits);
-  int32_t* grp = reinterpret_cast<int32_t*>(win_smem + kSmemVals + kSmemBits + kSmemPre);
-  unsigned char* ent = win_smem + kSmemVals + kSmemBits + kSmemPre + kSmemGrp;
+  uint16_t* pre = reinterpret_cast<uint16_t*>(win_smem + kSmemVals + kSmemBits);   // rank base of each word
+  unsigned char* ent = win_smem + kSmemVals + kSmemBits + kSmemPre;
   int64_t* e_rs = reinterpret_cast<int64_t*>(ent);                 // B row start
   double* e_av = reinterpret_cast<double*>(e_rs + kNumThreads);    // a_ik
   int64_t* c_bs = reinterpret_cast<int64_t*>(e_av + kNumThreads);  // segment start in B
@@ -462,15 +456,14 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
           } else {
             tpre = block_excl_scan<int32_t>(c, s_scan32, &tot);
           }
-          constexpr int kThreadsPerGroup = kGroupWords / kWordsPerThread;
-          const int lead = lane & ~(kThreadsPerGroup - 1);
-          const int32_t gbase = __shfl_sync(0xffffffffu, tpre, lead);
+          // each word's rank base, absolute in the window (a rank past 65,535 saturates there: any
+          // rank at or beyond kRankCap is skipped alike), so a product's rank takes two shared
+          // loads, its bitmap word and its base
           if (mine) {
-            if ((threadIdx.x & (kThreadsPerGroup - 1)) == 0) grp[wlo / kGroupWords] = gbase;
-            int run = tpre - gbase;
+            int run = tpre;
 #pragma unroll
             for (int t = 0; t < kWordsPerThread; ++t) {
-              pre[wlo + t] = static_cast<uint16_t>(run);
+              pre[wlo + t] = static_cast<uint16_t>(run < 65535 ? run : 65535);
               run += __popc(wv[t]);
             }
           }
@@ -533,7 +526,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
                   set_error(err, kErrWindowPlan);
                   continue;
                 }
-                const int r = grp[wd / kGroupWords] + pre[wd] + __popc(word & ((1u << (rel & 31)) - 1u));
+                const int r = pre[wd] + __popc(word & ((1u << (rel & 31)) - 1u));
                 if (r >= kRankCap) continue;
                 if constexpr (Mode == kModeF32C) {
                   // error-free product a*b = ph + pl (TwoProduct with fmaf); the sum's own rounding
@@ -618,7 +611,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
             uint32_t m = bm[w];
             if (!m) continue;
             bm[w] = 0u;
-            int r = grp[w / kGroupWords] + pre[w];
+            int r = pre[w];
             for (; m; m &= m - 1) {
               if (r < kRankCap) colbuf[r] = static_cast<int32_t>(w0 - cb + w * 32 + (__ffs(m) - 1));
               ++r;
