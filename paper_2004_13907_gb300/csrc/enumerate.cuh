@@ -279,7 +279,7 @@ __device__ __forceinline__ void block_range_for_each_product(const DevCsr& A, co
           for (int u = 0; u < U; ++u) j[u] = j0 + 32 * u;
         } else {
           int unused[U];
-          walk.step_many<U>(p0, hi, j, unused);
+          walk.template step_many<U>(p0, hi, j, unused);
         }
         f(j);
       }

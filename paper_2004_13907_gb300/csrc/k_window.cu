@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
                 for (int u = 0; u < kUnroll; ++u) j[u] = j0 + 32 * u;
               } else {
                 int unused[kUnroll];
-                walk.step_many<kUnroll>(p0, hi, j, unused);
+                walk.template step_many<kUnroll>(p0, hi, j, unused);
               }
               int32_t c[kUnroll];
 #pragma unroll
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
                   av[u] = walk.oval;
                 }
               } else {
-                walk.step_many<kUnroll>(p0, hi, j, av);
+                walk.template step_many<kUnroll>(p0, hi, j, av);
               }
               int32_t c[kUnroll];
               double bv[kUnroll];
