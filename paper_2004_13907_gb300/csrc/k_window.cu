@@ -55,7 +55,9 @@ struct WinGeom {
   static constexpr int kSmemPre = kSpanWords * 2;
   static constexpr int kValBytes = kWide ? 16 : 8;
   static constexpr int kSmemVals = kRankCap * kValBytes;
-  static constexpr int kSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemEnt + kCntCache * 2 + kMaxWin * 12;
+  static constexpr int kSmemBytes = kSmemVals + kSmemBits + kSmemPre + kSmemEnt + kCntCache * 2 + kMaxWin * 12 +
+                                    (kMaxWin + 1) * 4;
+  static_assert(kSmemPre >= 2 * kMaxWin * 4, "the list counters fit the rank bases' space");
   static constexpr int kBlocksPerSm = 2;
   static_assert(kWordsPerThread * kNumThreads == kSpanWords, "words per thread");
   static_assert(kWordsPerThread % 4 == 0, "a thread's words are copied as 16-byte vectors");
@@ -126,7 +128,8 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
     void* __restrict__ cval_, int32_t* __restrict__ row_flag, const int32_t* __restrict__ abase,
     const int32_t* __restrict__ awidth, int64_t width_all, const uint32_t* __restrict__ wbits,
     const int64_t* __restrict__ woff, const uint16_t* __restrict__ bexp, const int32_t* __restrict__ dev_count,
-    const int32_t* __restrict__ negflag, uint32_t* err) {
+    const int32_t* __restrict__ negflag, int64_t* __restrict__ list_bs, int32_t* __restrict__ list_len,
+    double* __restrict__ list_av, int64_t list_cap, uint32_t* err) {
   using G = WinGeom<Mode>;
   constexpr int kSmemBits = G::kSmemBits;
   constexpr int kSmemPre = G::kSmemPre;
@@ -157,6 +160,7 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
   int32_t* w_b0 = reinterpret_cast<int32_t*>(s_cnt + kCntCache);
   int32_t* w_b1 = w_b0 + kMaxWin;
   int32_t* w_cnt = w_b1 + kMaxWin;
+  int32_t* w_loff = w_cnt + kMaxWin;    // a long row's window list offsets (kMaxWin + 1)
   __shared__ long long s_scan64[33];
   __shared__ int32_t s_scan32[33];
   __shared__ int32_t s_ctl[8];
@@ -216,6 +220,38 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
       }
       bs = rs + s0;
       len = s1 - s0;
+    }
+    const long long packed = (static_cast<long long>(len > 0) << 32) | static_cast<long long>(len);
+    long long tot;
+    const long long ex = block_excl_scan<long long>(packed, s_scan64, &tot);
+    if (len > 0) {
+      const int pos = static_cast<int>(ex >> 32);
+      c_bs[pos] = bs;
+      c_excl[pos] = static_cast<int32_t>(ex & 0xffffffffLL);
+      c_ent[pos] = threadIdx.x;
+    }
+    if (threadIdx.x == 0) {
+      const int nent = static_cast<int>(tot >> 32);
+      c_excl[nent] = static_cast<int32_t>(tot & 0xffffffffLL);
+      s_ctl[6] = nent;
+      s_ctl[7] = static_cast<int32_t>(tot & 0xffffffffLL);
+    }
+    __syncthreads();
+  };
+  // This block's lists of a long row's window segments (list_cap entries each; none when null).
+  int64_t* const l_bs = list_cap > 0 ? list_bs + int64_t(blockIdx.x) * list_cap : nullptr;
+  int32_t* const l_len = list_cap > 0 ? list_len + int64_t(blockIdx.x) * list_cap : nullptr;
+  double* const l_av = list_cap > 0 ? list_av + int64_t(blockIdx.x) * list_cap : nullptr;
+  // Pass-2 chunk [base, base + kNumThreads) of a window's list (ending at end), compacted as
+  // build_chunk does; every listed segment is non-empty.
+  auto build_list_chunk = [&](int64_t base, int64_t end) {
+    const int64_t q = base + threadIdx.x;
+    int64_t bs = 0;
+    int32_t len = 0;
+    if (q < end) {
+      bs = l_bs[q];
+      len = l_len[q];
+      e_av[threadIdx.x] = l_av[q];
     }
     const long long packed = (static_cast<long long>(len > 0) << 32) | static_cast<long long>(len);
     long long tot;
@@ -343,6 +379,64 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
       __syncthreads();
       const int nwin = s_ctl[1];
       if (nwin == 0) break;
+      // A row that is not resident lists its segments per planned window once for the batch: a
+      // warp takes one entry at a time and its lanes the windows, reading the entry's split
+      // offsets at the windows' bounds from the entry's row of the split table (coalesced). An
+      // entry with nothing in a window stays out of that window's list, so pass 2 builds chunks
+      // only from what each window holds. The counters live in the rank bases' space, which
+      // every window rewrites; a batch whose lists exceed list_cap keeps the chunks of A entries.
+      bool listed = false;
+      if (Mode != kModeF64X && !resident && split != nullptr && list_cap > 0) {
+        int32_t* s_wcnt = reinterpret_cast<int32_t*>(pre);
+        int32_t* s_wfill = s_wcnt + kMaxWin;
+        for (int w = threadIdx.x; w < nwin; w += kNumThreads) {
+          s_wcnt[w] = 0;
+          s_wfill[w] = 0;
+        }
+        __syncthreads();
+        for (int64_t e = wid; e < na; e += kWarps) {
+          const int32_t* sp = split + int64_t(A.col[a0 + e]) * (nblocks + 1);
+          for (int w = lane; w < nwin; w += 32)
+            if (sp[w_b1[w]] > sp[w_b0[w]]) atomicAdd(&s_wcnt[w], 1);
+        }
+        __syncthreads();
+        if (wid == 0) {
+          int32_t run = 0;
+          for (int wb = 0; wb < nwin; wb += 32) {
+            const int w = wb + lane;
+            const int32_t c = w < nwin ? s_wcnt[w] : 0;
+            int32_t incl = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+              const int32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+              if (lane >= d) incl += v;
+            }
+            if (w < nwin) w_loff[w] = run + incl - c;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+          }
+          if (lane == 0) w_loff[nwin] = run;
+        }
+        __syncthreads();
+        listed = w_loff[nwin] <= list_cap;
+        if (listed) {
+          for (int64_t e = wid; e < na; e += kWarps) {
+            const int32_t k = A.col[a0 + e];
+            const int32_t* sp = split + int64_t(k) * (nblocks + 1);
+            const int64_t rs = B.rp[k];
+            const double av = a_at(a0 + e);
+            for (int w = lane; w < nwin; w += 32) {
+              const int32_t s0 = sp[w_b0[w]], s1 = sp[w_b1[w]];
+              if (s1 > s0) {
+                const int32_t pos = w_loff[w] + atomicAdd(&s_wfill[w], 1);
+                l_bs[pos] = rs + s0;
+                l_len[pos] = s1 - s0;
+                l_av[pos] = av;
+              }
+            }
+          }
+        }
+        __syncthreads();
+      }
       for (int wi = 0; wi < nwin; ++wi) {
         const int64_t b0 = w_b0[wi], b1 = w_b1[wi];
         const int64_t w0 = cb + b0 * kBlockCols;
@@ -481,8 +575,10 @@ __global__ void __launch_bounds__(kNumThreads, WinGeom<Mode>::kBlocksPerSm) k_nu
             asm volatile("prefetch.global.L2 [%0];" ::"l"(wbits + toff + nb0 * kBlockWords + wlo));
         }
         // pass 2: accumulate a_ik * b_kj by rank
-        for (int64_t base = 0; base < na; base += kNumThreads) {
-          if (na > kNumThreads || (stored && !fused)) build_chunk(a0, na, base, resident, b0, b1, w0, w1, ps0, ps1);
+        const int64_t p2_lo = listed ? w_loff[wi] : 0, p2_hi = listed ? w_loff[wi + 1] : na;
+        for (int64_t base = p2_lo; base < p2_hi; base += kNumThreads) {
+          if (listed) build_list_chunk(base, p2_hi);
+          else if (na > kNumThreads || (stored && !fused)) build_chunk(a0, na, base, resident, b0, b1, w0, w1, ps0, ps1);
           const int nent = s_ctl[6];    // a resident row's single chunk: from pass 1 or the prefix scan
           const int32_t total = s_ctl[7];
           int32_t per = (total + kWarps - 1) / kWarps;
@@ -813,13 +909,18 @@ int launch_bsplit(const DevCsr& B, int64_t nblocks, const int32_t* bbase, int32_
   return 1;
 }
 
+int64_t num_window_blocks(int64_t count, int num_sms) {
+  return count < int64_t(2) * num_sms ? count : int64_t(2) * num_sms;
+}
+
 int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t* perm, int64_t count,
                       int32_t* counter, const int64_t* c_off, const int32_t* win_slot,
                       const uint16_t* blockcnt, int64_t nblocks, int64_t nslots, const int32_t* split,
                       int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag,
                       const int32_t* abase, const int32_t* awidth, int64_t width, const uint32_t* wbits,
                       const int64_t* woff, const uint16_t* bexp, const int32_t* dev_count,
-                      const int32_t* negflag, int num_sms, uint32_t* err, cudaStream_t s) {
+                      const int32_t* negflag, int64_t* list_bs, int32_t* list_len, double* list_av,
+                      int64_t list_cap, int num_sms, uint32_t* err, cudaStream_t s) {
   if (count <= 0) return 0;
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   auto go = [&](auto kernel, int smem, int per_sm) {
@@ -828,7 +929,8 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
     kernel<<<static_cast<unsigned>(g), kNumThreads, smem, s>>>(A, B, perm, count, counter, c_off, win_slot,
                                                                blockcnt, nblocks, nslots, split, merge_cap,
                                                                ccol, cval, row_flag, abase, awidth, width, wbits,
-                                                               woff, bexp, dev_count, negflag, err);
+                                                               woff, bexp, dev_count, negflag, list_bs, list_len,
+                                                               list_av, list_cap, err);
   };
   if (mode == kModeF32C) go(k_num_window<kModeF32C>, WinGeom<kModeF32C>::kSmemBytes, 2);
   else if (mode == kModeF32R) go(k_num_window<kModeF32R>, WinGeom<kModeF32R>::kSmemBytes, 2);

@@ -161,7 +161,11 @@ int launch_num_window(int mode, const DevCsr& A, const DevCsr& B, const int32_t*
                       int32_t merge_cap, int32_t* ccol, void* cval, int32_t* row_flag,
                       const int32_t* abase, const int32_t* awidth, int64_t width, const uint32_t* wbits,
                       const int64_t* woff, const uint16_t* bexp, const int32_t* dev_count,
-                      const int32_t* negflag, int num_sms, uint32_t* err, cudaStream_t s);
+                      const int32_t* negflag, int64_t* list_bs, int32_t* list_len, double* list_av,
+                      int64_t list_cap, int num_sms, uint32_t* err, cudaStream_t s);
+// Blocks of k_num_window for `count` rows (its grid), and the entries each block's window lists of
+// a row with more than 512 A entries can hold (list_cap; 0 turns the lists off).
+int64_t num_window_blocks(int64_t count, int num_sms);
 // *flag = 1 if a value of the FP32 arrays a[na] or b[nb] is negative, infinite or NaN, else 0.
 int launch_negative_check(const void* a, int64_t na, const void* b, int64_t nb, int32_t* flag, int num_sms,
                           cudaStream_t s);

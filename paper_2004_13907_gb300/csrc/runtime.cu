@@ -481,6 +481,26 @@ void plan_bytes_bounds(int64_t m, int64_t a_nnz, int64_t width, int a_rowptr32, 
   *hi = fixed + tiles + window;
 }
 
+namespace {
+
+// Entries of each windowed-kernel block's window lists (rows with more than 512 A entries list
+// their segments per window; a batch of windows whose lists exceed this keeps chunks of A entries):
+// 16 per A entry of the windowed rows, spread over the blocks, at most 2^20 (20 MB a block). None
+// for the exact fixed-point mode or without a split table.
+constexpr int64_t kListCapMax = int64_t(1) << 20;
+constexpr int64_t kListBytesPerEntry = 8 + 4 + 8;
+
+int64_t window_list_cap(const spgemm_plan_s* p, int64_t nwin) {
+  if (nwin <= 0 || (p->prec == SPGEMM_F64 && p->opts.fp64_accumulate != 0)) return 0;
+  unsigned long long annz = 0;
+  for (int c = kNumWin0; c <= kNumWin3; ++c) annz += p->cls_sums[c][1];
+  if (annz <= 512) return 0;
+  const int64_t cap = static_cast<int64_t>(annz) * 16 / num_window_blocks(nwin, p->num_sms);
+  return cap < kListCapMax ? cap : kListCapMax;
+}
+
+}  // namespace
+
 int64_t numeric_extra_bytes(const spgemm_plan_s* p) {
   const int64_t m = p->A.rows;
   if (m <= 0) return 0;
@@ -497,7 +517,13 @@ int64_t numeric_extra_bytes(const spgemm_plan_s* p) {
   }
   if (nwin > 0 && !p->split_tried) {
     const int64_t bytes = split_table_bytes(p->B.rows, p->nblocks);
-    if (bytes <= (int64_t(p->opts.window_split_max_mb) << 20)) extra += ws_rounded(bytes);
+    if (bytes <= (int64_t(p->opts.window_split_max_mb) << 20)) {
+      extra += ws_rounded(bytes);
+      if (!p->lists_tried) {
+        const int64_t n = num_window_blocks(nwin, p->num_sms) * window_list_cap(p, nwin);
+        if (n > 0) extra += ws_rounded(8 * n) + ws_rounded(4 * n) + ws_rounded(8 * n);
+      }
+    }
   }
   return extra;
 }
@@ -572,10 +598,23 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
         if (p->split) nl += launch_bsplit(p->B, p->nblocks, p->bbase, p->split, s);
       }
     }
+    if (nwin > 0 && !p->lists_tried && !fx) {
+      p->lists_tried = true;
+      const int64_t cap = p->split ? window_list_cap(p, nwin) : 0;
+      const int64_t n = num_window_blocks(nwin, p->num_sms) * cap;
+      if (n > 0) {
+        p->list_bs = static_cast<int64_t*>(p->ws.get(static_cast<size_t>(8 * n)));
+        p->list_len = static_cast<int32_t*>(p->ws.get(static_cast<size_t>(4 * n)));
+        p->list_av = static_cast<double*>(p->ws.get(static_cast<size_t>(8 * n)));
+        if (p->list_bs && p->list_len && p->list_av) p->list_cap = cap;
+      }
+    }
     nl += launch_num_window(fx ? kModeF64X : mode, p->A, p->B, seg(kNumWin0), nwin, p->counters + 1, p->c_off,
                             p->win_slot, p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col,
                             C->val, p->rerun_flag, p->abase, p->awidth, p->width, p->wbits, p->woff, p->bexp,
-                            nullptr, f32c ? p->counters + 8 : nullptr, p->num_sms, err, s);
+                            nullptr, f32c ? p->counters + 8 : nullptr, fx ? nullptr : p->list_bs,
+                            fx ? nullptr : p->list_len, fx ? nullptr : p->list_av, fx ? 0 : p->list_cap, p->num_sms,
+                            err, s);
     if (fx && nwin > 0) {
       // rows outside the fixed-point range (a very wide spread of product magnitudes, subnormal or
       // non-finite values) are redone with FP64 shared atomics; the list stays on the device
@@ -583,7 +622,7 @@ spgemm_status numeric_run(spgemm_plan_s* p, spgemm_csr_out* C, cudaStream_t s) {
       nl += launch_num_window(kModeF64, p->A, p->B, p->rerun_list, nwin, p->counters + 7, p->c_off, p->win_slot,
                               p->blockcnt, p->nblocks, nslots, p->split, p->opts.window_hash_fill, C->col, C->val,
                               nullptr, p->abase, p->awidth, p->width, p->wbits, p->woff, nullptr, p->counters + 6,
-                              nullptr, p->num_sms, err, s);
+                              nullptr, nullptr, nullptr, nullptr, 0, p->num_sms, err, s);
       p->fx_rerun_pending = true;
     }
     stage_end(p, SPGEMM_STAGE_NUM_WINDOW, nl, s);

@@ -70,6 +70,11 @@ struct spgemm_plan_s {
   const int32_t* bbase = nullptr;
   int64_t width = 0;
   bool split_tried = false;
+  bool lists_tried = false;        // windowed rows: lists of long rows' window segments
+  int64_t* list_bs = nullptr;
+  int32_t* list_len = nullptr;
+  double* list_av = nullptr;
+  int64_t list_cap = 0;           // entries per block of the windowed kernel
   // FP32-compensated path
   int32_t* rerun_flag = nullptr;     // per row: 1 = recompute in FP64
   uint16_t* bexp = nullptr;          // largest biased exponent per row of B (exact FP64 accumulation)
