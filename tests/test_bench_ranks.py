@@ -97,3 +97,29 @@ def test_fp64_pipe_fraction():
     assert abs(r["fp64_frac"] - 0.2757) < 1e-3
     assert abs(r["fp64_floor_ms"] - 66.49) < 0.01
     assert bench._fp64_pipe(1, 1.0, 1, None)["fp64_peak_ops_per_s"] == 2.0 * 2070e6
+
+
+def test_algorithmic_bytes_follow_the_value_width():
+    """The numeric pass's algorithmic bytes: A rows (8 per row pointer pair), per A entry its column,
+    value and the named B row's bounds, per partial product the gathered B column and value, per
+    entry of C its column and value, with 8-byte (FP64) or 4-byte (FP32) values."""
+    sys.path.insert(0, ROOT)
+    import bench
+    info = {"num_class_rows": [2, 3, 0, 0] + [7] * 12, "num_class_annz": [10, 20, 0, 0] + [5] * 12,
+            "num_class_products": [100, 300, 0, 0] + [9] * 12, "num_class_cnnz": [40, 60, 0, 0] + [3] * 12,
+            "products": 400 + 9 * 12, "nnz_c": 100 + 3 * 12}
+    # windowed classes only (the first four)
+    b64, p64 = bench._window_bytes(info, 8)
+    b32, p32 = bench._window_bytes(info, 4)
+    assert p64 == p32 == 400
+    assert b64 == 8 * 5 + (12 + 8) * 30 + (4 + 8) * 400 + (4 + 8) * 100
+    assert b32 == 8 * 5 + (12 + 4) * 30 + (4 + 4) * 400 + (4 + 4) * 100
+    assert bench._window_bytes(info) == (b64, p64)
+    # a whole pass: every class, both row pointer arrays
+    m = 50
+    annz = 30 + 5 * 12
+    n64 = bench._numeric_bytes(info, m, 8)
+    n32 = bench._numeric_bytes(info, m, 4)
+    assert n64 == 4 * (m + 1) + 12 * annz + 8 * annz + 12 * info["products"] + 8 * (m + 1) + 12 * info["nnz_c"]
+    assert n64 - n32 == 4 * (annz + info["products"] + info["nnz_c"])
+    assert bench._vbytes("f32c") == 4 and bench._vbytes("f64") == 8
